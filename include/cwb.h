@@ -1,0 +1,219 @@
+/*
+ * cwb.h -- C ABI of the GB300 (sm_103a) componentwise boosting library.
+ *
+ * The library fits additive models by componentwise gradient boosting on
+ * binned numerical features (Schalk, Bischl, Ruegamer, arXiv 2110.03513):
+ *
+ *   CWB   App. A.1, Algorithm 1  -- every base learner is fitted to the pseudo
+ *         residuals, the one with the smallest SSE updates the model;
+ *   ACWB  Sec. 3.2, Algorithm 3  -- Nesterov momentum: a primary model f, a
+ *         momentum model h and a second (error-corrected) fit per iteration;
+ *   HCWB  Sec. 3.2.3, Algorithm 4 -- ACWB on training rows until the validation
+ *         risk stops improving for `patience` iterations, then CWB on all rows.
+ *
+ * Each base learner is univariate (Sec. 2.2): a cubic P-spline (B-spline basis
+ * with a difference penalty, App. A.2) or a linear learner (1, x).  Features
+ * are discretised per learner into n* design points with an index vector
+ * (Sec. 3.1.1); every iteration computes Z_k^T W r through the index vector
+ * (binMatVec, Algorithm 2) and solves with the cached (Z_k^T W Z_k + lambda K)^-1.
+ *
+ * Conventions for every entry point:
+ *  - Matrices of observations are feature-major (column-major): X[j * n + i]
+ *    is feature j of row i.
+ *  - `device_ptrs` = 0: pointer arguments are host memory; = 1: they are
+ *    device memory on the model's device (CUDA global memory).  Host buffers
+ *    may be pageable or pinned.
+ *  - Output buffers are allocated by the caller.
+ *  - Nothing crosses the ABI as an exception; every failure returns a
+ *    cwb_status and leaves a message readable through cwb_last_error() on the
+ *    calling thread.  CUDA errors are reported as CWB_ECUDA.
+ *  - A model is not thread-safe: calls on one model must not overlap.
+ *    Different models may be used from different threads.
+ *  - Work is issued on the model's stream (cwb_config.stream).  Calls that
+ *    return host data synchronise that stream; cwb_fit does not, unless a
+ *    device-side error has to be read back (see cwb_fit).
+ */
+#ifndef CWB_H
+#define CWB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cwb_model cwb_model;   /* opaque; owns all device state of one fit */
+
+typedef enum {
+    CWB_OK = 0,
+    CWB_EINVAL = 1,     /* invalid argument or unsupported combination */
+    CWB_ENOMEM = 2,     /* device or host allocation failed */
+    CWB_ECUDA = 3,      /* a CUDA call failed */
+    CWB_ENUMERIC = 4,   /* a factorisation failed or df cannot be reached */
+    CWB_ETIMEOUT = 5,   /* a device-side wait ran out (the kernel returned early) */
+    CWB_ESTATE = 6      /* call not valid in the model's current state */
+} cwb_status;
+
+typedef enum { CWB_LOSS_L2 = 0, CWB_LOSS_BINOMIAL = 1 } cwb_loss;
+typedef enum { CWB_OPT_CWB = 0, CWB_OPT_ACWB = 1, CWB_OPT_HCWB = 2 } cwb_optimizer;
+typedef enum { CWB_BL_PSPLINE = 0, CWB_BL_LINEAR = 1 } cwb_bl_type;
+typedef enum { CWB_F32 = 0, CWB_F64 = 1 } cwb_dtype;
+
+/* n_bins codes (cwb_learner.n_bins) */
+#define CWB_BINS_EXACT 0     /* design points = the sorted unique values of the feature */
+#define CWB_BINS_SQRT (-1)   /* n* = floor(sqrt(n)) equidistant design points (Sec. 3.1.1) */
+
+/* Limits */
+#define CWB_MAX_D 64          /* basis dimension per learner */
+#define CWB_MAX_BINS 65535    /* design points per learner (uint16 index vector) */
+
+/* One univariate base learner (Sec. 2.2). */
+typedef struct {
+    int32_t type;        /* cwb_bl_type */
+    int32_t feature;     /* column of X, 0 <= feature < p */
+    int32_t degree;      /* B-spline degree, 0..3 (P-spline only; 3 = cubic) */
+    int32_t n_knots;     /* interior equidistant knots (P-spline only); d = n_knots + degree + 1 */
+    int32_t diff_order;  /* order of the difference penalty, 1 <= diff_order < d (P-spline only) */
+    double df;           /* > 0: lambda is chosen so that tr(H_k) = df (App. A.2, Eq. df1) */
+    double lambda;       /* used when df <= 0 (P-spline only); linear learners are unpenalised */
+    int32_t n_bins;      /* CWB_BINS_EXACT, CWB_BINS_SQRT, or an explicit n* >= 2 */
+} cwb_learner;
+
+/* Optimiser settings (Algorithm 1, 3, 4 inputs). */
+typedef struct {
+    int32_t loss;              /* cwb_loss; binomial needs y in {0, 1} */
+    int32_t opt;               /* cwb_optimizer */
+    double nu;                 /* learning rate nu > 0 */
+    double gamma;              /* momentum parameter gamma >= 0 (ACWB/HCWB) */
+    int32_t iterations;        /* default M for cwb_fit(model, 0) */
+    int32_t patience;          /* pat_0 >= 0 (HCWB) */
+    const uint8_t* val_mask;   /* HCWB: n entries, 1 = validation row; same memory kind as X */
+    void* stream;              /* cudaStream_t to issue work on; NULL = the legacy default stream */
+    int32_t device;            /* CUDA device ordinal; -1 = the calling thread's current device */
+} cwb_config;
+
+/* Per-learner description after setup. */
+typedef struct {
+    int32_t d;            /* basis dimension */
+    int32_t nstar;        /* number of design points n* */
+    int32_t binning;      /* index of the shared binning (learners on the same feature and n_bins share one) */
+    int32_t reserved;
+    double xmin, xmax;    /* training range of the feature */
+    double lambda;        /* smoothing parameter of the first phase (train rows for HCWB) */
+    double lambda_full;   /* smoothing parameter on all rows (HCWB second phase; = lambda otherwise) */
+} cwb_learner_info;
+
+/*
+ * cwb_create -- set up a model: copy and bin the data, build the reduced designs,
+ * choose lambda per learner from its df and cache the inverse of
+ * Z_k^T W Z_k + lambda K_k (Sec. 2.4, Sec. 3.1.2: factorise once before boosting).
+ *
+ *   cfg         optimiser settings (copied; the val_mask is read during the call only)
+ *   X           p x n feature-major observations, dtype x_dtype (CWB_F32 or CWB_F64)
+ *   n, p        rows (>= 2) and features (>= 1)
+ *   y           n targets, same dtype as X
+ *   w           n observation weights (> 0) in FP64, or NULL for w = 1 (App. A.2, W_k = diag(w))
+ *   bl, K       K >= 1 base learners
+ *   device_ptrs 0: X, y, w, val_mask are host pointers; 1: device pointers.  Either way
+ *               the model keeps its own copies; the caller's buffers are only read
+ *               during this call.
+ *   out         receives the new model (NULL on failure)
+ *
+ * Errors: CWB_EINVAL for bad sizes, a constant feature (max == min), n* outside
+ * [2, 65535], d > CWB_MAX_D, binomial targets outside {0, 1}, or HCWB without a
+ * validation mask holding at least one training and one validation row;
+ * CWB_ENUMERIC if a Gram matrix is singular or df is not reachable;
+ * CWB_ENOMEM / CWB_ECUDA on device failures.
+ */
+cwb_status cwb_create(const cwb_config* cfg, const void* X, int32_t x_dtype, int64_t n, int32_t p,
+                      const void* y, const double* w, const cwb_learner* bl, int32_t K,
+                      int32_t device_ptrs, cwb_model** out);
+
+/*
+ * cwb_fit -- run `iterations` boosting iterations (<= 0: cfg.iterations) on the
+ * device, continuing from the model's current state (fits are resumable).  One
+ * iteration is: pseudo residuals, binMatVec scatter of W r into every binning's
+ * histogram (Algorithm 2), Z^T u, theta = P (Z^T u), the SSE criterion, argmin
+ * over learners and the update f += nu Z_k theta_k (Algorithm 1; Algorithm 3 for
+ * ACWB with two fits per iteration).  No host synchronisation happens between
+ * iterations; the call returns once the work is queued on the model's stream.
+ * A device-side wait that ran out is reported by the next call that
+ * synchronises, as CWB_ETIMEOUT.
+ */
+cwb_status cwb_fit(cwb_model* m, int32_t iterations);
+
+/*
+ * cwb_predict -- evaluate offset + sum_k g_k(x)^T theta_k (primary model, aggregated
+ * parameters; Sec. 2.3, Sec. 3.2.1) at n_new new rows.  Xnew is p x n_new
+ * feature-major (dtype x_dtype); values are clamped to each learner's training
+ * range.  `out` receives n_new FP32 predictions on the link scale.  Memory kind of
+ * Xnew and out follows device_ptrs.  Synchronises the model's stream.
+ */
+cwb_status cwb_predict(const cwb_model* m, const void* Xnew, int32_t x_dtype, int64_t n_new, float* out,
+                       int32_t device_ptrs);
+
+/*
+ * cwb_get_coefficients -- aggregated parameters of learner k (eq. (1) additivity;
+ * Sec. 3.2.1 for ACWB/HCWB).  which = 0: primary model theta_f; which = 1: momentum
+ * model theta_h (zeros for CWB).  theta receives min(d_k, cap) FP64 values (host
+ * memory); *offset (nullable) receives the constant initial model.
+ */
+cwb_status cwb_get_coefficients(const cwb_model* m, int32_t k, int32_t which, double* theta, int32_t cap,
+                                double* offset);
+
+/*
+ * cwb_get_trace -- selected learners per iteration (0-based), host memory.
+ * k_sel[t] for t < min(cap, done); k_cor (nullable) the correction learner of
+ * ACWB iterations, -1 for CWB iterations; *switch_iter (nullable) the first CWB
+ * iteration of HCWB (1-based) or 0; *done (nullable) iterations run so far.
+ */
+cwb_status cwb_get_trace(const cwb_model* m, int32_t* k_sel, int32_t* k_cor, int32_t cap, int32_t* switch_iter,
+                         int32_t* done);
+
+/*
+ * cwb_get_criteria -- per iteration t < min(cap, done), the best and second-best
+ * value of Q_k = theta^T G theta - 2 theta^T s (SSE_k minus the common r^T W r)
+ * of the primary fit, FP64, host memory.  For checking near ties.
+ */
+cwb_status cwb_get_criteria(const cwb_model* m, double* q_best, double* q_second, int32_t cap);
+
+/*
+ * cwb_get_fitted -- the primary model at the n training rows (original row order),
+ * FP32, memory kind per device_ptrs.  Synchronises the model's stream.
+ */
+cwb_status cwb_get_fitted(const cwb_model* m, float* f, int32_t device_ptrs);
+
+/* cwb_get_learner_info -- setup results of learner k. */
+cwb_status cwb_get_learner_info(const cwb_model* m, int32_t k, cwb_learner_info* info);
+
+/*
+ * cwb_get_learner_matrices -- FP64 d x d row-major G = Z^T W Z and P = (G + lambda K)^-1
+ * of learner k for phase 0 (first phase) or 1 (all rows, HCWB).  Either pointer may be NULL.
+ */
+cwb_status cwb_get_learner_matrices(const cwb_model* m, int32_t k, int32_t phase, double* G, double* P);
+
+/* cwb_get_bin_index -- index vector of learner k (n entries, original row order, 0-based), host int32. */
+cwb_status cwb_get_bin_index(const cwb_model* m, int32_t k, int32_t* ind);
+
+/*
+ * cwb_force_selection -- testing hook: for the next `count` iterations the primary
+ * learner is `k_forced[t]` instead of the argmin (k_forced host int32, -1 = no
+ * override).  Used to keep comparing against the FP64 oracle past a near tie.
+ */
+cwb_status cwb_force_selection(cwb_model* m, const int32_t* k_forced, int32_t count);
+
+/* cwb_synchronize -- wait for the model's queued work; reports device-side errors. */
+cwb_status cwb_synchronize(cwb_model* m);
+
+/* cwb_last_error -- message of the last failure on the calling thread ("" if none). */
+const char* cwb_last_error(void);
+
+/* cwb_free -- release a model and all its device memory; NULL is a no-op. */
+void cwb_free(cwb_model* m);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CWB_H */

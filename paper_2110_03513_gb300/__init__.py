@@ -1,0 +1,13 @@
+"""GB300 (sm_103a) componentwise boosting: Python binding of the C ABI in include/cwb.h.
+
+The functions named ``cwb_*`` mirror the C entry points one to one (argument
+marshalling only); :class:`Model` is a small convenience wrapper built on
+them.  Every step of the method runs in the CUDA library; importing this
+package fails loudly if ``libcwb.so`` has not been built.
+"""
+from .binding import (  # noqa: F401
+    BINS_EXACT, BINS_SQRT, BL_LINEAR, BL_PSPLINE, LOSS_BINOMIAL, LOSS_L2, OPT_ACWB, OPT_CWB, OPT_HCWB,
+    CwbError, Model, cwb_create, cwb_fit, cwb_force_selection, cwb_free, cwb_get_bin_index, cwb_get_coefficients,
+    cwb_get_criteria, cwb_get_fitted, cwb_get_learner_info, cwb_get_learner_matrices, cwb_get_trace,
+    cwb_last_error, cwb_predict, cwb_synchronize, learner, library_path, load_library,
+)

@@ -1,0 +1,324 @@
+"""ctypes binding of libcwb.so (include/cwb.h).
+
+Arrays may be numpy arrays (host memory, device_ptrs = 0) or CUDA tensors /
+objects exposing ``data_ptr()`` (device memory, device_ptrs = 1).  Nothing
+here computes any part of the method.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libcwb.so")
+
+LOSS_L2, LOSS_BINOMIAL = 0, 1
+OPT_CWB, OPT_ACWB, OPT_HCWB = 0, 1, 2
+BL_PSPLINE, BL_LINEAR = 0, 1
+F32, F64 = 0, 1
+BINS_EXACT, BINS_SQRT = 0, -1
+
+_STATUS = {0: "CWB_OK", 1: "CWB_EINVAL", 2: "CWB_ENOMEM", 3: "CWB_ECUDA", 4: "CWB_ENUMERIC", 5: "CWB_ETIMEOUT",
+           6: "CWB_ESTATE"}
+
+
+class CwbError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__(f"{where}: {_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class cwb_learner(C.Structure):
+    _fields_ = [("type", C.c_int32), ("feature", C.c_int32), ("degree", C.c_int32), ("n_knots", C.c_int32),
+                ("diff_order", C.c_int32), ("df", C.c_double), ("lam", C.c_double), ("n_bins", C.c_int32)]
+
+
+class cwb_config(C.Structure):
+    _fields_ = [("loss", C.c_int32), ("opt", C.c_int32), ("nu", C.c_double), ("gamma", C.c_double),
+                ("iterations", C.c_int32), ("patience", C.c_int32), ("val_mask", C.c_void_p),
+                ("stream", C.c_void_p), ("device", C.c_int32)]
+
+
+class cwb_learner_info(C.Structure):
+    _fields_ = [("d", C.c_int32), ("nstar", C.c_int32), ("binning", C.c_int32), ("reserved", C.c_int32),
+                ("xmin", C.c_double), ("xmax", C.c_double), ("lam", C.c_double), ("lam_full", C.c_double)]
+
+
+_lib = None
+
+_SIGS = {
+    "cwb_create": (C.c_int, [C.POINTER(cwb_config), C.c_void_p, C.c_int32, C.c_int64, C.c_int32, C.c_void_p,
+                             C.c_void_p, C.POINTER(cwb_learner), C.c_int32, C.c_int32, C.POINTER(C.c_void_p)]),
+    "cwb_fit": (C.c_int, [C.c_void_p, C.c_int32]),
+    "cwb_predict": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int64, C.c_void_p, C.c_int32]),
+    "cwb_get_coefficients": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p]),
+    "cwb_get_trace": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
+    "cwb_get_criteria": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
+    "cwb_get_fitted": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
+    "cwb_get_learner_info": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(cwb_learner_info)]),
+    "cwb_get_learner_matrices": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]),
+    "cwb_get_bin_index": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
+    "cwb_force_selection": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
+    "cwb_synchronize": (C.c_int, [C.c_void_p]),
+    "cwb_last_error": (C.c_char_p, []),
+    "cwb_free": (None, [C.c_void_p]),
+}
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load_library():
+    """Load libcwb.so (built by __graft_entry__.build()); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise ImportError(f"{_LIB_PATH} is missing: build the CUDA library first "
+                              "(python -c 'import __graft_entry__ as g; g.build()')")
+        lib = C.CDLL(_LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def cwb_last_error() -> str:
+    return load_library().cwb_last_error().decode()
+
+
+def _check(st: int, where: str):
+    if st != 0:
+        raise CwbError(st, where, cwb_last_error())
+
+
+def _is_device(a) -> bool:
+    return hasattr(a, "data_ptr") and getattr(a, "is_cuda", False)
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if _is_device(a):
+        return C.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _dtype_code(a) -> int:
+    name = str(a.dtype)
+    if name.endswith("float64"):
+        return F64
+    if name.endswith("float32"):
+        return F32
+    raise TypeError(f"unsupported dtype {a.dtype}; use float32 or float64")
+
+
+def learner(feature: int, *, type: int = BL_PSPLINE, degree: int = 3, n_knots: int = 20, diff_order: int = 2,
+            df: float = 5.0, lam: float = 0.0, n_bins: int = BINS_SQRT) -> cwb_learner:
+    return cwb_learner(type=type, feature=feature, degree=degree, n_knots=n_knots, diff_order=diff_order, df=df,
+                       lam=lam, n_bins=n_bins)
+
+
+# ---- one wrapper per C entry point -------------------------------------------------
+
+def cwb_create(cfg: cwb_config, X, x_dtype: int, n: int, p: int, y, w, learners, device_ptrs: int) -> C.c_void_p:
+    arr = (cwb_learner * len(learners))(*learners)
+    out = C.c_void_p()
+    st = load_library().cwb_create(C.byref(cfg), _ptr(X), x_dtype, n, p, _ptr(y), _ptr(w), arr, len(learners),
+                                   device_ptrs, C.byref(out))
+    _check(st, "cwb_create")
+    return out
+
+
+def cwb_fit(model, iterations: int):
+    _check(load_library().cwb_fit(model, iterations), "cwb_fit")
+
+
+def cwb_predict(model, Xnew, x_dtype: int, n_new: int, out, device_ptrs: int):
+    _check(load_library().cwb_predict(model, _ptr(Xnew), x_dtype, n_new, _ptr(out), device_ptrs), "cwb_predict")
+
+
+def cwb_get_coefficients(model, k: int, which: int, theta: np.ndarray, offset: np.ndarray | None = None):
+    _check(load_library().cwb_get_coefficients(model, k, which, _ptr(theta), theta.size, _ptr(offset)),
+           "cwb_get_coefficients")
+
+
+def cwb_get_trace(model, k_sel: np.ndarray, k_cor: np.ndarray | None, switch_iter: np.ndarray | None,
+                  done: np.ndarray | None):
+    _check(load_library().cwb_get_trace(model, _ptr(k_sel), _ptr(k_cor), k_sel.size, _ptr(switch_iter),
+                                        _ptr(done)), "cwb_get_trace")
+
+
+def cwb_get_criteria(model, q_best: np.ndarray, q_second: np.ndarray):
+    _check(load_library().cwb_get_criteria(model, _ptr(q_best), _ptr(q_second), q_best.size), "cwb_get_criteria")
+
+
+def cwb_get_fitted(model, f, device_ptrs: int):
+    _check(load_library().cwb_get_fitted(model, _ptr(f), device_ptrs), "cwb_get_fitted")
+
+
+def cwb_get_learner_info(model, k: int) -> cwb_learner_info:
+    info = cwb_learner_info()
+    _check(load_library().cwb_get_learner_info(model, k, C.byref(info)), "cwb_get_learner_info")
+    return info
+
+
+def cwb_get_learner_matrices(model, k: int, phase: int, G: np.ndarray | None, P: np.ndarray | None):
+    _check(load_library().cwb_get_learner_matrices(model, k, phase, _ptr(G), _ptr(P)), "cwb_get_learner_matrices")
+
+
+def cwb_get_bin_index(model, k: int, ind: np.ndarray):
+    _check(load_library().cwb_get_bin_index(model, k, _ptr(ind)), "cwb_get_bin_index")
+
+
+def cwb_force_selection(model, k_forced: np.ndarray):
+    _check(load_library().cwb_force_selection(model, _ptr(k_forced), k_forced.size), "cwb_force_selection")
+
+
+def cwb_synchronize(model):
+    _check(load_library().cwb_synchronize(model), "cwb_synchronize")
+
+
+def cwb_free(model):
+    if model:
+        load_library().cwb_free(model)
+
+
+# ---- convenience wrapper --------------------------------------------------------
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(getattr(stream, "cuda_stream"))
+
+
+class Model:
+    """A fitted (or fitting) componentwise boosting model on one GPU.
+
+    X is p x n feature-major (numpy on the host, or a CUDA tensor); y has n
+    entries of the same dtype; learners is a list of ``learner(...)`` specs.
+    """
+
+    def __init__(self, X, y, learners, *, loss=LOSS_L2, opt=OPT_CWB, nu=0.1, gamma=0.0, iterations=100,
+                 patience=5, val_mask=None, w=None, stream=None, device=-1):
+        dev = _is_device(X)
+        if not dev:
+            X = np.ascontiguousarray(X)
+            y = np.ascontiguousarray(y, dtype=X.dtype)
+            w = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
+            val_mask = None if val_mask is None else np.ascontiguousarray(val_mask, dtype=np.uint8)
+        if X.ndim == 1:
+            X = X.reshape(1, -1)
+        p, n = int(X.shape[0]), int(X.shape[1])
+        self.p, self.n = p, n
+        self.learners = list(learners)
+        self._keep = (X, y, w, val_mask)
+        sh = _stream_handle(stream)
+        cfg = cwb_config(loss=loss, opt=opt, nu=nu, gamma=gamma, iterations=iterations, patience=patience,
+                         val_mask=None if val_mask is None else _ptr(val_mask).value,
+                         stream=sh, device=device)
+        self.handle = cwb_create(cfg, X, _dtype_code(X), n, p, y, w, self.learners, 1 if dev else 0)
+        self._keep = None
+
+    def __del__(self):
+        self.free()
+
+    def free(self):
+        h = getattr(self, "handle", None)
+        if h:
+            cwb_free(h)
+            self.handle = None
+
+    def fit(self, iterations: int = 0):
+        cwb_fit(self.handle, iterations)
+        return self
+
+    def synchronize(self):
+        cwb_synchronize(self.handle)
+
+    def predict(self, Xnew, out=None):
+        dev = _is_device(Xnew)
+        if not dev:
+            Xnew = np.ascontiguousarray(Xnew)
+            if Xnew.ndim == 1:
+                Xnew = Xnew.reshape(1, -1)
+        n_new = int(Xnew.shape[1])
+        if out is None:
+            if dev:
+                import torch
+                out = torch.empty(n_new, dtype=torch.float32, device=Xnew.device)
+            else:
+                out = np.empty(n_new, dtype=np.float32)
+        cwb_predict(self.handle, Xnew, _dtype_code(Xnew), n_new, out, 1 if dev else 0)
+        return out
+
+    def coefficients(self, k: int, which: int = 0) -> np.ndarray:
+        info = cwb_get_learner_info(self.handle, k)
+        theta = np.zeros(info.d, dtype=np.float64)
+        cwb_get_coefficients(self.handle, k, which, theta)
+        return theta
+
+    def all_coefficients(self, which: int = 0, dmax: int | None = None) -> np.ndarray:
+        ds = [cwb_get_learner_info(self.handle, k).d for k in range(len(self.learners))]
+        D = dmax or max(ds)
+        out = np.zeros((len(ds), D))
+        for k, d in enumerate(ds):
+            th = np.zeros(d)
+            cwb_get_coefficients(self.handle, k, which, th)
+            out[k, :d] = th
+        return out
+
+    @property
+    def offset(self) -> float:
+        theta = np.zeros(1, dtype=np.float64)
+        off = np.zeros(1, dtype=np.float64)
+        cwb_get_coefficients(self.handle, 0, 0, theta, off)
+        return float(off[0])
+
+    def trace(self):
+        done = np.zeros(1, dtype=np.int32)
+        sw = np.zeros(1, dtype=np.int32)
+        probe = np.zeros(0, dtype=np.int32)
+        cwb_get_trace(self.handle, probe, None, sw, done)
+        M = int(done[0])
+        k_sel = np.zeros(M, dtype=np.int32)
+        k_cor = np.zeros(M, dtype=np.int32)
+        cwb_get_trace(self.handle, k_sel, k_cor, sw, done)
+        return k_sel, k_cor, int(sw[0])
+
+    def criteria(self):
+        k_sel, _, _ = self.trace()
+        qb = np.zeros(k_sel.size)
+        qs = np.zeros(k_sel.size)
+        cwb_get_criteria(self.handle, qb, qs)
+        return qb, qs
+
+    def fitted(self, out=None):
+        if out is None:
+            out = np.empty(self.n, dtype=np.float32)
+        cwb_get_fitted(self.handle, out, 1 if _is_device(out) else 0)
+        return out
+
+    def learner_info(self, k: int) -> cwb_learner_info:
+        return cwb_get_learner_info(self.handle, k)
+
+    def matrices(self, k: int, phase: int = 0):
+        d = cwb_get_learner_info(self.handle, k).d
+        G = np.zeros((d, d))
+        P = np.zeros((d, d))
+        cwb_get_learner_matrices(self.handle, k, phase, G, P)
+        return G, P
+
+    def bin_index(self, k: int) -> np.ndarray:
+        ind = np.zeros(self.n, dtype=np.int32)
+        cwb_get_bin_index(self.handle, k, ind)
+        return ind
+
+    def force_selection(self, ks):
+        cwb_force_selection(self.handle, np.ascontiguousarray(ks, dtype=np.int32))

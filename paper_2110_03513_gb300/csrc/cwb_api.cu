@@ -1,0 +1,564 @@
+// cwb_api.cu -- the C ABI (include/cwb.h): argument checks, model lifecycle,
+// prediction and read-back.  All arithmetic of the method runs in kernels;
+// host code here validates, allocates, orders launches and copies results.
+#include <math.h>
+
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "cwb_internal.cuh"
+
+namespace cwb {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+cwb_status cuda_status(cudaError_t e, const char* what)
+{
+    set_error(std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e));
+    return (e == cudaErrorMemoryAllocation) ? CWB_ENOMEM : CWB_ECUDA;
+}
+
+cwb_status dev_alloc(void** p, size_t bytes, cudaStream_t)
+{
+    *p = nullptr;
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        set_error(std::string("device allocation of ") + std::to_string(bytes) + " bytes failed: " +
+                  cudaGetErrorString(e));
+        return CWB_ENOMEM;
+    }
+    return CWB_OK;
+}
+
+void dev_free(void* p)
+{
+    if (p) cudaFree(p);
+}
+
+namespace {
+
+// Evaluate g_k(x)^T theta for a P-spline (B-spline basis on the equidistant
+// extended knot vector, Sec. 2.2) or a linear learner (1, x).
+__device__ __forceinline__ double knot_at(double xmin, double delta, int i_minus_q)
+{
+    return __dadd_rn(xmin, __dmul_rn((double)i_minus_q, delta));
+}
+
+__device__ double learner_eval(double x, int type, int q, int nk, double xmin, double xmax, const double* theta)
+{
+    if (type == CWB_BL_LINEAR) return theta[0] + theta[1] * x;
+    const double delta = __ddiv_rn(__dsub_rn(xmax, xmin), (double)(nk + 1));
+    const int last = nk + q;
+    int mu = (int)floor(__ddiv_rn(__dsub_rn(x, xmin), delta)) + q;
+    if (mu < q) mu = q;
+    if (mu > last) mu = last;
+    while (mu > q && x < knot_at(xmin, delta, mu - q)) --mu;
+    while (mu < last && x >= knot_at(xmin, delta, mu + 1 - q)) ++mu;
+    double N[kMaxNnz], left[kMaxNnz], right[kMaxNnz];
+    N[0] = 1.0;
+    for (int j = 1; j <= q; ++j) {
+        left[j] = x - knot_at(xmin, delta, mu + 1 - j - q);
+        right[j] = knot_at(xmin, delta, mu + j - q) - x;
+        double saved = 0.0;
+        for (int r = 0; r < j; ++r) {
+            double tmp = N[r] / (right[r + 1] + left[j - r]);
+            N[r] = saved + right[r + 1] * tmp;
+            saved = left[j - r] * tmp;
+        }
+        N[j] = saved;
+    }
+    double acc = 0.0;
+    for (int t = 0; t <= q; ++t) acc += N[t] * theta[mu - q + t];
+    return acc;
+}
+
+template <typename T>
+__global__ void k_predict(const T* __restrict__ X, int64_t n_new, int K, int D, const int32_t* __restrict__ l_feat,
+                          const int32_t* __restrict__ l_type, const int32_t* __restrict__ l_degree,
+                          const int32_t* __restrict__ l_nknots, const double* __restrict__ l_xmin,
+                          const double* __restrict__ l_xmax, const double* __restrict__ coef, double offset,
+                          float* __restrict__ out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_new; i += (int64_t)gridDim.x * blockDim.x) {
+        double acc = offset;
+        for (int k = 0; k < K; ++k) {
+            double x = (double)X[(int64_t)l_feat[k] * n_new + i];
+            const double lo = l_xmin[k], hi = l_xmax[k];
+            x = fmin(fmax(x, lo), hi);
+            acc += learner_eval(x, l_type[k], l_degree[k], l_nknots[k], lo, hi, coef + (int64_t)k * D);
+        }
+        out[i] = (float)acc;
+    }
+}
+
+__global__ void k_unpermute(const float* __restrict__ f, const int32_t* __restrict__ perm, int64_t n,
+                            float* __restrict__ out)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+        out[perm ? perm[q] : q] = f[q];
+}
+
+int grid_1d(int64_t work, int device)
+{
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    int64_t g = (work + 255) / 256;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(g, (int64_t)std::max(sms, 1) * 8));
+}
+
+// Makes the model's device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+void free_model(cwb_model* m)
+{
+    if (!m) return;
+    if (m->stream) cudaStreamSynchronize(m->stream);
+    void* bufs[] = {m->ind, m->y, m->w, m->f, m->h, m->c, m->rw, m->perm, m->zb, m->zb64, m->zcol, m->crange, m->G,
+                    m->P, m->lambda, m->l_bin, m->l_d, m->l_nstar, m->l_type, m->l_xmin, m->l_xmax, m->l_degree,
+                    m->l_nknots, m->l_feat, m->part, m->theta_it, m->q_it, m->v, m->state, m->risk_part, m->tr_k,
+                    m->tr_mode, m->tr_theta, m->tr_q, m->forced, m->coef};
+    for (void* p : bufs) dev_free(p);
+    if (m->graph_exec) cudaGraphExecDestroy(m->graph_exec);
+    if (m->capture_stream) cudaStreamDestroy(m->capture_stream);
+    if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
+    delete m;
+}
+
+cwb_status validate_learner(const cwb_learner& b, int32_t p, int k)
+{
+    auto bad = [&](const std::string& why) {
+        set_error("learner " + std::to_string(k) + ": " + why);
+        return CWB_EINVAL;
+    };
+    if (b.feature < 0 || b.feature >= p) return bad("feature index out of range");
+    if (b.type != CWB_BL_PSPLINE && b.type != CWB_BL_LINEAR) return bad("unknown base-learner type");
+    if (b.n_bins != CWB_BINS_EXACT && b.n_bins != CWB_BINS_SQRT && (b.n_bins < 2 || b.n_bins > CWB_MAX_BINS))
+        return bad("n_bins must be CWB_BINS_EXACT, CWB_BINS_SQRT or in [2, 65535]");
+    if (b.type == CWB_BL_PSPLINE) {
+        if (b.degree < 0 || b.degree > 3) return bad("degree must be in [0, 3]");
+        if (b.n_knots < 0) return bad("n_knots must be >= 0");
+        int d = b.n_knots + b.degree + 1;
+        if (d > CWB_MAX_D) return bad("basis dimension exceeds CWB_MAX_D");
+        if (b.diff_order < 1 || b.diff_order >= d) return bad("diff_order must be in [1, d)");
+        if (!(b.df > 0.0) && !(b.lambda >= 0.0)) return bad("need df > 0 or lambda >= 0");
+        if (b.df > 0.0 && !(b.df > b.diff_order)) return bad("df must exceed the penalty null-space dimension");
+    }
+    return CWB_OK;
+}
+
+cwb_status create_impl(const cwb_config* cfg, const void* X, int32_t x_dtype, int64_t n, int32_t p, const void* y,
+                       const double* w, const cwb_learner* bl, int32_t K, int32_t device_ptrs, cwb_model** out)
+{
+    if (!out) { set_error("out is NULL"); return CWB_EINVAL; }
+    *out = nullptr;
+    if (!cfg || !X || !y || !bl) { set_error("NULL argument"); return CWB_EINVAL; }
+    if (n < 2 || n > (int64_t)INT32_MAX) { set_error("n must be in [2, 2^31-1]"); return CWB_EINVAL; }
+    if (p < 1 || K < 1) { set_error("p and K must be >= 1"); return CWB_EINVAL; }
+    if (x_dtype != CWB_F32 && x_dtype != CWB_F64) { set_error("x_dtype must be CWB_F32 or CWB_F64"); return CWB_EINVAL; }
+    if (cfg->loss != CWB_LOSS_L2 && cfg->loss != CWB_LOSS_BINOMIAL) { set_error("unknown loss"); return CWB_EINVAL; }
+    if (cfg->opt < CWB_OPT_CWB || cfg->opt > CWB_OPT_HCWB) { set_error("unknown optimizer"); return CWB_EINVAL; }
+    if (!(cfg->nu > 0.0) || !isfinite(cfg->nu)) { set_error("nu must be > 0"); return CWB_EINVAL; }
+    if (!(cfg->gamma >= 0.0) || !isfinite(cfg->gamma)) { set_error("gamma must be >= 0"); return CWB_EINVAL; }
+    if (cfg->iterations < 0 || cfg->patience < 0) { set_error("iterations and patience must be >= 0"); return CWB_EINVAL; }
+    if (cfg->opt == CWB_OPT_HCWB && !cfg->val_mask) { set_error("HCWB needs a validation mask"); return CWB_EINVAL; }
+    for (int k = 0; k < K; ++k) CWB_TRY(validate_learner(bl[k], p, k));
+
+    cwb_model* m = new cwb_model();
+    int dev = cfg->device;
+    if (dev < 0) {
+        if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+    }
+    m->device = dev;
+    DeviceGuard guard(dev);
+    if (!guard.ok) {
+        delete m;
+        set_error("cannot select CUDA device " + std::to_string(dev));
+        return CWB_ECUDA;
+    }
+    m->cfg = *cfg;
+    m->cfg.val_mask = nullptr;
+    m->cfg.device = dev;
+    m->n = n;
+    m->p = p;
+    m->K = K;
+    m->hybrid = cfg->opt == CWB_OPT_HCWB;
+    m->accel = cfg->opt != CWB_OPT_CWB;
+    if (cfg->stream) {
+        m->stream = static_cast<cudaStream_t>(cfg->stream);
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete m;
+            return cuda_status(e, "cudaStreamCreate");
+        }
+        m->own_stream = true;
+    }
+    // learners on the same feature with the same binning share one index vector
+    std::map<std::pair<int, int>, int> bmap;
+    for (int k = 0; k < K; ++k) {
+        HostLearner L;
+        L.spec = bl[k];
+        auto key = std::make_pair(bl[k].feature, bl[k].n_bins);
+        auto it = bmap.find(key);
+        if (it == bmap.end()) {
+            HostBinning hb{};
+            hb.feature = bl[k].feature;
+            hb.nbins_spec = bl[k].n_bins;
+            it = bmap.emplace(key, (int)m->bins.size()).first;
+            m->bins.push_back(hb);
+        }
+        L.binning = it->second;
+        if (bl[k].type == CWB_BL_LINEAR) {
+            L.d = 2;
+            L.nnz = 2;
+        } else {
+            L.d = bl[k].n_knots + bl[k].degree + 1;
+            L.nnz = bl[k].degree + 1;
+        }
+        m->lrn.push_back(L);
+    }
+    m->B = (int)m->bins.size();
+
+    cwb_status st = setup_model(m, X, x_dtype, y, w, cfg->val_mask, device_ptrs);
+    if (st == CWB_OK) {
+        for (int k = 0; k < K; ++k) {
+            const cwb_learner& b = bl[k];
+            if (b.type == CWB_BL_PSPLINE && m->bins[m->lrn[k].binning].nstar < 2) st = CWB_EINVAL;
+        }
+    }
+    if (st == CWB_OK) st = plan_scatter(m);
+    if (st == CWB_OK) {
+        const int S = m->nstar_max, D = m->d_max;
+        std::vector<int32_t> feat(K);
+        for (int k = 0; k < K; ++k) feat[k] = bl[k].feature;
+        int32_t* l_feat = nullptr;
+        st = dev_alloc((void**)&m->part, sizeof(float) * std::max<size_t>(m->plan.part_floats, 1), m->stream);
+        if (st == CWB_OK) st = dev_alloc((void**)&m->theta_it, sizeof(double) * 2 * K * D, m->stream);
+        if (st == CWB_OK) st = dev_alloc((void**)&m->q_it, sizeof(double) * 2 * K, m->stream);
+        if (st == CWB_OK) st = dev_alloc((void**)&m->v, sizeof(float) * (2 * (size_t)S + 2 * (size_t)K * S), m->stream);
+        if (st == CWB_OK) st = dev_alloc((void**)&m->state, sizeof(DevState), m->stream);
+        if (st == CWB_OK) st = dev_alloc((void**)&m->coef, sizeof(double) * 2 * K * D, m->stream);
+        if (st == CWB_OK) st = dev_alloc((void**)&l_feat, sizeof(int32_t) * K, m->stream);
+        if (st == CWB_OK) {
+            m->risk_blocks = 0;
+            int sms = 0;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            st = dev_alloc((void**)&m->risk_part, sizeof(double) * (size_t)std::max(sms, 1) * 8, m->stream);
+        }
+        if (st == CWB_OK) {
+            cudaError_t e = cudaMemcpyAsync(l_feat, feat.data(), sizeof(int32_t) * K, cudaMemcpyHostToDevice, m->stream);
+            if (e != cudaSuccess) st = cuda_status(e, "cudaMemcpyAsync");
+        }
+        if (st == CWB_OK) {
+            DevState s0{};
+            s0.m = 0;
+            s0.m_applied = 0;
+            s0.mode = m->accel ? kModeACWB : kModeCWB;
+            s0.phase = 0;
+            s0.k_sel = -1;
+            s0.k_cor = -1;
+            s0.pend_mode = kModeCWB;
+            cudaError_t e = cudaMemcpyAsync(m->state, &s0, sizeof(s0), cudaMemcpyHostToDevice, m->stream);
+            if (e == cudaSuccess) e = cudaMemsetAsync(m->v, 0, sizeof(float) * 2 * S, m->stream);
+            if (e == cudaSuccess) e = cudaMemsetAsync(m->coef, 0, sizeof(double) * 2 * K * D, m->stream);
+            if (e != cudaSuccess) st = cuda_status(e, "state init");
+        }
+        if (st == CWB_OK) st = ensure_trace(m, std::max(cfg->iterations, 1));
+        if (st == CWB_OK) st = launch_initial_rows(m);
+        if (st == CWB_OK) {
+            cudaError_t e = cudaStreamSynchronize(m->stream);
+            if (e != cudaSuccess) st = cuda_status(e, "create");
+        }
+        if (st == CWB_OK) st = read_device_error(m);
+        if (st == CWB_OK) m->l_feat = l_feat;
+        else dev_free(l_feat);
+    }
+    if (st != CWB_OK) {
+        free_model(m);
+        return st;
+    }
+    *out = m;
+    return CWB_OK;
+}
+
+}  // namespace
+
+cwb_status launch_predict(const cwb_model* m, const void* Xnew, int x_dtype, int64_t n_new, float* out_dev)
+{
+    const int g = grid_1d(n_new, m->device);
+    if (x_dtype == CWB_F64)
+        k_predict<<<g, 256, 0, m->stream>>>((const double*)Xnew, n_new, m->K, m->d_max, m->l_feat, m->l_type,
+                                            m->l_degree, m->l_nknots, m->l_xmin, m->l_xmax, m->coef, m->offset,
+                                            out_dev);
+    else
+        k_predict<<<g, 256, 0, m->stream>>>((const float*)Xnew, n_new, m->K, m->d_max, m->l_feat, m->l_type,
+                                            m->l_degree, m->l_nknots, m->l_xmin, m->l_xmax, m->coef, m->offset,
+                                            out_dev);
+    CWB_CUDA_TRY(cudaGetLastError());
+    return CWB_OK;
+}
+
+}  // namespace cwb
+
+using namespace cwb;
+
+extern "C" {
+
+cwb_status cwb_create(const cwb_config* cfg, const void* X, int32_t x_dtype, int64_t n, int32_t p, const void* y,
+                      const double* w, const cwb_learner* bl, int32_t K, int32_t device_ptrs, cwb_model** out)
+{
+    set_error("");
+    try {
+        return create_impl(cfg, X, x_dtype, n, p, y, w, bl, K, device_ptrs, out);
+    } catch (const std::exception& e) {
+        set_error(std::string("host exception: ") + e.what());
+        return CWB_ENOMEM;
+    }
+}
+
+cwb_status cwb_fit(cwb_model* m, int32_t iterations)
+{
+    set_error("");
+    if (!m) { set_error("model is NULL"); return CWB_EINVAL; }
+    DeviceGuard guard(m->device);
+    int32_t it = iterations > 0 ? iterations : m->cfg.iterations;
+    if (it <= 0) return CWB_OK;
+    try {
+        CWB_TRY(launch_iterations(m, it));
+        CWB_TRY(launch_final_update(m));
+    } catch (const std::exception& e) {
+        set_error(std::string("host exception: ") + e.what());
+        return CWB_ENOMEM;
+    }
+    return CWB_OK;
+}
+
+cwb_status cwb_synchronize(cwb_model* m)
+{
+    set_error("");
+    if (!m) { set_error("model is NULL"); return CWB_EINVAL; }
+    DeviceGuard guard(m->device);
+    CWB_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    return read_device_error(m);
+}
+
+cwb_status cwb_predict(const cwb_model* mc, const void* Xnew, int32_t x_dtype, int64_t n_new, float* out,
+                       int32_t device_ptrs)
+{
+    set_error("");
+    cwb_model* m = const_cast<cwb_model*>(mc);
+    if (!m || !Xnew || !out) { set_error("NULL argument"); return CWB_EINVAL; }
+    if (n_new < 0) { set_error("n_new must be >= 0"); return CWB_EINVAL; }
+    if (x_dtype != CWB_F32 && x_dtype != CWB_F64) { set_error("x_dtype must be CWB_F32 or CWB_F64"); return CWB_EINVAL; }
+    if (n_new == 0) return CWB_OK;
+    DeviceGuard guard(m->device);
+    CWB_TRY(launch_aggregate(m));
+    const size_t xsz = (x_dtype == CWB_F64 ? 8 : 4) * (size_t)n_new * m->p;
+    void* xd = const_cast<void*>(Xnew);
+    float* od = out;
+    if (!device_ptrs) {
+        CWB_TRY(dev_alloc(&xd, xsz, m->stream));
+        CWB_TRY(dev_alloc((void**)&od, sizeof(float) * n_new, m->stream));
+        cudaError_t e = cudaMemcpyAsync(xd, Xnew, xsz, cudaMemcpyHostToDevice, m->stream);
+        if (e != cudaSuccess) { dev_free(xd); dev_free(od); return cuda_status(e, "cudaMemcpyAsync"); }
+    }
+    cwb_status st = launch_predict(m, xd, x_dtype, n_new, od);
+    if (st == CWB_OK && !device_ptrs) {
+        cudaError_t e = cudaMemcpyAsync(out, od, sizeof(float) * n_new, cudaMemcpyDeviceToHost, m->stream);
+        if (e != cudaSuccess) st = cuda_status(e, "cudaMemcpyAsync");
+    }
+    if (st == CWB_OK) {
+        cudaError_t e = cudaStreamSynchronize(m->stream);
+        if (e != cudaSuccess) st = cuda_status(e, "predict");
+    }
+    if (!device_ptrs) { dev_free(xd); dev_free(od); }
+    if (st == CWB_OK) st = read_device_error(m);
+    return st;
+}
+
+cwb_status cwb_get_coefficients(const cwb_model* mc, int32_t k, int32_t which, double* theta, int32_t cap,
+                                double* offset)
+{
+    set_error("");
+    cwb_model* m = const_cast<cwb_model*>(mc);
+    if (!m) { set_error("model is NULL"); return CWB_EINVAL; }
+    if (k < 0 || k >= m->K || (which != 0 && which != 1) || (cap > 0 && !theta)) {
+        set_error("bad learner index, which or buffer");
+        return CWB_EINVAL;
+    }
+    DeviceGuard guard(m->device);
+    CWB_TRY(launch_aggregate(m));
+    const int d = m->lrn[k].d;
+    const int cnt = std::min(d, std::max(cap, 0));
+    if (cnt > 0)
+        CWB_CUDA_TRY(cudaMemcpyAsync(theta, m->coef + ((int64_t)which * m->K + k) * m->d_max, sizeof(double) * cnt,
+                                     cudaMemcpyDeviceToHost, m->stream));
+    CWB_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    if (offset) *offset = m->offset;
+    return read_device_error(m);
+}
+
+cwb_status cwb_get_trace(const cwb_model* mc, int32_t* k_sel, int32_t* k_cor, int32_t cap, int32_t* switch_iter,
+                         int32_t* done)
+{
+    set_error("");
+    cwb_model* m = const_cast<cwb_model*>(mc);
+    if (!m) { set_error("model is NULL"); return CWB_EINVAL; }
+    DeviceGuard guard(m->device);
+    const int32_t cnt = std::min(std::max(cap, 0), m->done);
+    std::vector<int32_t> tk(2 * (size_t)std::max(cnt, 1));
+    if (cnt > 0)
+        CWB_CUDA_TRY(cudaMemcpyAsync(tk.data(), m->tr_k, sizeof(int32_t) * 2 * cnt, cudaMemcpyDeviceToHost, m->stream));
+    DevState st;
+    CWB_CUDA_TRY(cudaMemcpyAsync(&st, m->state, sizeof(st), cudaMemcpyDeviceToHost, m->stream));
+    CWB_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    for (int32_t t = 0; t < cnt; ++t) {
+        if (k_sel) k_sel[t] = tk[2 * t];
+        if (k_cor) k_cor[t] = tk[2 * t + 1];
+    }
+    if (switch_iter) *switch_iter = st.switch_iter;
+    if (done) *done = m->done;
+    return read_device_error(m);
+}
+
+cwb_status cwb_get_criteria(const cwb_model* mc, double* q_best, double* q_second, int32_t cap)
+{
+    set_error("");
+    cwb_model* m = const_cast<cwb_model*>(mc);
+    if (!m) { set_error("model is NULL"); return CWB_EINVAL; }
+    DeviceGuard guard(m->device);
+    const int32_t cnt = std::min(std::max(cap, 0), m->done);
+    std::vector<double> tq(2 * (size_t)std::max(cnt, 1));
+    if (cnt > 0)
+        CWB_CUDA_TRY(cudaMemcpyAsync(tq.data(), m->tr_q, sizeof(double) * 2 * cnt, cudaMemcpyDeviceToHost, m->stream));
+    CWB_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    for (int32_t t = 0; t < cnt; ++t) {
+        if (q_best) q_best[t] = tq[2 * t];
+        if (q_second) q_second[t] = tq[2 * t + 1];
+    }
+    return read_device_error(m);
+}
+
+cwb_status cwb_get_fitted(const cwb_model* mc, float* f, int32_t device_ptrs)
+{
+    set_error("");
+    cwb_model* m = const_cast<cwb_model*>(mc);
+    if (!m || !f) { set_error("NULL argument"); return CWB_EINVAL; }
+    DeviceGuard guard(m->device);
+    float* od = f;
+    if (!device_ptrs) CWB_TRY(dev_alloc((void**)&od, sizeof(float) * m->n, m->stream));
+    k_unpermute<<<grid_1d(m->n, m->device), 256, 0, m->stream>>>(m->f, m->perm, m->n, od);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && !device_ptrs)
+        e = cudaMemcpyAsync(f, od, sizeof(float) * m->n, cudaMemcpyDeviceToHost, m->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    if (!device_ptrs) dev_free(od);
+    if (e != cudaSuccess) return cuda_status(e, "cwb_get_fitted");
+    return read_device_error(m);
+}
+
+cwb_status cwb_get_learner_info(const cwb_model* m, int32_t k, cwb_learner_info* info)
+{
+    set_error("");
+    if (!m || !info || k < 0 || k >= m->K) { set_error("bad argument"); return CWB_EINVAL; }
+    DeviceGuard guard(m->device);
+    const HostLearner& L = m->lrn[k];
+    const HostBinning& hb = m->bins[L.binning];
+    double lam[2] = {0.0, 0.0};
+    CWB_CUDA_TRY(cudaMemcpyAsync(&lam[0], m->lambda + k, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+    CWB_CUDA_TRY(cudaMemcpyAsync(&lam[1], m->lambda + m->K + k, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+    CWB_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    info->d = L.d;
+    info->nstar = hb.nstar;
+    info->binning = L.binning;
+    info->reserved = 0;
+    info->xmin = hb.xmin;
+    info->xmax = hb.xmax;
+    info->lambda = lam[0];
+    info->lambda_full = m->hybrid ? lam[1] : lam[0];
+    return CWB_OK;
+}
+
+cwb_status cwb_get_learner_matrices(const cwb_model* m, int32_t k, int32_t phase, double* G, double* P)
+{
+    set_error("");
+    if (!m || k < 0 || k >= m->K || phase < 0 || phase > 1) { set_error("bad argument"); return CWB_EINVAL; }
+    DeviceGuard guard(m->device);
+    const int d = m->lrn[k].d, D = m->d_max;
+    const int ph = m->hybrid ? phase : 0;
+    std::vector<double> buf((size_t)D * D);
+    for (int which = 0; which < 2; ++which) {
+        double* dst = which == 0 ? G : P;
+        if (!dst) continue;
+        const double* src = (which == 0 ? m->G : m->P) + ((int64_t)ph * m->K + k) * D * D;
+        CWB_CUDA_TRY(cudaMemcpyAsync(buf.data(), src, sizeof(double) * D * D, cudaMemcpyDeviceToHost, m->stream));
+        CWB_CUDA_TRY(cudaStreamSynchronize(m->stream));
+        for (int i = 0; i < d; ++i)
+            for (int j = 0; j < d; ++j) dst[i * d + j] = buf[(size_t)i * D + j];
+    }
+    return CWB_OK;
+}
+
+cwb_status cwb_get_bin_index(const cwb_model* m, int32_t k, int32_t* ind)
+{
+    set_error("");
+    if (!m || !ind || k < 0 || k >= m->K) { set_error("bad argument"); return CWB_EINVAL; }
+    DeviceGuard guard(m->device);
+    const int b = m->lrn[k].binning;
+    const size_t nb = (size_t)m->ind_bytes * m->n;
+    std::vector<uint8_t> raw(nb);
+    std::vector<int32_t> perm;
+    CWB_CUDA_TRY(cudaMemcpyAsync(raw.data(), (const uint8_t*)m->ind + (size_t)m->ind_bytes * b * m->n_pad, nb,
+                                 cudaMemcpyDeviceToHost, m->stream));
+    if (m->perm) {
+        perm.resize(m->n);
+        CWB_CUDA_TRY(cudaMemcpyAsync(perm.data(), m->perm, sizeof(int32_t) * m->n, cudaMemcpyDeviceToHost, m->stream));
+    }
+    CWB_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    for (int64_t q = 0; q < m->n; ++q) {
+        int v = m->ind_bytes == 1 ? raw[q] : ((const uint16_t*)raw.data())[q];
+        ind[m->perm ? perm[q] : q] = v;
+    }
+    return CWB_OK;
+}
+
+cwb_status cwb_force_selection(cwb_model* m, const int32_t* k_forced, int32_t count)
+{
+    set_error("");
+    if (!m || (count > 0 && !k_forced) || count < 0) { set_error("bad argument"); return CWB_EINVAL; }
+    m->forced_host.assign(k_forced, k_forced + count);
+    return CWB_OK;
+}
+
+const char* cwb_last_error(void) { return g_last_error.c_str(); }
+
+void cwb_free(cwb_model* m)
+{
+    if (!m) return;
+    DeviceGuard guard(m->device);
+    free_model(m);
+}
+
+}  // extern "C"

@@ -1,0 +1,182 @@
+// cwb_internal.cuh -- shared declarations of the sm_103a componentwise boosting library.
+//
+// Device memory layout of one model (all owned by cwb_model, freed by cwb_free):
+//   ind      [B][n_pad]   uint8 or uint16 index vectors, one row per binning (learners on the
+//                         same feature with the same n_bins share a binning), rows train-first
+//   y, w     [n_pad]      FP32 targets and weights (w omitted when all ones)
+//   f, h, c  [n_pad]      FP32 primary model, momentum model, error-corrected residual
+//   rw       [2][n_pad]   FP32 scatter inputs w*r (channel 0) and w*c (channel 1), zero past
+//                         the active rows
+//   zb       [K][S][4]    FP32 non-zero basis values at the design points (S = max n*)
+//   zcol     [K][S]       int32 first non-zero column of each design point
+//   crange   [K][D][2]    int32 contiguous bin range contributing to each column
+//   G, P     [2][K][D][D] FP64 Gram matrix and cached inverse per phase
+//   part     histogram partials written by the scatter kernel
+//   trace    per iteration: mode, selected learners, FP64 fits, criteria
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "cwb.h"
+
+namespace cwb {
+
+constexpr int kMaxD = CWB_MAX_D;
+constexpr int kMaxNnz = 4;              // degree <= 3
+constexpr int kNumPhases = 2;
+constexpr int kRowAlign = 256;          // n_pad multiple (elements)
+
+// Error bits written by kernels into DevState::err.
+enum : uint32_t {
+    kErrTimeout = 1u,      // a bounded device wait ran out
+    kErrNumeric = 2u,      // factorisation failed / df not reachable
+    kErrIndex = 4u,        // an index fell outside its table (should never happen)
+    kErrNonFinite = 8u,    // non-finite criterion
+};
+
+enum : int32_t { kModeCWB = 0, kModeACWB = 1 };
+
+// Iteration state kept on the device; every kernel reads it, only last blocks write it.
+struct DevState {
+    int32_t m;            // iterations whose fits are computed
+    int32_t m_applied;    // iterations whose updates have been applied to f (and h)
+    int32_t mode;         // mode of iteration m+1
+    int32_t phase;        // cache used by CWB iterations (1 after an HCWB switch)
+    int32_t counter;      // HCWB patience counter
+    int32_t switch_iter;  // first CWB iteration of HCWB (1-based), 0 if none
+    int32_t pend_mode;    // mode of iteration m (the one whose update may be pending)
+    int32_t k_sel;        // learner of iteration m's primary fit
+    int32_t k_cor;        // learner of iteration m's correction fit (ACWB)
+    int32_t risk_valid;   // risk_prev holds a value
+    uint32_t err;
+    uint32_t ticket_rows;
+    uint32_t ticket_solve;
+    uint32_t pad0;
+    double risk_prev;
+};
+
+// Static description of the scatter decomposition.
+struct ScatterPlan {
+    int f_lane;       // binnings handled side by side in a warp (lane-private histogram columns)
+    int groups;       // ceil(B / f_lane)
+    int chunks;       // row chunks
+    int bin_ranges;   // bin sub-ranges (only when one feature's bins do not fit shared memory)
+    int nb_cta;       // bins held by one CTA
+    int nbins_pad;    // bins per partial histogram (>= max n*)
+    int ch_stride;    // shared-memory floats between the two channels' histograms
+    int threads;
+    size_t smem;      // dynamic shared memory bytes
+    size_t part_floats;
+};
+
+struct HostBinning {
+    int feature;
+    int nbins_spec;      // n_bins code requested
+    int nstar;
+    int exact;
+    double xmin, xmax;
+};
+
+struct HostLearner {
+    cwb_learner spec;
+    int binning;
+    int d;
+    int nnz;
+};
+
+}  // namespace cwb
+
+struct cwb_model {
+    int device = 0;
+    cudaStream_t stream = nullptr;        // work stream (user's or owned)
+    bool own_stream = false;
+    cudaStream_t capture_stream = nullptr;
+    cwb_config cfg{};
+    int64_t n = 0, n_tr = 0, n_pad = 0;
+    int32_t p = 0, K = 0, B = 0;
+    bool hybrid = false, accel = false, weighted = false;
+    int ind_bytes = 2;
+    int d_max = 0, nstar_max = 0;
+    double offset = 0.0;
+    std::vector<cwb::HostBinning> bins;
+    std::vector<cwb::HostLearner> lrn;
+    cwb::ScatterPlan plan{};
+
+    // device buffers
+    void* ind = nullptr;
+    float *y = nullptr, *w = nullptr, *f = nullptr, *h = nullptr, *c = nullptr, *rw = nullptr;
+    int32_t* perm = nullptr;              // new row -> original row (HCWB)
+    float* zb = nullptr;
+    double* zb64 = nullptr;
+    int32_t* zcol = nullptr;
+    int32_t* crange = nullptr;
+    double *G = nullptr, *P = nullptr, *lambda = nullptr;
+    int32_t *l_bin = nullptr, *l_d = nullptr, *l_nstar = nullptr, *l_type = nullptr;
+    double *l_xmin = nullptr, *l_xmax = nullptr;
+    int32_t *l_degree = nullptr, *l_nknots = nullptr, *l_feat = nullptr;
+    float* part = nullptr;
+    double* theta_it = nullptr;           // [2][K][D]
+    double* q_it = nullptr;               // [2][K]
+    float* v = nullptr;                   // [2][S]
+    cwb::DevState* state = nullptr;
+    double* risk_part = nullptr;
+    int risk_blocks = 0;
+    // trace
+    int32_t trace_cap = 0;
+    int32_t* tr_k = nullptr;              // [cap][2]
+    int32_t* tr_mode = nullptr;           // [cap]
+    double* tr_theta = nullptr;           // [cap][2][D]
+    double* tr_q = nullptr;               // [cap][2]
+    int32_t* forced = nullptr;            // [cap]
+    double* coef = nullptr;               // [2][K][D] aggregated
+    int32_t coef_valid_at = -1;
+    int32_t done = 0;                     // iterations queued so far
+    std::vector<int32_t> forced_host;     // pending host-side forced selections
+    // CUDA graph of a fixed block of iterations
+    cudaGraphExec_t graph_exec = nullptr;
+    int graph_iters = 0;
+    int graph_cap = 0;                    // trace capacity the graph was captured with
+};
+
+namespace cwb {
+
+// Error plumbing (thread-local message).
+void set_error(const std::string& msg);
+cwb_status cuda_status(cudaError_t e, const char* what);
+
+#define CWB_CUDA_TRY(expr)                                                 \
+    do {                                                                   \
+        cudaError_t _e = (expr);                                           \
+        if (_e != cudaSuccess) return ::cwb::cuda_status(_e, #expr);       \
+    } while (0)
+
+#define CWB_TRY(expr)                                                      \
+    do {                                                                   \
+        cwb_status _s = (expr);                                            \
+        if (_s != CWB_OK) return _s;                                       \
+    } while (0)
+
+cwb_status dev_alloc(void** p, size_t bytes, cudaStream_t s);
+void dev_free(void* p);
+
+// Setup (cwb_setup.cu)
+cwb_status setup_model(cwb_model* m, const void* X, int x_dtype, const void* y, const double* w,
+                       const uint8_t* val_mask, int device_ptrs);
+
+// Iterations (cwb_iter.cu)
+cwb_status plan_scatter(cwb_model* m);
+cwb_status ensure_trace(cwb_model* m, int32_t cap);
+cwb_status launch_iterations(cwb_model* m, int32_t iters);
+cwb_status launch_final_update(cwb_model* m);
+cwb_status launch_initial_rows(cwb_model* m);
+cwb_status launch_aggregate(cwb_model* m);
+cwb_status read_device_error(cwb_model* m);
+
+// Predict / fitted (cwb_api.cu)
+cwb_status launch_predict(const cwb_model* m, const void* Xnew, int x_dtype, int64_t n_new, float* out_dev);
+
+}  // namespace cwb

@@ -1,0 +1,1036 @@
+// cwb_setup.cu -- one-time model setup on the device (FP64 where the paper's
+// algebra needs it): binning (Sec. 3.1.1), reduced designs at the design
+// points (Sec. 2.2), weighted bin counts and Z^T W Z (binMatMat, Algorithm 2),
+// lambda from df via the Demmler-Reinsch orthogonalisation (App. A.2) and the
+// cached inverse (Z^T W Z + lambda K)^-1 (Sec. 2.4, Sec. 3.1.2).
+#include <math.h>
+
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "cwb_internal.cuh"
+
+namespace cwb {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+int num_sms(int device)
+{
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device);
+    return v > 0 ? v : 1;
+}
+
+// ---------------------------------------------------------------------------
+// Gathers and conversions (rows permuted train-first: new row q holds original row perm[q]).
+
+template <typename T>
+__global__ void k_gather_to_f32(const T* __restrict__ src, const int32_t* __restrict__ perm, int64_t n,
+                                int64_t n_pad, float* __restrict__ dst)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n_pad; q += (int64_t)gridDim.x * blockDim.x) {
+        float v = 0.0f;
+        if (q < n) v = (float)src[perm ? perm[q] : q];
+        dst[q] = v;
+    }
+}
+
+__global__ void k_gather_f64(const double* __restrict__ src, const int32_t* __restrict__ perm, int64_t n,
+                             double* __restrict__ dst)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+        dst[q] = src[perm ? perm[q] : q];
+}
+
+template <typename T>
+__global__ void k_check_binary(const T* __restrict__ y, int64_t n, uint32_t* bad)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        T v = y[i];
+        if (!(v == (T)0 || v == (T)1)) atomicOr(bad, 1u);
+    }
+}
+
+template <typename T>
+__global__ void k_check_weights(const T* __restrict__ w, int64_t n, uint32_t* bad)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        T v = w[i];
+        if (!(v > (T)0) || !isfinite((double)v)) atomicOr(bad, 1u);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Feature range: per binning min and max over all rows (FP64 compare).
+
+template <typename T>
+__global__ void k_minmax_partial(const T* __restrict__ X, const int32_t* __restrict__ feat, int64_t n,
+                                 double* __restrict__ pmin, double* __restrict__ pmax, uint32_t* nonfinite)
+{
+    const int b = blockIdx.y;
+    const T* x = X + (int64_t)feat[b] * n;
+    double lo = INFINITY, hi = -INFINITY;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double v = (double)x[i];
+        if (!isfinite(v)) { atomicOr(nonfinite, 1u); continue; }
+        lo = fmin(lo, v);
+        hi = fmax(hi, v);
+    }
+    __shared__ double slo[kThreads], shi[kThreads];
+    slo[threadIdx.x] = lo;
+    shi[threadIdx.x] = hi;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            slo[threadIdx.x] = fmin(slo[threadIdx.x], slo[threadIdx.x + s]);
+            shi[threadIdx.x] = fmax(shi[threadIdx.x], shi[threadIdx.x + s]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        pmin[(int64_t)b * gridDim.x + blockIdx.x] = slo[0];
+        pmax[(int64_t)b * gridDim.x + blockIdx.x] = shi[0];
+    }
+}
+
+__global__ void k_minmax_final(const double* __restrict__ pmin, const double* __restrict__ pmax, int nblk,
+                               double* __restrict__ xmin, double* __restrict__ xmax)
+{
+    const int b = blockIdx.x;
+    if (threadIdx.x == 0) {
+        double lo = INFINITY, hi = -INFINITY;
+        for (int i = 0; i < nblk; ++i) {
+            lo = fmin(lo, pmin[(int64_t)b * nblk + i]);
+            hi = fmax(hi, pmax[(int64_t)b * nblk + i]);
+        }
+        xmin[b] = lo;
+        xmax[b] = hi;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Index vectors (Sec. 3.1.1).
+
+// Equidistant design points z_l = xmin + l h: closest point, half-way values to the
+// lower one, i.e. l = ceil((x - xmin)/h - 1/2) clamped to [0, n*-1].  Correctly
+// rounded FP64 operations only, so the index is reproducible bit for bit.
+template <typename T, typename IndT>
+__global__ void k_bin_equidistant(const T* __restrict__ X, int64_t feat, const int32_t* __restrict__ perm,
+                                  int64_t n, int64_t n_pad, double xmin, double h, int nstar,
+                                  IndT* __restrict__ out)
+{
+    const T* x = X + feat * n;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n_pad; q += (int64_t)gridDim.x * blockDim.x) {
+        int l = 0;
+        if (q < n) {
+            double v = (double)x[perm ? perm[q] : q];
+            double t = __ddiv_rn(__dsub_rn(v, xmin), h);
+            double c = ceil(__dsub_rn(t, 0.5));
+            c = fmax(c, 0.0);
+            c = fmin(c, (double)(nstar - 1));
+            l = (int)c;
+        }
+        out[q] = (IndT)l;
+    }
+}
+
+// Exact binning: the design points are the sorted unique values.
+template <typename T>
+__global__ void k_load_sort_keys(const T* __restrict__ X, int64_t feat, int64_t n, int64_t npow2,
+                                 double* __restrict__ keys)
+{
+    const T* x = X + feat * n;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npow2; i += (int64_t)gridDim.x * blockDim.x)
+        keys[i] = i < n ? (double)x[i] : INFINITY;
+}
+
+// One compare-exchange pass of a bitonic sorting network (ascending).
+__global__ void k_bitonic_pass(double* __restrict__ a, int64_t npow2, int64_t j, int64_t k)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npow2; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t l = i ^ j;
+        if (l > i) {
+            double ai = a[i], al = a[l];
+            bool up = (i & k) == 0;
+            if ((up && ai > al) || (!up && ai < al)) {
+                a[i] = al;
+                a[l] = ai;
+            }
+        }
+    }
+}
+
+// Single-block scan of "first of its value" flags: writes the unique values in order.
+__global__ void k_unique_single_block(const double* __restrict__ s, int64_t n, double* __restrict__ z,
+                                      int32_t* __restrict__ count)
+{
+    __shared__ int32_t warp_sums[32];
+    __shared__ int32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int64_t base = 0; base < n; base += blockDim.x) {
+        int64_t i = base + threadIdx.x;
+        int flag = 0;
+        double v = 0.0;
+        if (i < n) {
+            v = s[i];
+            flag = (i == 0 || s[i - 1] != v) ? 1 : 0;
+        }
+        int incl = flag;
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) warp_sums[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            int ws = lane < nw ? warp_sums[lane] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                int t = __shfl_up_sync(0xffffffffu, ws, o);
+                if (lane >= o) ws += t;
+            }
+            if (lane < nw) warp_sums[lane] = ws;
+        }
+        __syncthreads();
+        int before = (wid > 0 ? warp_sums[wid - 1] : 0) + incl - flag;
+        if (flag) z[carry + before] = v;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry += before + flag;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *count = carry;
+}
+
+template <typename T, typename IndT>
+__global__ void k_bin_exact(const T* __restrict__ X, int64_t feat, const int32_t* __restrict__ perm, int64_t n,
+                            int64_t n_pad, const double* __restrict__ z, int nstar, IndT* __restrict__ out,
+                            uint32_t* err)
+{
+    const T* x = X + feat * n;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n_pad; q += (int64_t)gridDim.x * blockDim.x) {
+        int l = 0;
+        if (q < n) {
+            double v = (double)x[perm ? perm[q] : q];
+            int lo = 0, hi = nstar - 1;
+            while (lo < hi) {
+                int mid = (lo + hi) >> 1;
+                if (z[mid] < v) lo = mid + 1; else hi = mid;
+            }
+            if (z[lo] != v) atomicOr(err, kErrIndex);
+            l = lo;
+        }
+        out[q] = (IndT)l;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Weighted bin counts cnt[b][l] = sum over rows [r0, r1) with ind = l of w (binMatMat input).
+
+template <typename IndT>
+__global__ void k_counts(const IndT* __restrict__ ind, int64_t n_pad, int64_t r0, int64_t r1,
+                         const double* __restrict__ w, int stride, double* __restrict__ cnt)
+{
+    const int b = blockIdx.y;
+    const IndT* row = ind + (int64_t)b * n_pad;
+    double* c = cnt + (int64_t)b * stride;
+    for (int64_t q = r0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < r1; q += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&c[row[q]], w ? w[q] : 1.0);
+}
+
+// ---------------------------------------------------------------------------
+// B-spline basis on an equidistant extended knot vector (Sec. 2.2, P-splines).
+// Knots t_i = xmin + (i - q) delta, delta = (xmax - xmin)/(n_knots + 1).  The
+// q+1 non-zero functions on the knot interval holding x come from the
+// triangular form of the Cox-de Boor recursion.  Returns the first non-zero
+// column.  Degrees 1..3.
+
+__device__ __forceinline__ double knot(double xmin, double delta, int i_minus_q)
+{
+    return __dadd_rn(xmin, __dmul_rn((double)i_minus_q, delta));
+}
+
+__device__ int bspline_nonzero(double x, double xmin, double xmax, int q, int nk, double* N /* q+1 */)
+{
+    const double delta = __ddiv_rn(__dsub_rn(xmax, xmin), (double)(nk + 1));
+    const int last = nk + q;                      // last interval with a full set of functions: [t_last, t_last+1]
+    int mu = (int)floor(__ddiv_rn(__dsub_rn(x, xmin), delta)) + q;
+    if (mu < q) mu = q;
+    if (mu > last) mu = last;
+    // agree with the half-open rule t_mu <= x < t_mu+1 on the rounded knot values
+    while (mu > q && x < knot(xmin, delta, mu - q)) --mu;
+    while (mu < last && x >= knot(xmin, delta, mu + 1 - q)) ++mu;
+    double left[kMaxNnz], right[kMaxNnz];
+    N[0] = 1.0;
+    for (int j = 1; j <= q; ++j) {
+        left[j] = x - knot(xmin, delta, mu + 1 - j - q);
+        right[j] = knot(xmin, delta, mu + j - q) - x;
+        double saved = 0.0;
+        for (int r = 0; r < j; ++r) {
+            double tmp = N[r] / (right[r + 1] + left[j - r]);
+            N[r] = saved + right[r + 1] * tmp;
+            saved = left[j - r] * tmp;
+        }
+        N[j] = saved;
+    }
+    return mu - q;
+}
+
+struct BasisArgs {
+    int K, S;
+    const int32_t* l_bin;
+    const int32_t* l_type;
+    const int32_t* l_degree;
+    const int32_t* l_nknots;
+    const int32_t* l_nstar;
+    const double* b_xmin;
+    const double* b_xmax;
+    const double* b_h;           // equidistant step, 0 for exact binnings
+    const double* b_z;           // [B][S] exact design points
+    float* zb;                   // [K][S][4]
+    double* zb64;                // [K][S][4]
+    int32_t* zcol;               // [K][S]
+};
+
+__global__ void k_basis(BasisArgs a)
+{
+    const int k = blockIdx.x;
+    const int b = a.l_bin[k];
+    const int nst = a.l_nstar[k];
+    const double xmin = a.b_xmin[b], xmax = a.b_xmax[b], h = a.b_h[b];
+    for (int l = threadIdx.x; l < a.S; l += blockDim.x) {
+        double N[kMaxNnz] = {0.0, 0.0, 0.0, 0.0};
+        int col = 0;
+        if (l < nst) {
+            double z = (h > 0.0) ? __dadd_rn(xmin, __dmul_rn((double)l, h)) : a.b_z[(int64_t)b * a.S + l];
+            if (a.l_type[k] == CWB_BL_LINEAR) {
+                N[0] = 1.0;
+                N[1] = z;
+            } else {
+                col = bspline_nonzero(z, xmin, xmax, a.l_degree[k], a.l_nknots[k], N);
+            }
+        }
+        int64_t o = ((int64_t)k * a.S + l) * kMaxNnz;
+        for (int t = 0; t < kMaxNnz; ++t) {
+            a.zb64[o + t] = N[t];
+            a.zb[o + t] = (float)N[t];
+        }
+        a.zcol[(int64_t)k * a.S + l] = col;
+    }
+}
+
+// Contiguous bin range [lo, hi) whose rows have a non-zero in column j (first
+// non-zero columns are non-decreasing in the bin index).
+__global__ void k_col_ranges(int S, int D, const int32_t* __restrict__ l_nstar, const int32_t* __restrict__ l_d,
+                             const int32_t* __restrict__ l_nnz, const int32_t* __restrict__ zcol,
+                             int32_t* __restrict__ crange)
+{
+    const int k = blockIdx.x;
+    const int nst = l_nstar[k], d = l_d[k], nnz = l_nnz[k];
+    for (int j = threadIdx.x; j < D; j += blockDim.x) {
+        int lo = nst, hi = 0;
+        if (j < d) {
+            for (int l = 0; l < nst; ++l) {
+                int c0 = zcol[(int64_t)k * S + l];
+                if (c0 <= j && j < c0 + nnz) {
+                    if (l < lo) lo = l;
+                    hi = l + 1;
+                }
+            }
+        }
+        if (lo > hi) lo = hi = 0;
+        crange[((int64_t)k * D + j) * 2] = lo;
+        crange[((int64_t)k * D + j) * 2 + 1] = hi;
+    }
+}
+
+// G = Z^b^T diag(cnt) Z^b (binMatMat, Algorithm 2), FP64, bins visited in order.
+__global__ void k_gram(int S, int D, int K, const int32_t* __restrict__ l_bin, const int32_t* __restrict__ l_d,
+                       const int32_t* __restrict__ l_nnz, const double* __restrict__ zb64,
+                       const int32_t* __restrict__ zcol, const int32_t* __restrict__ crange,
+                       const double* __restrict__ cnt /* [phase][B][S] */, int B, double* __restrict__ G)
+{
+    const int k = blockIdx.x, ph = blockIdx.y;
+    const int d = l_d[k], nnz = l_nnz[k], b = l_bin[k];
+    const double* c = cnt + ((int64_t)ph * B + b) * S;
+    double* g = G + ((int64_t)ph * K + k) * D * D;
+    for (int e = threadIdx.x; e < D * D; e += blockDim.x) {
+        int i = e / D, j = e % D;
+        double s = 0.0;
+        if (i < d && j < d && (i - j < nnz && j - i < nnz)) {
+            int lo = max(crange[((int64_t)k * D + i) * 2], crange[((int64_t)k * D + j) * 2]);
+            int hi = min(crange[((int64_t)k * D + i) * 2 + 1], crange[((int64_t)k * D + j) * 2 + 1]);
+            for (int l = lo; l < hi; ++l) {
+                int c0 = zcol[(int64_t)k * S + l];
+                const double* z = zb64 + ((int64_t)k * S + l) * kMaxNnz;
+                s += c[l] * z[i - c0] * z[j - c0];
+            }
+        }
+        g[e] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Dense FP64 kernels for one learner (single thread, d <= 64, row-major in shared memory).
+
+__device__ bool dev_cholesky(const double* A, int d, int ld, double* L)
+{
+    for (int i = 0; i < d * ld; ++i) L[i] = 0.0;
+    for (int j = 0; j < d; ++j) {
+        double s = A[j * ld + j];
+        for (int k = 0; k < j; ++k) s -= L[j * ld + k] * L[j * ld + k];
+        if (!(s > 0.0)) return false;
+        double ljj = sqrt(s);
+        L[j * ld + j] = ljj;
+        for (int i = j + 1; i < d; ++i) {
+            double t = A[i * ld + j];
+            for (int k = 0; k < j; ++k) t -= L[i * ld + k] * L[j * ld + k];
+            L[i * ld + j] = t / ljj;
+        }
+    }
+    return true;
+}
+
+// Solve L L^T x = b in place.
+__device__ void dev_chol_solve(const double* L, int d, int ld, double* b)
+{
+    for (int i = 0; i < d; ++i) {
+        double t = b[i];
+        for (int k = 0; k < i; ++k) t -= L[i * ld + k] * b[k];
+        b[i] = t / L[i * ld + i];
+    }
+    for (int i = d - 1; i >= 0; --i) {
+        double t = b[i];
+        for (int k = i + 1; k < d; ++k) t -= L[k * ld + i] * b[k];
+        b[i] = t / L[i * ld + i];
+    }
+}
+
+// Eigenvalues of a symmetric matrix by cyclic Jacobi rotations (A is overwritten).
+__device__ void dev_jacobi_eigenvalues(double* A, int d, int ld, double* ev)
+{
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int i = 0; i < d; ++i)
+            for (int j = 0; j < d; ++j) {
+                double v = A[i * ld + j] * A[i * ld + j];
+                tot += v;
+                if (i != j) off += v;
+            }
+        if (off <= 1e-30 * tot || off == 0.0) break;
+        for (int p = 0; p < d - 1; ++p)
+            for (int q = p + 1; q < d; ++q) {
+                double apq = A[p * ld + q];
+                if (fabs(apq) <= 1e-300) continue;
+                double app = A[p * ld + p], aqq = A[q * ld + q];
+                double theta = (aqq - app) / (2.0 * apq);
+                double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < d; ++k) {        // A <- A J (columns p, q)
+                    double akp = A[k * ld + p], akq = A[k * ld + q];
+                    A[k * ld + p] = c * akp - s * akq;
+                    A[k * ld + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < d; ++k) {        // A <- J^T A (rows p, q)
+                    double apk = A[p * ld + k], aqk = A[q * ld + k];
+                    A[p * ld + k] = c * apk - s * aqk;
+                    A[q * ld + k] = s * apk + c * aqk;
+                }
+            }
+    }
+    for (int i = 0; i < d; ++i) ev[i] = A[i * ld + i];
+}
+
+__device__ double dev_df_from_eigen(const double* ev, int d, double lambda)
+{
+    double s = 0.0;
+    for (int i = 0; i < d; ++i) s += 1.0 / (1.0 + lambda * ev[i]);
+    return s;
+}
+
+// df1(lambda) = tr((G + lambda K)^-1 G) by its definition (used when G is singular).
+__device__ bool dev_df_direct(const double* G, const double* Kp, int d, int ld, double lambda, double* A, double* L,
+                              double* col, double* out)
+{
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) A[i * ld + j] = G[i * ld + j] + lambda * Kp[i * ld + j];
+    if (!dev_cholesky(A, d, ld, L)) return false;
+    double tr = 0.0;
+    for (int j = 0; j < d; ++j) {
+        for (int i = 0; i < d; ++i) col[i] = G[i * ld + j];
+        dev_chol_solve(L, d, ld, col);
+        tr += col[j];
+    }
+    *out = tr;
+    return true;
+}
+
+struct DroArgs {
+    int K, D;
+    const int32_t* l_type;
+    const int32_t* l_d;
+    const int32_t* l_diff;
+    const double* l_df;
+    const double* l_lambda;
+    const double* G;        // [2][K][D][D]
+    double* P;              // [2][K][D][D]
+    double* lambda;         // [2][K]
+    int32_t* status;        // [2][K]: 0 ok, 1 singular, 2 df unreachable
+    int phases;
+};
+
+// Per learner and phase: penalty K = D^T D, lambda with df1(lambda) = df via the
+// Demmler-Reinsch orthogonalisation (G = L L^T, eigenvalues s_i of L^-1 K L^-T,
+// df1 = sum 1/(1 + lambda s_i)), then P = (G + lambda K)^-1.
+__global__ void k_dro(DroArgs a)
+{
+    const int k = blockIdx.x, ph = blockIdx.y;
+    if (ph >= a.phases || threadIdx.x != 0) return;
+    const int d = a.l_d[k], ld = d;
+    extern __shared__ double sm[];
+    double* G = sm;
+    double* Kp = G + d * d;
+    double* L = Kp + d * d;
+    double* M = L + d * d;
+    double* A = M + d * d;
+    double* col = A + d * d;
+    double* ev = col + d;
+    const double* Gs = a.G + ((int64_t)ph * a.K + k) * a.D * a.D;
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) G[i * ld + j] = Gs[i * a.D + j];
+    // penalty: difference matrix of the requested order, K = D^T D
+    for (int i = 0; i < d * d; ++i) Kp[i] = 0.0;
+    const bool pspline = a.l_type[k] == CWB_BL_PSPLINE;
+    int status = 0;
+    double lam = 0.0;
+    if (pspline) {
+        const int ord = a.l_diff[k];
+        for (int i = 0; i < d * d; ++i) M[i] = 0.0;
+        for (int i = 0; i < d; ++i) M[i * ld + i] = 1.0;
+        int rows = d;
+        for (int o = 0; o < ord; ++o) {
+            for (int i = 0; i < rows - 1; ++i)
+                for (int j = 0; j < d; ++j) M[i * ld + j] = M[(i + 1) * ld + j] - M[i * ld + j];
+            rows -= 1;
+        }
+        for (int p = 0; p < d; ++p)
+            for (int q = 0; q < d; ++q) {
+                double s = 0.0;
+                for (int i = 0; i < rows; ++i) s += M[i * ld + p] * M[i * ld + q];
+                Kp[p * ld + q] = s;
+            }
+        const double df = a.l_df[k];
+        if (!(df > 0.0)) {
+            lam = a.l_lambda[k];
+        } else if (df >= (double)d) {
+            lam = 0.0;
+        } else {
+            double trg = 0.0, trk = 0.0;
+            for (int i = 0; i < d; ++i) { trg += G[i * ld + i]; trk += Kp[i * ld + i]; }
+            double c = log10(trg / trk);
+            double lo = c - 20.0, hi = c + 20.0;
+            if (dev_cholesky(G, d, ld, L)) {
+                // M = L^-1 K L^-T: solve L X = K column by column, then L M = X^T
+                for (int j = 0; j < d; ++j) {
+                    for (int i = 0; i < d; ++i) {
+                        double t = Kp[i * ld + j];
+                        for (int q = 0; q < i; ++q) t -= L[i * ld + q] * A[q * ld + j];
+                        A[i * ld + j] = t / L[i * ld + i];
+                    }
+                }
+                for (int j = 0; j < d; ++j) {
+                    for (int i = 0; i < d; ++i) {
+                        double t = A[j * ld + i];          // (X^T)[i][j] = X[j][i]
+                        for (int q = 0; q < i; ++q) t -= L[i * ld + q] * M[q * ld + j];
+                        M[i * ld + j] = t / L[i * ld + i];
+                    }
+                }
+                for (int i = 0; i < d; ++i)                 // symmetrise rounding
+                    for (int j = i + 1; j < d; ++j) {
+                        double s = 0.5 * (M[i * ld + j] + M[j * ld + i]);
+                        M[i * ld + j] = s;
+                        M[j * ld + i] = s;
+                    }
+                dev_jacobi_eigenvalues(M, d, ld, ev);
+                for (int i = 0; i < d; ++i) ev[i] = fmax(ev[i], 0.0);
+                if (dev_df_from_eigen(ev, d, pow(10.0, hi)) > df) {
+                    status = 2;
+                } else if (dev_df_from_eigen(ev, d, pow(10.0, lo)) < df) {
+                    lam = pow(10.0, lo);
+                } else {
+                    for (int it = 0; it < 400 && hi - lo >= 1e-15; ++it) {
+                        double mid = 0.5 * (lo + hi);
+                        if (dev_df_from_eigen(ev, d, pow(10.0, mid)) > df) lo = mid; else hi = mid;
+                    }
+                    lam = pow(10.0, 0.5 * (lo + hi));
+                }
+            } else {
+                // singular G: root search on the definition, fresh factorisation per step
+                double v;
+                if (!dev_df_direct(G, Kp, d, ld, pow(10.0, hi), A, L, col, &v) || v > df) {
+                    status = 2;
+                } else if (dev_df_direct(G, Kp, d, ld, pow(10.0, lo), A, L, col, &v) && v < df) {
+                    lam = pow(10.0, lo);
+                } else {
+                    for (int it = 0; it < 400 && hi - lo >= 1e-15; ++it) {
+                        double mid = 0.5 * (lo + hi);
+                        if (!dev_df_direct(G, Kp, d, ld, pow(10.0, mid), A, L, col, &v)) { lo = mid; continue; }
+                        if (v > df) lo = mid; else hi = mid;
+                    }
+                    lam = pow(10.0, 0.5 * (lo + hi));
+                }
+            }
+        }
+    }
+    double* Pout = a.P + ((int64_t)ph * a.K + k) * a.D * a.D;
+    for (int i = 0; i < a.D * a.D; ++i) Pout[i] = 0.0;
+    if (status == 0) {
+        for (int i = 0; i < d; ++i)
+            for (int j = 0; j < d; ++j) A[i * ld + j] = G[i * ld + j] + lam * Kp[i * ld + j];
+        if (!dev_cholesky(A, d, ld, L)) {
+            status = 1;
+        } else {
+            for (int j = 0; j < d; ++j) {
+                for (int i = 0; i < d; ++i) col[i] = (i == j) ? 1.0 : 0.0;
+                dev_chol_solve(L, d, ld, col);
+                for (int i = 0; i < d; ++i) Pout[i * a.D + j] = col[i];
+            }
+        }
+    }
+    a.lambda[(int64_t)ph * a.K + k] = lam;
+    a.status[(int64_t)ph * a.K + k] = status;
+}
+
+// ---------------------------------------------------------------------------
+// Offset: loss-optimal constant over the fitting rows (L2: weighted mean,
+// binomial: logit of the weighted mean).
+
+__global__ void k_offset(const float* __restrict__ y, const double* __restrict__ w, int64_t n_fit, int loss,
+                         double* __restrict__ out /* [0] offset, [1] mean */)
+{
+    __shared__ double s1[1024], s2[1024];
+    double a = 0.0, b = 0.0;
+    for (int64_t i = threadIdx.x; i < n_fit; i += blockDim.x) {
+        double wi = w ? w[i] : 1.0;
+        a += wi * (double)y[i];
+        b += wi;
+    }
+    s1[threadIdx.x] = a;
+    s2[threadIdx.x] = b;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            s1[threadIdx.x] += s1[threadIdx.x + s];
+            s2[threadIdx.x] += s2[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double mean = s1[0] / s2[0];
+        out[1] = mean;
+        out[0] = (loss == CWB_LOSS_L2) ? mean : log(mean / (1.0 - mean));
+    }
+}
+
+__global__ void k_init_rows(int64_t n_pad, float offset, float* f, float* h, float* c, float* rw)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_pad; i += (int64_t)gridDim.x * blockDim.x) {
+        f[i] = offset;
+        if (h) h[i] = offset;
+        if (c) c[i] = 0.0f;
+        rw[i] = 0.0f;
+        rw[n_pad + i] = 0.0f;
+    }
+}
+
+// ---------------------------------------------------------------------------
+
+struct TempBuf {
+    std::vector<void*> ptrs;
+    ~TempBuf()
+    {
+        for (void* p : ptrs) dev_free(p);
+    }
+    template <typename T>
+    cwb_status get(T** out, size_t count, cudaStream_t s)
+    {
+        void* p = nullptr;
+        cwb_status st = dev_alloc(&p, sizeof(T) * (count ? count : 1), s);
+        if (st != CWB_OK) return st;
+        ptrs.push_back(p);
+        *out = static_cast<T*>(p);
+        return CWB_OK;
+    }
+};
+
+int64_t isqrt64(int64_t n)
+{
+    int64_t s = (int64_t)sqrt((double)n);
+    while (s > 0 && s * s > n) --s;
+    while ((s + 1) * (s + 1) <= n) ++s;
+    return s;
+}
+
+int grid_for(int64_t work, int device)
+{
+    int64_t g = ceil_div(work, kThreads);
+    int64_t cap = (int64_t)num_sms(device) * 8;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+}  // namespace
+
+cwb_status setup_model(cwb_model* m, const void* X_in, int x_dtype, const void* y_in, const double* w_in,
+                       const uint8_t* val_mask, int device_ptrs)
+{
+    cudaStream_t s = m->stream;
+    const int64_t n = m->n;
+    const int32_t p = m->p;
+    const size_t xsz = x_dtype == CWB_F64 ? 8 : 4;
+    TempBuf tmp;
+
+    // --- row order: training rows first (HCWB), original order otherwise
+    std::vector<int32_t> perm_h;
+    if (m->hybrid) {
+        std::vector<uint8_t> mask(n);
+        if (device_ptrs) {
+            CWB_CUDA_TRY(cudaMemcpyAsync(mask.data(), val_mask, (size_t)n, cudaMemcpyDeviceToHost, s));
+            CWB_CUDA_TRY(cudaStreamSynchronize(s));
+        } else {
+            std::memcpy(mask.data(), val_mask, (size_t)n);
+        }
+        perm_h.reserve(n);
+        for (int64_t i = 0; i < n; ++i)
+            if (!mask[i]) perm_h.push_back((int32_t)i);
+        m->n_tr = (int64_t)perm_h.size();
+        for (int64_t i = 0; i < n; ++i)
+            if (mask[i]) perm_h.push_back((int32_t)i);
+        if (m->n_tr < 2 || m->n_tr == n) {
+            set_error("HCWB needs at least two training rows and one validation row");
+            return CWB_EINVAL;
+        }
+        CWB_TRY(dev_alloc((void**)&m->perm, sizeof(int32_t) * n, s));
+        CWB_CUDA_TRY(cudaMemcpyAsync(m->perm, perm_h.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+    } else {
+        m->n_tr = n;
+    }
+    m->n_pad = ceil_div(n, kRowAlign) * kRowAlign;
+    const int64_t n_pad = m->n_pad;
+
+    // --- inputs on the device (caller's buffers are only read during this call)
+    const void* Xd = X_in;
+    const void* yd = y_in;
+    const double* wd = w_in;
+    if (!device_ptrs) {
+        void* xb = nullptr;
+        CWB_TRY(tmp.get((char**)&xb, xsz * (size_t)n * p, s));
+        CWB_CUDA_TRY(cudaMemcpyAsync(xb, X_in, xsz * (size_t)n * p, cudaMemcpyHostToDevice, s));
+        Xd = xb;
+        void* yb = nullptr;
+        CWB_TRY(tmp.get((char**)&yb, xsz * (size_t)n, s));
+        CWB_CUDA_TRY(cudaMemcpyAsync(yb, y_in, xsz * (size_t)n, cudaMemcpyHostToDevice, s));
+        yd = yb;
+        if (w_in) {
+            double* wb = nullptr;
+            CWB_TRY(tmp.get(&wb, (size_t)n, s));
+            CWB_CUDA_TRY(cudaMemcpyAsync(wb, w_in, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+            wd = wb;
+        }
+    }
+    const int g_rows = grid_for(n_pad, m->device);
+
+    // --- validity checks on the data
+    uint32_t* flags = nullptr;
+    CWB_TRY(tmp.get(&flags, 4, s));
+    CWB_CUDA_TRY(cudaMemsetAsync(flags, 0, 16, s));
+    if (m->cfg.loss == CWB_LOSS_BINOMIAL) {
+        if (x_dtype == CWB_F64) k_check_binary<<<g_rows, kThreads, 0, s>>>((const double*)yd, n, flags);
+        else k_check_binary<<<g_rows, kThreads, 0, s>>>((const float*)yd, n, flags);
+    }
+    if (wd) k_check_weights<<<g_rows, kThreads, 0, s>>>(wd, n, flags + 1);
+
+    // --- y, w in the fitting order
+    CWB_TRY(dev_alloc((void**)&m->y, sizeof(float) * n_pad, s));
+    if (x_dtype == CWB_F64) k_gather_to_f32<<<g_rows, kThreads, 0, s>>>((const double*)yd, m->perm, n, n_pad, m->y);
+    else k_gather_to_f32<<<g_rows, kThreads, 0, s>>>((const float*)yd, m->perm, n, n_pad, m->y);
+    double* w64 = nullptr;
+    if (wd) {
+        m->weighted = true;
+        CWB_TRY(tmp.get(&w64, (size_t)n, s));
+        k_gather_f64<<<g_rows, kThreads, 0, s>>>(wd, m->perm, n, w64);
+        CWB_TRY(dev_alloc((void**)&m->w, sizeof(float) * n_pad, s));
+        k_gather_to_f32<<<g_rows, kThreads, 0, s>>>(w64, nullptr, n, n_pad, m->w);
+    }
+    CWB_CUDA_TRY(cudaGetLastError());
+
+    // --- binnings: one per distinct (feature, n_bins) pair
+    const int B = (int)m->bins.size();
+    std::vector<int32_t> feat_h(B);
+    for (int b = 0; b < B; ++b) feat_h[b] = m->bins[b].feature;
+    int32_t* feat_d = nullptr;
+    CWB_TRY(tmp.get(&feat_d, (size_t)B, s));
+    CWB_CUDA_TRY(cudaMemcpyAsync(feat_d, feat_h.data(), sizeof(int32_t) * B, cudaMemcpyHostToDevice, s));
+    const int nblk = std::min<int>(64, (int)ceil_div(n, kThreads));
+    double *pmin = nullptr, *pmax = nullptr, *xmin_d = nullptr, *xmax_d = nullptr;
+    CWB_TRY(tmp.get(&pmin, (size_t)B * nblk, s));
+    CWB_TRY(tmp.get(&pmax, (size_t)B * nblk, s));
+    CWB_TRY(tmp.get(&xmin_d, (size_t)B, s));
+    CWB_TRY(tmp.get(&xmax_d, (size_t)B, s));
+    {
+        dim3 grid(nblk, B);
+        if (x_dtype == CWB_F64) k_minmax_partial<<<grid, kThreads, 0, s>>>((const double*)Xd, feat_d, n, pmin, pmax, flags + 2);
+        else k_minmax_partial<<<grid, kThreads, 0, s>>>((const float*)Xd, feat_d, n, pmin, pmax, flags + 2);
+        k_minmax_final<<<B, 32, 0, s>>>(pmin, pmax, nblk, xmin_d, xmax_d);
+    }
+    std::vector<double> xmin_h(B), xmax_h(B);
+    uint32_t flags_h[4] = {0, 0, 0, 0};
+    CWB_CUDA_TRY(cudaMemcpyAsync(xmin_h.data(), xmin_d, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
+    CWB_CUDA_TRY(cudaMemcpyAsync(xmax_h.data(), xmax_d, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
+    CWB_CUDA_TRY(cudaMemcpyAsync(flags_h, flags, sizeof(flags_h), cudaMemcpyDeviceToHost, s));
+    CWB_CUDA_TRY(cudaStreamSynchronize(s));
+    if (flags_h[0]) { set_error("binomial loss needs targets in {0, 1}"); return CWB_EINVAL; }
+    if (flags_h[1]) { set_error("observation weights must be finite and > 0"); return CWB_EINVAL; }
+    if (flags_h[2]) { set_error("features must be finite"); return CWB_EINVAL; }
+    for (int b = 0; b < B; ++b) {
+        m->bins[b].xmin = xmin_h[b];
+        m->bins[b].xmax = xmax_h[b];
+        if (!(xmax_h[b] > xmin_h[b])) {
+            set_error("feature " + std::to_string(m->bins[b].feature) + " is constant (max == min)");
+            return CWB_EINVAL;
+        }
+    }
+
+    // --- exact binnings: sorted unique values on the device
+    int64_t npow2 = 1;
+    while (npow2 < n) npow2 <<= 1;
+    int S = 2;
+    bool any_exact = false;
+    for (int b = 0; b < B; ++b) {
+        HostBinning& hb = m->bins[b];
+        if (hb.nbins_spec == CWB_BINS_EXACT) {
+            hb.exact = 1;
+            any_exact = true;
+        } else {
+            hb.exact = 0;
+            hb.nstar = hb.nbins_spec == CWB_BINS_SQRT ? (int)std::min<int64_t>(isqrt64(n), 1 << 30) : hb.nbins_spec;
+        }
+    }
+    double* keys = nullptr;
+    std::vector<double*> zvals(B, nullptr);
+    if (any_exact) {
+        CWB_TRY(tmp.get(&keys, (size_t)npow2, s));
+        int32_t* cnt_d = nullptr;
+        CWB_TRY(tmp.get(&cnt_d, (size_t)B, s));
+        const int gp = grid_for(npow2, m->device);
+        for (int b = 0; b < B; ++b) {
+            if (!m->bins[b].exact) continue;
+            CWB_TRY(tmp.get(&zvals[b], (size_t)n, s));
+            if (x_dtype == CWB_F64) k_load_sort_keys<<<gp, kThreads, 0, s>>>((const double*)Xd, m->bins[b].feature, n, npow2, keys);
+            else k_load_sort_keys<<<gp, kThreads, 0, s>>>((const float*)Xd, m->bins[b].feature, n, npow2, keys);
+            for (int64_t k2 = 2; k2 <= npow2; k2 <<= 1)
+                for (int64_t j = k2 >> 1; j > 0; j >>= 1) k_bitonic_pass<<<gp, kThreads, 0, s>>>(keys, npow2, j, k2);
+            k_unique_single_block<<<1, 1024, 0, s>>>(keys, n, zvals[b], cnt_d + b);
+        }
+        std::vector<int32_t> cnt_h(B, 0);
+        CWB_CUDA_TRY(cudaMemcpyAsync(cnt_h.data(), cnt_d, sizeof(int32_t) * B, cudaMemcpyDeviceToHost, s));
+        CWB_CUDA_TRY(cudaStreamSynchronize(s));
+        for (int b = 0; b < B; ++b)
+            if (m->bins[b].exact) m->bins[b].nstar = cnt_h[b];
+    }
+    for (int b = 0; b < B; ++b) {
+        int ns = m->bins[b].nstar;
+        if (ns < 2 || ns > CWB_MAX_BINS) {
+            set_error("feature " + std::to_string(m->bins[b].feature) + ": number of design points " +
+                      std::to_string(ns) + " outside [2, 65535]");
+            return CWB_EINVAL;
+        }
+        S = std::max(S, ns);
+    }
+    m->nstar_max = S;
+    m->ind_bytes = S <= 256 ? 1 : 2;
+
+    // --- index vectors [B][n_pad]
+    CWB_TRY(dev_alloc(&m->ind, (size_t)m->ind_bytes * B * n_pad, s));
+    std::vector<double> h_h(B, 0.0);
+    for (int b = 0; b < B; ++b) {
+        const HostBinning& hb = m->bins[b];
+        if (hb.exact) {
+            uint32_t* errp = flags + 3;
+            if (m->ind_bytes == 1) {
+                uint8_t* out = (uint8_t*)m->ind + (int64_t)b * n_pad;
+                if (x_dtype == CWB_F64) k_bin_exact<<<g_rows, kThreads, 0, s>>>((const double*)Xd, hb.feature, m->perm, n, n_pad, zvals[b], hb.nstar, out, errp);
+                else k_bin_exact<<<g_rows, kThreads, 0, s>>>((const float*)Xd, hb.feature, m->perm, n, n_pad, zvals[b], hb.nstar, out, errp);
+            } else {
+                uint16_t* out = (uint16_t*)m->ind + (int64_t)b * n_pad;
+                if (x_dtype == CWB_F64) k_bin_exact<<<g_rows, kThreads, 0, s>>>((const double*)Xd, hb.feature, m->perm, n, n_pad, zvals[b], hb.nstar, out, errp);
+                else k_bin_exact<<<g_rows, kThreads, 0, s>>>((const float*)Xd, hb.feature, m->perm, n, n_pad, zvals[b], hb.nstar, out, errp);
+            }
+        } else {
+            double h = (hb.xmax - hb.xmin) / (double)(hb.nstar - 1);
+            h_h[b] = h;
+            if (m->ind_bytes == 1) {
+                uint8_t* out = (uint8_t*)m->ind + (int64_t)b * n_pad;
+                if (x_dtype == CWB_F64) k_bin_equidistant<<<g_rows, kThreads, 0, s>>>((const double*)Xd, hb.feature, m->perm, n, n_pad, hb.xmin, h, hb.nstar, out);
+                else k_bin_equidistant<<<g_rows, kThreads, 0, s>>>((const float*)Xd, hb.feature, m->perm, n, n_pad, hb.xmin, h, hb.nstar, out);
+            } else {
+                uint16_t* out = (uint16_t*)m->ind + (int64_t)b * n_pad;
+                if (x_dtype == CWB_F64) k_bin_equidistant<<<g_rows, kThreads, 0, s>>>((const double*)Xd, hb.feature, m->perm, n, n_pad, hb.xmin, h, hb.nstar, out);
+                else k_bin_equidistant<<<g_rows, kThreads, 0, s>>>((const float*)Xd, hb.feature, m->perm, n, n_pad, hb.xmin, h, hb.nstar, out);
+            }
+        }
+    }
+    CWB_CUDA_TRY(cudaGetLastError());
+
+    // --- per-learner tables
+    const int K = m->K;
+    int D = 0;
+    for (const HostLearner& L : m->lrn) D = std::max(D, L.d);
+    m->d_max = D;
+    std::vector<int32_t> lb(K), lt(K), ldeg(K), lnk(K), lns(K), ld(K), lnnz(K), ldiff(K);
+    std::vector<double> ldf(K), llam(K), lxmin(K), lxmax(K);
+    for (int k = 0; k < K; ++k) {
+        const HostLearner& L = m->lrn[k];
+        lb[k] = L.binning;
+        lt[k] = L.spec.type;
+        ldeg[k] = L.spec.degree;
+        lnk[k] = L.spec.n_knots;
+        lns[k] = m->bins[L.binning].nstar;
+        ld[k] = L.d;
+        lnnz[k] = L.nnz;
+        ldiff[k] = L.spec.diff_order;
+        ldf[k] = L.spec.df;
+        llam[k] = L.spec.lambda;
+        lxmin[k] = m->bins[L.binning].xmin;
+        lxmax[k] = m->bins[L.binning].xmax;
+    }
+    auto upload_i = [&](int32_t** dst, const std::vector<int32_t>& v, bool keep) -> cwb_status {
+        if (keep) CWB_TRY(dev_alloc((void**)dst, sizeof(int32_t) * v.size(), s));
+        else CWB_TRY(tmp.get(dst, v.size(), s));
+        CWB_CUDA_TRY(cudaMemcpyAsync(*dst, v.data(), sizeof(int32_t) * v.size(), cudaMemcpyHostToDevice, s));
+        return CWB_OK;
+    };
+    auto upload_d = [&](double** dst, const std::vector<double>& v, bool keep) -> cwb_status {
+        if (keep) CWB_TRY(dev_alloc((void**)dst, sizeof(double) * v.size(), s));
+        else CWB_TRY(tmp.get(dst, v.size(), s));
+        CWB_CUDA_TRY(cudaMemcpyAsync(*dst, v.data(), sizeof(double) * v.size(), cudaMemcpyHostToDevice, s));
+        return CWB_OK;
+    };
+    int32_t *nnz_d = nullptr, *ldiff_d = nullptr;
+    double *ldf_d = nullptr, *llam_d = nullptr, *bxmin_d = nullptr, *bxmax_d = nullptr, *bh_d = nullptr;
+    CWB_TRY(upload_i(&m->l_bin, lb, true));
+    CWB_TRY(upload_i(&m->l_type, lt, true));
+    CWB_TRY(upload_i(&m->l_degree, ldeg, true));
+    CWB_TRY(upload_i(&m->l_nknots, lnk, true));
+    CWB_TRY(upload_i(&m->l_nstar, lns, true));
+    CWB_TRY(upload_i(&m->l_d, ld, true));
+    CWB_TRY(upload_d(&m->l_xmin, lxmin, true));
+    CWB_TRY(upload_d(&m->l_xmax, lxmax, true));
+    CWB_TRY(upload_i(&nnz_d, lnnz, false));
+    CWB_TRY(upload_i(&ldiff_d, ldiff, false));
+    CWB_TRY(upload_d(&ldf_d, ldf, false));
+    CWB_TRY(upload_d(&llam_d, llam, false));
+    CWB_TRY(upload_d(&bxmin_d, xmin_h, false));
+    CWB_TRY(upload_d(&bxmax_d, xmax_h, false));
+    CWB_TRY(upload_d(&bh_d, h_h, false));
+    double* bz_d = nullptr;
+    if (any_exact) {
+        CWB_TRY(tmp.get(&bz_d, (size_t)B * S, s));
+        for (int b = 0; b < B; ++b)
+            if (m->bins[b].exact)
+                CWB_CUDA_TRY(cudaMemcpyAsync(bz_d + (int64_t)b * S, zvals[b], sizeof(double) * m->bins[b].nstar,
+                                             cudaMemcpyDeviceToDevice, s));
+    }
+    CWB_TRY(dev_alloc((void**)&m->zb, sizeof(float) * (size_t)K * S * kMaxNnz, s));
+    CWB_TRY(dev_alloc((void**)&m->zb64, sizeof(double) * (size_t)K * S * kMaxNnz, s));
+    CWB_TRY(dev_alloc((void**)&m->zcol, sizeof(int32_t) * (size_t)K * S, s));
+    CWB_TRY(dev_alloc((void**)&m->crange, sizeof(int32_t) * (size_t)K * D * 2, s));
+    {
+        BasisArgs a{K, S, m->l_bin, m->l_type, m->l_degree, m->l_nknots, m->l_nstar, bxmin_d, bxmax_d, bh_d, bz_d,
+                    m->zb, m->zb64, m->zcol};
+        k_basis<<<K, kThreads, 0, s>>>(a);
+        k_col_ranges<<<K, 64, 0, s>>>(S, D, m->l_nstar, m->l_d, nnz_d, m->zcol, m->crange);
+    }
+
+    // --- weighted bin counts per phase: phase 0 = fitting rows of the first phase, phase 1 = all rows
+    const int phases = m->hybrid ? 2 : 1;
+    double* cnt = nullptr;
+    CWB_TRY(tmp.get(&cnt, (size_t)2 * B * S, s));
+    CWB_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(double) * (size_t)2 * B * S, s));
+    for (int ph = 0; ph < phases; ++ph) {
+        int64_t r1 = (ph == 0) ? m->n_tr : n;
+        dim3 grid(std::min<int>(grid_for(r1, m->device), 64), B);
+        if (m->ind_bytes == 1)
+            k_counts<<<grid, kThreads, 0, s>>>((const uint8_t*)m->ind, n_pad, 0, r1, w64, S, cnt + (int64_t)ph * B * S);
+        else
+            k_counts<<<grid, kThreads, 0, s>>>((const uint16_t*)m->ind, n_pad, 0, r1, w64, S, cnt + (int64_t)ph * B * S);
+    }
+    if (phases == 1)
+        CWB_CUDA_TRY(cudaMemcpyAsync(cnt + (int64_t)B * S, cnt, sizeof(double) * (size_t)B * S, cudaMemcpyDeviceToDevice, s));
+
+    // --- G, lambda, P per learner and phase
+    const size_t dd = (size_t)D * D;
+    CWB_TRY(dev_alloc((void**)&m->G, sizeof(double) * 2 * K * dd, s));
+    CWB_TRY(dev_alloc((void**)&m->P, sizeof(double) * 2 * K * dd, s));
+    CWB_TRY(dev_alloc((void**)&m->lambda, sizeof(double) * 2 * K, s));
+    int32_t* lstat = nullptr;
+    CWB_TRY(tmp.get(&lstat, (size_t)2 * K, s));
+    k_gram<<<dim3(K, 2), kThreads, 0, s>>>(S, D, K, m->l_bin, m->l_d, nnz_d, m->zb64, m->zcol, m->crange, cnt, B, m->G);
+    {
+        DroArgs a{K, D, m->l_type, m->l_d, ldiff_d, ldf_d, llam_d, m->G, m->P, m->lambda, lstat, 2};
+        size_t smem = sizeof(double) * (5 * dd + 2 * D);
+        CWB_CUDA_TRY(cudaFuncSetAttribute(k_dro, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_dro<<<dim3(K, 2), 32, smem, s>>>(a);
+    }
+    CWB_CUDA_TRY(cudaGetLastError());
+    std::vector<int32_t> lstat_h(2 * K);
+    CWB_CUDA_TRY(cudaMemcpyAsync(lstat_h.data(), lstat, sizeof(int32_t) * 2 * K, cudaMemcpyDeviceToHost, s));
+    CWB_CUDA_TRY(cudaMemcpyAsync(flags_h, flags, sizeof(flags_h), cudaMemcpyDeviceToHost, s));
+    CWB_CUDA_TRY(cudaStreamSynchronize(s));
+    if (flags_h[3]) { set_error("internal: exact binning lookup failed"); return CWB_ENUMERIC; }
+    for (int ph = 0; ph < phases; ++ph)
+        for (int k = 0; k < K; ++k) {
+            int st = lstat_h[(size_t)ph * K + k];
+            if (st == 1) {
+                set_error("learner " + std::to_string(k) + ": Z^T W Z + lambda K is not positive definite");
+                return CWB_ENUMERIC;
+            }
+            if (st == 2) {
+                set_error("learner " + std::to_string(k) + ": df is not reachable (at or below the penalty null space)");
+                return CWB_ENUMERIC;
+            }
+        }
+
+    // --- offset and initial models
+    double* off_d = nullptr;
+    CWB_TRY(tmp.get(&off_d, 2, s));
+    k_offset<<<1, 1024, 0, s>>>(m->y, w64, m->n_tr, m->cfg.loss, off_d);
+    double off_h[2] = {0.0, 0.0};
+    CWB_CUDA_TRY(cudaMemcpyAsync(off_h, off_d, sizeof(off_h), cudaMemcpyDeviceToHost, s));
+    CWB_CUDA_TRY(cudaStreamSynchronize(s));
+    if (m->cfg.loss == CWB_LOSS_BINOMIAL && !(off_h[1] > 0.0 && off_h[1] < 1.0)) {
+        set_error("binomial loss needs both classes among the fitting rows");
+        return CWB_EINVAL;
+    }
+    m->offset = off_h[0];
+    CWB_TRY(dev_alloc((void**)&m->f, sizeof(float) * n_pad, s));
+    if (m->accel) {
+        CWB_TRY(dev_alloc((void**)&m->h, sizeof(float) * n_pad, s));
+        CWB_TRY(dev_alloc((void**)&m->c, sizeof(float) * n_pad, s));
+    }
+    CWB_TRY(dev_alloc((void**)&m->rw, sizeof(float) * 2 * n_pad, s));
+    k_init_rows<<<g_rows, kThreads, 0, s>>>(n_pad, (float)m->offset, m->f, m->h, m->c, m->rw);
+    CWB_CUDA_TRY(cudaGetLastError());
+    CWB_CUDA_TRY(cudaStreamSynchronize(s));     // temporaries are released on return
+    return CWB_OK;
+}
+
+}  // namespace cwb

@@ -1,0 +1,243 @@
+"""Parity of the CUDA library (through the C ABI) with the FP64 oracle, on the GPU.
+
+Inputs are seeded and synthetic; sizes span several scatter tiles, ragged row
+counts, both index widths (uint8 for n* <= 256, uint16 otherwise), exact and
+equidistant binning, both losses, weights, all three optimisers.
+"""
+import numpy as np
+import pytest
+
+import synthetic_inputs as S
+from oracle import oracle as O
+from parity_util import REL_TOL, check_coefficients, check_sequences, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cwb():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2110_03513_gb300 as pkg
+    return pkg
+
+
+def _specs_to_gpu(cwb, specs):
+    out = []
+    for s in specs:
+        out.append(cwb.learner(s["feature"], type=s.get("type", 0), degree=s.get("degree", 3),
+                               n_knots=s.get("n_knots", 20), diff_order=s.get("diff_order", 2),
+                               df=s.get("df", 5.0), lam=s.get("lam", 0.0), n_bins=s.get("n_bins", -1)))
+    return out
+
+
+def run_pair(cwb, X, y, specs, *, M, loss=0, opt=0, nu=0.1, gamma=0.0, patience=5, w=None, val_mask=None,
+             check_predict=True):
+    """Fit on the GPU and in the oracle, compare everything; returns (model, oracle result)."""
+    X = np.ascontiguousarray(X)
+    model = cwb.Model(X, y, _specs_to_gpu(cwb, specs), loss=loss, opt=opt, nu=nu, gamma=gamma, iterations=M,
+                      patience=patience, w=w, val_mask=val_mask, device=0)
+    model.fit(M)
+    ref = O.fit(X.astype(np.float64), np.asarray(y, dtype=np.float64), specs, loss=loss, opt=opt, nu=nu,
+                gamma=gamma, iterations=M, patience=patience, w=w, val_mask=val_mask)
+    k_sel, k_cor, sw = model.trace()
+    assert k_sel.size == M
+    tie = check_sequences(k_sel, ref, k_cor if opt != 0 else None)
+    if tie >= 0:
+        # an oracle near-tie: replay the GPU with the oracle's choices forced and compare the rest
+        model.free()
+        model = cwb.Model(X, y, _specs_to_gpu(cwb, specs), loss=loss, opt=opt, nu=nu, gamma=gamma, iterations=M,
+                          patience=patience, w=w, val_mask=val_mask, device=0)
+        model.force_selection(ref.k_sel)
+        model.fit(M)
+        k_sel, k_cor, sw = model.trace()
+    if opt == 2:
+        assert sw == ref.switch_iter
+    theta = model.all_coefficients(0, dmax=ref.dmax)
+    check_coefficients(theta, ref.theta_f)
+    if opt != 0:
+        check_coefficients(model.all_coefficients(1, dmax=ref.dmax), ref.theta_h)
+    f = model.fitted()
+    assert rel_err(f, ref.f) <= REL_TOL, rel_err(f, ref.f)
+    assert abs(model.offset - ref.offset) <= 1e-12 * max(1.0, abs(ref.offset))
+    if check_predict:
+        rng = np.random.default_rng(99)
+        p, n = X.shape
+        idx = rng.integers(0, n, size=min(n, 3000))
+        Xn = X[:, idx].astype(np.float64) + rng.normal(scale=0.01, size=(p, idx.size))
+        xmin = [X[s["feature"]].min() for s in specs]
+        xmax = [X[s["feature"]].max() for s in specs]
+        pred_ref = O.predict(Xn, specs, xmin, xmax, ref.theta_f, ref.offset)
+        pred = model.predict(np.ascontiguousarray(Xn))
+        assert rel_err(pred, pred_ref) <= REL_TOL, rel_err(pred, pred_ref)
+    return model, ref
+
+
+# ------------------------------------------------------------------ setup
+
+@pytest.mark.parametrize("n_bins,n", [(-1, 5000), (300, 4099), (2, 777)])
+def test_setup_matches_oracle(cwb, n_bins, n):
+    data = S.additive_regression(n, 4, 3, seed=21, dtype=np.float32)
+    specs = [dict(feature=j, n_bins=n_bins) for j in range(4)]
+    if n_bins == 2:
+        specs = [dict(feature=j, n_bins=2, type=1) for j in range(4)]
+    model = cwb.Model(data.X, data.y, _specs_to_gpu(cwb, specs), iterations=1, device=0)
+    for k, s in enumerate(specs):
+        x = data.X[s["feature"]].astype(np.float64)
+        nstar = O.isqrt(n) if n_bins == -1 else n_bins
+        ind_ref, z = O.bin_equidistant(x, nstar)
+        ind = model.bin_index(k)
+        np.testing.assert_array_equal(ind, ind_ref)          # integer work: bit-exact
+        info = model.learner_info(k)
+        assert info.nstar == nstar and info.xmin == x.min() and info.xmax == x.max()
+        if s.get("type", 0) == 1:
+            Zb = O.linear_basis(z)
+        else:
+            Zb = O.bspline_basis(z, x.min(), x.max(), 3, 20)
+        G_ref = O.bin_matmat(ind_ref, Zb)
+        G, P = model.matrices(k)
+        assert rel_err(G, G_ref) < 1e-12
+        if s.get("type", 0) == 1:
+            lam = 0.0
+        else:
+            lam = O.lambda_for_df(G_ref, O.penalty(24, 2), 5.0)
+        assert abs(info.lam - lam) <= 1e-8 * max(lam, 1e-300)
+        K = O.penalty(Zb.shape[1], 2) if s.get("type", 0) == 0 else np.zeros((2, 2))
+        P_ref = O.spd_inverse(G_ref + lam * K)
+        assert rel_err(P, P_ref) < 1e-7
+    model.free()
+
+
+def test_exact_binning_setup(cwb):
+    data = S.sim_small_exact(seed=0, n=3000, p=3)
+    X = np.round(data.X * 400) / 400          # repeated values
+    specs = [dict(feature=j, n_bins=0) for j in range(3)]
+    model = cwb.Model(X, data.y, _specs_to_gpu(cwb, specs), iterations=1, device=0)
+    for k in range(3):
+        ind_ref, z = O.bin_exact(X[k])
+        np.testing.assert_array_equal(model.bin_index(k), ind_ref)
+        assert model.learner_info(k).nstar == z.size
+    model.free()
+
+
+# ------------------------------------------------------------------ CWB
+
+def test_cwb_l2_binned_uint8(cwb):
+    data = S.additive_regression(20_011, 6, 4, seed=22, dtype=np.float32)   # n* = 141, ragged n
+    specs = [dict(feature=j, n_bins=-1) for j in range(6)]
+    run_pair(cwb, data.X, data.y, specs, M=120)
+
+
+def test_cwb_l2_binned_uint16_many_tiles(cwb):
+    data = S.additive_regression(100_003, 40, 10, seed=23, dtype=np.float32)
+    specs = [dict(feature=j, n_bins=400) for j in range(40)]
+    run_pair(cwb, data.X, data.y, specs, M=150)
+
+
+def test_cwb_exact_binning_small_config(cwb):
+    """n = 10,000, p = 10 FP64, exact binning (n* = number of unique values), M = 500."""
+    data = S.sim_small_exact(seed=0)
+    specs = [dict(feature=j, n_bins=0) for j in range(10)]
+    model, ref = run_pair(cwb, data.X, data.y, specs, M=500)
+    assert model.learner_info(0).nstar == 10_000
+
+
+def test_cwb_binomial(cwb):
+    data = S.sim_binomial_hybrid(seed=24, n=30_000, p=8, n_informative=4)
+    specs = [dict(feature=j, n_bins=-1) for j in range(8)]
+    run_pair(cwb, data.X, data.y, specs, M=150, loss=1)
+
+
+def test_cwb_weights_and_mixed_learners(cwb):
+    data = S.additive_regression(12_345, 5, 3, seed=25, dtype=np.float64)
+    rng = np.random.default_rng(3)
+    w = rng.uniform(0.2, 3.0, size=data.n)
+    specs = [dict(feature=j, n_bins=-1) for j in range(5)] + [dict(feature=j, n_bins=-1, type=1) for j in range(5)]
+    specs += [dict(feature=1, n_bins=50, degree=2, n_knots=10, df=4.0)]
+    run_pair(cwb, data.X, data.y, specs, M=120, w=w)
+
+
+def test_duplicate_learners_tie_to_lowest_index(cwb):
+    data = S.additive_regression(9_000, 3, 3, seed=26, dtype=np.float32)
+    specs = [dict(feature=0, n_bins=-1), dict(feature=1, n_bins=-1), dict(feature=1, n_bins=-1),
+             dict(feature=2, n_bins=-1)]
+    model, ref = run_pair(cwb, data.X, data.y, specs, M=60)
+    k_sel, _, _ = model.trace()
+    assert not np.any(k_sel == 2)
+
+
+def test_resumed_fit_equals_single_fit(cwb):
+    data = S.additive_regression(15_000, 5, 4, seed=27, dtype=np.float32)
+    specs = [dict(feature=j, n_bins=-1) for j in range(5)]
+    a = cwb.Model(data.X, data.y, _specs_to_gpu(cwb, specs), iterations=80, device=0)
+    a.fit(30)
+    a.fit(17)
+    a.fit(33)
+    ref = O.fit(data.X.astype(np.float64), data.y.astype(np.float64), specs, iterations=80)
+    k_sel, _, _ = a.trace()
+    check_sequences(k_sel, ref)
+    check_coefficients(a.all_coefficients(0, dmax=ref.dmax), ref.theta_f)
+    assert rel_err(a.fitted(), ref.f) <= REL_TOL
+
+
+# ------------------------------------------------------------------ ACWB / HCWB
+
+def test_acwb_l2(cwb):
+    data = S.additive_regression(25_000, 6, 4, seed=28, dtype=np.float32)
+    specs = [dict(feature=j, n_bins=-1) for j in range(6)]
+    run_pair(cwb, data.X, data.y, specs, M=120, opt=1, gamma=0.05)
+
+
+def test_acwb_binomial_uint16(cwb):
+    data = S.sim_binomial_hybrid(seed=29, n=70_000, p=10, n_informative=4)
+    specs = [dict(feature=j, n_bins=300) for j in range(10)]
+    run_pair(cwb, data.X, data.y, specs, M=100, opt=1, loss=1, gamma=0.01)
+
+
+def test_hcwb_binomial_switches_like_oracle(cwb):
+    data = S.sim_binomial_hybrid(seed=30, n=40_000, p=8, n_informative=3)
+    specs = [dict(feature=j, n_bins=-1) for j in range(8)]
+    model, ref = run_pair(cwb, data.X, data.y, specs, M=200, opt=2, loss=1, gamma=0.3, nu=0.3, patience=3,
+                          val_mask=data.val_mask)
+    assert ref.switch_iter > 0
+
+
+def test_hcwb_patience_zero_starts_with_cwb(cwb):
+    data = S.sim_binomial_hybrid(seed=31, n=20_000, p=5, n_informative=3)
+    specs = [dict(feature=j, n_bins=-1) for j in range(5)]
+    model, ref = run_pair(cwb, data.X, data.y, specs, M=40, opt=2, loss=1, gamma=0.05, patience=0,
+                          val_mask=data.val_mask)
+    assert ref.switch_iter == 1
+
+
+# ------------------------------------------------------------------ edge cases and errors
+
+def test_tiny_problem_linear_learners(cwb):
+    X = np.array([[0.0, 1.0, 2.0, 3.0, 5.0], [1.0, -1.0, 0.5, 0.25, 2.0]])
+    y = np.array([1.0, 2.0, 2.5, 4.0, 7.0])
+    specs = [dict(feature=0, type=1, n_bins=0), dict(feature=1, type=1, n_bins=0)]
+    run_pair(cwb, X, y, specs, M=25, nu=0.5)
+
+
+def test_invalid_inputs_are_rejected(cwb):
+    X = np.ones((2, 100), dtype=np.float32)
+    y = np.zeros(100, dtype=np.float32)
+    with pytest.raises(cwb.CwbError) as e:
+        cwb.Model(X, y, [cwb.learner(0)], device=0)
+    assert e.value.status == 1 and "constant" in str(e.value)
+    Xr = np.random.default_rng(0).random((2, 100)).astype(np.float32)
+    with pytest.raises(cwb.CwbError):
+        cwb.Model(Xr, y + 2, [cwb.learner(0)], loss=cwb.LOSS_BINOMIAL, device=0)
+    with pytest.raises(cwb.CwbError):
+        cwb.Model(Xr, y, [cwb.learner(0)], opt=cwb.OPT_HCWB, device=0)
+    with pytest.raises(cwb.CwbError):
+        cwb.Model(Xr, y, [cwb.learner(5)], device=0)
+
+
+# ------------------------------------------------------------------ full-size workload, sampled
+
+def test_full_size_binned_l2_first_iterations(cwb):
+    """n = 1,000,000, p = 50, n* = 1000 (uint16): the first 12 iterations against the oracle."""
+    data = S.sim_binned_l2(seed=1)
+    specs = [dict(feature=j, n_bins=-1) for j in range(50)]
+    run_pair(cwb, data.X, data.y, specs, M=12, check_predict=False)
