@@ -1,0 +1,345 @@
+#!/usr/bin/env python3
+"""Benchmark of the binned CWB iteration on GB300.
+
+Workload (the headline configuration): binned componentwise boosting, L2
+loss, n = 1,000,000 rows, p = 50 U[0,1] FP32 features (10 informative,
+SNR 1), n* = floor(sqrt(n)) = 1000 equidistant bins per feature (uint16
+index vectors), one cubic P-spline learner per feature (d = 24, df = 5),
+nu = 0.1.  Seeded synthetic data stands in for the paper's simulation data.
+
+A step is one boosting iteration through the public C ABI (cwb_fit(model, 1)):
+pseudo residuals, binMatVec scatter of every feature, Z^T u, the solve with
+the cached inverse, the SSE criterion, the argmin and the model update.  The
+L2 cache is flushed (a 256 MiB buffer is written) before every timed step and
+each step is timed with CUDA events on the model's stream; the flush is not
+timed.
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "binned CWB iters/s & HBM GB/s at n=1M,p=50; served fits/s, p50/p99 latency"
+UNIT = "iters/s"
+N_ROWS, N_FEAT, NSTAR, M_FIT = 1_000_000, 50, 1000, 2000
+NU = 0.1
+# Algorithmic bytes (FP32 vectors, uint16 indices): the index stream of every feature
+# plus y (read), f (read + write) and the update gather of the selected feature.
+ALG_BYTES_ITER = N_FEAT * N_ROWS * 2 + N_ROWS * (4 + 8 + 2)
+# Per launch of the scatter kernel: the index stream plus the residual vector.
+ALG_BYTES_SCATTER = N_FEAT * N_ROWS * 2 + N_ROWS * 4
+FLUSH_BYTES = 256 << 20
+WORKLOAD = ("binned CWB, L2 loss, n=1,000,000, p=50 U[0,1] FP32 features (10 informative, SNR 1), "
+            "n*=1000 equidistant bins per feature (uint16 index), cubic P-splines d=24 df=5, nu=0.1")
+
+# DRAM traffic of one scatter launch from the committed ncu capture, valid for the
+# scatter kernel source with this SHA-256 prefix (null once the kernel changes).
+SCATTER_TRAFFIC = {"sha256": None, "bytes": None}
+
+
+def scatter_source_hash() -> str:
+    path = os.path.join(ROOT, "paper_2110_03513_gb300", "csrc", "cwb_iter.cu")
+    text = open(path).read()
+    start = text.find("// binMatVec scatter")
+    end = text.find("// Per-learner fit, criterion and argmin")
+    return hashlib.sha256(text[start:end].encode()).hexdigest()[:16]
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--skip-cpu-baseline", action="store_true", help="do not time the CPU oracle")
+    ap.add_argument("--skip-e2e", action="store_true", help="do not run the end-to-end fit")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        time.sleep(0.3)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.1)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        return self.summary()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------- CPU oracle
+
+def time_oracle(X, y, specs, iters: int):
+    """Seconds per oracle iteration (setup timed separately and subtracted)."""
+    from oracle import oracle as O
+    t0 = time.perf_counter()
+    O.fit(X, y, specs, nu=NU, iterations=0)
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    O.fit(X, y, specs, nu=NU, iterations=iters)
+    t_all = time.perf_counter() - t0
+    return max(t_all - t_setup, 1e-9) / iters, t_setup
+
+
+def cpu_baseline_full(data, iters: int = 6):
+    import numpy as np
+    specs = [dict(feature=j, n_bins=-1, df=5.0) for j in range(N_FEAT)]
+    X = data.X.astype(np.float64)
+    y = data.y.astype(np.float64)
+    per_iter, t_setup = time_oracle(X, y, specs, iters)
+    return {"value": 1.0 / per_iter, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"FP64 C oracle, single thread, {iters} iterations of the full n=1,000,000 p=50 workload "
+                      f"(setup {t_setup:.1f} s timed separately and excluded)"}
+
+
+def run_reference(args):
+    """The FP64 CPU oracle timed as the reference arm (rank 0 only)."""
+    import numpy as np
+    import synthetic_inputs as S
+    from oracle import oracle as O
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    O.build()
+    data = S.sim_binned_l2(seed=args.seed)
+    # bounded sample: the first n' rows, one iteration per step; the iteration is linear in n
+    budget_s = 150.0
+    per_row = 1.6e-6              # rough oracle seconds per row and iteration at p = 50
+    steps = max(args.steps, 1) + max(args.warmup, 0)
+    n_s = int(min(N_ROWS, max(20_000, budget_s / steps / per_row)))
+    X = data.X[:, :n_s].astype(np.float64)
+    y = data.y[:n_s].astype(np.float64)
+    specs = [dict(feature=j, n_bins=NSTAR, df=5.0) for j in range(N_FEAT)]
+    t0 = time.perf_counter()
+    O.fit(X, y, specs, nu=NU, iterations=0)
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    O.fit(X, y, specs, nu=NU, iterations=steps)
+    per_step = max(time.perf_counter() - t0 - t_setup, 1e-9) / steps
+    value = 1.0 / (per_step * N_ROWS / n_s)
+    sample = (f"FP64 C oracle, single thread: {steps} iterations on the first {n_s} rows of the n=1,000,000 p=50 "
+              f"workload (n*=1000 bins), time per iteration scaled by n/n' = {N_ROWS / n_s:.2f}")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * N_ROWS / n_s * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "n": N_ROWS, "p": N_FEAT, "nstar": NSTAR},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------- GPU arm
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import synthetic_inputs as S
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__ as g
+    g.build()
+    import paper_2110_03513_gb300 as cwb
+
+    data = S.sim_binned_l2(seed=args.seed + rank)
+    stream = torch.cuda.Stream(device=dev)
+    learners = [cwb.learner(j, n_bins=NSTAR, df=5.0) for j in range(N_FEAT)]
+    with torch.cuda.stream(stream):
+        Xd = torch.from_numpy(data.X).to(dev)
+        yd = torch.from_numpy(data.y).to(dev)
+        stream.synchronize()
+        model = cwb.Model(Xd, yd, learners, nu=NU, iterations=M_FIT, stream=stream, device=local)
+        del Xd, yd
+        flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        for _ in range(max(args.warmup, 3)):
+            flush.zero_()
+            model.fit(1)
+        stream.synchronize()
+        K = args.steps
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        props = torch.cuda.get_device_properties(dev)
+        gpu_id = str(getattr(props, "uuid", local))
+        if gpu_id and not gpu_id.startswith("GPU-") and len(gpu_id) > 8:
+            gpu_id = "GPU-" + gpu_id
+        sampler = ClockSampler(gpu_id if rank == 0 else str(local))
+        if rank == 0:
+            sampler.start()
+        model.profile(True)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        for i in range(K):
+            flush.zero_()
+            starts[i].record(stream)
+            model.fit(1)
+            ends[i].record(stream)
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+        clocks = sampler.stop() if rank == 0 else None
+        prof = model.get_profile()
+        model.profile(False)
+        step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * K / (total_ms / 1e3)
+    ms_per_step = total_ms / K
+    launches = sum(v[1] for v in prof.values())
+
+    # roofline of the dominant kernel (the scatter), from its own events on the model's stream
+    sc_ms, sc_n = prof["scatter"]
+    sc_avg = sc_ms / max(sc_n, 1) / 1e3
+    peak, peak_kind = measured_peaks()
+    achieved = ALG_BYTES_SCATTER / sc_avg / 1e9
+    traffic = SCATTER_TRAFFIC["bytes"] if SCATTER_TRAFFIC["sha256"] == scatter_source_hash() else None
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": N_ROWS, "p": N_FEAT, "nstar": NSTAR, "index": "uint16",
+                       "learners": N_FEAT, "l2": "flushed before every timed step (256 MiB write, untimed)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "hbm_gbs": ALG_BYTES_ITER / (ms_per_step / 1e3) / 1e9,
+            "kernel_ms": {k: v[0] / max(v[1], 1) for k, v in prof.items()},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "kernel": "k_scatter",
+                         "peak_source": f"{peak_kind} hbm_gbs"},
+            "gpu_launches": launches, "clocks": clocks}
+
+    if not args.skip_e2e:
+        line["e2e"] = run_e2e(cwb, data, stream, dev, local)
+    if rank == 0 and world == 1 and not args.skip_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_full(data)
+    model.free()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_e2e(cwb, data, stream, dev, local):
+    """A full fit (M = 2000) through the C ABI from pinned host buffers, results read back."""
+    import numpy as np
+    import torch
+    Xh = torch.from_numpy(data.X).pin_memory()
+    yh = torch.from_numpy(data.y).pin_memory()
+    Xn, yn = Xh.numpy(), yh.numpy()
+    learners = [cwb.learner(j, n_bins=NSTAR, df=5.0) for j in range(N_FEAT)]
+    theta = np.zeros((N_FEAT, 24))
+    fitted = torch.empty(N_ROWS, dtype=torch.float32).pin_memory().numpy()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        m = cwb.Model(Xn, yn, learners, nu=NU, iterations=M_FIT, stream=stream, device=local)
+        m.fit(M_FIT)
+        for k in range(N_FEAT):
+            cwb.cwb_get_coefficients(m.handle, k, 0, theta[k])
+        m.fitted(fitted)
+    dt = time.perf_counter() - t0
+    m.free()
+    h2d = Xn.nbytes + yn.nbytes
+    d2h = theta.nbytes + fitted.nbytes
+    return {"value": M_FIT / dt, "unit": UNIT, "h2d_bytes_per_step": h2d / M_FIT, "d2h_bytes_per_step": d2h / M_FIT,
+            "what": f"cwb_create from pinned host X, y + cwb_fit({M_FIT}) + coefficients and fitted values read "
+                    f"back, wall clock {dt * 1e3:.1f} ms"}
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -89,7 +89,7 @@ typedef struct {
     int32_t iterations;        /* default M for cwb_fit(model, 0) */
     int32_t patience;          /* pat_0 >= 0 (HCWB) */
     const uint8_t* val_mask;   /* HCWB: n entries, 1 = validation row; same memory kind as X */
-    void* stream;              /* cudaStream_t to issue work on; NULL = the legacy default stream */
+    void* stream;              /* cudaStream_t to issue work on; NULL: the model creates and owns a stream */
     int32_t device;            /* CUDA device ordinal; -1 = the calling thread's current device */
 } cwb_config;
 
@@ -202,6 +202,23 @@ cwb_status cwb_get_bin_index(const cwb_model* m, int32_t k, int32_t* ind);
  * override).  Used to keep comparing against the FP64 oracle past a near tie.
  */
 cwb_status cwb_force_selection(cwb_model* m, const int32_t* k_forced, int32_t count);
+
+/*
+ * cwb_profile -- enable (1) or disable (0) per-kernel timing: while enabled, every
+ * kernel an iteration launches is bracketed by CUDA events recorded on the model's
+ * stream (iterations are then launched one by one instead of from a CUDA graph).
+ * Enabling also clears the accumulated figures.
+ */
+cwb_status cwb_profile(cwb_model* m, int32_t enable);
+
+/*
+ * cwb_get_profile -- accumulated device time (ms) and launch counts per kernel
+ * class since profiling was enabled: index 0 = row pass (update / pseudo
+ * residuals), 1 = binMatVec scatter, 2 = solve / criterion / argmin.  `ms` and
+ * `launches` hold `cap` entries (host memory, either may be NULL).  Synchronises
+ * the model's stream.
+ */
+cwb_status cwb_get_profile(cwb_model* m, double* ms, int64_t* launches, int32_t cap);
 
 /* cwb_synchronize -- wait for the model's queued work; reports device-side errors. */
 cwb_status cwb_synchronize(cwb_model* m);

@@ -62,6 +62,8 @@ _SIGS = {
     "cwb_get_bin_index": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     "cwb_force_selection": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
     "cwb_synchronize": (C.c_int, [C.c_void_p]),
+    "cwb_profile": (C.c_int, [C.c_void_p, C.c_int32]),
+    "cwb_get_profile": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
     "cwb_last_error": (C.c_char_p, []),
     "cwb_free": (None, [C.c_void_p]),
 }
@@ -181,6 +183,14 @@ def cwb_force_selection(model, k_forced: np.ndarray):
 
 def cwb_synchronize(model):
     _check(load_library().cwb_synchronize(model), "cwb_synchronize")
+
+
+def cwb_profile(model, enable: int):
+    _check(load_library().cwb_profile(model, enable), "cwb_profile")
+
+
+def cwb_get_profile(model, ms: np.ndarray, launches: np.ndarray):
+    _check(load_library().cwb_get_profile(model, _ptr(ms), _ptr(launches), ms.size), "cwb_get_profile")
 
 
 def cwb_free(model):
@@ -319,6 +329,15 @@ class Model:
         ind = np.zeros(self.n, dtype=np.int32)
         cwb_get_bin_index(self.handle, k, ind)
         return ind
+
+    def profile(self, enable: bool = True):
+        cwb_profile(self.handle, 1 if enable else 0)
+
+    def get_profile(self):
+        ms = np.zeros(3)
+        launches = np.zeros(3, dtype=np.int64)
+        cwb_get_profile(self.handle, ms, launches)
+        return {name: (float(ms[i]), int(launches[i])) for i, name in enumerate(("rows", "scatter", "solve"))}
 
     def force_selection(self, ks):
         cwb_force_selection(self.handle, np.ascontiguousarray(ks, dtype=np.int32))

@@ -101,11 +101,12 @@ __global__ void k_predict(const T* __restrict__ X, int64_t n_new, int K, int D, 
     }
 }
 
+// Fitted values in the caller's row order; f holds compensated (hi, lo) pairs.
 __global__ void k_unpermute(const float* __restrict__ f, const int32_t* __restrict__ perm, int64_t n,
                             float* __restrict__ out)
 {
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
-        out[perm ? perm[q] : q] = f[q];
+        out[perm ? perm[q] : q] = f[2 * q] + f[2 * q + 1];
 }
 
 int grid_1d(int64_t work, int device)
@@ -135,11 +136,12 @@ void free_model(cwb_model* m)
 {
     if (!m) return;
     if (m->stream) cudaStreamSynchronize(m->stream);
-    void* bufs[] = {m->ind, m->y, m->w, m->f, m->h, m->c, m->rw, m->perm, m->zb, m->zb64, m->zcol, m->crange, m->G,
+    void* bufs[] = {m->ind, m->y, m->y_lo, m->w, m->f, m->h, m->c, m->rw, m->perm, m->zb, m->zb64, m->zcol, m->crange, m->G,
                     m->P, m->lambda, m->l_bin, m->l_d, m->l_nstar, m->l_type, m->l_xmin, m->l_xmax, m->l_degree,
                     m->l_nknots, m->l_feat, m->part, m->theta_it, m->q_it, m->v, m->state, m->risk_part, m->tr_k,
                     m->tr_mode, m->tr_theta, m->tr_q, m->forced, m->coef};
     for (void* p : bufs) dev_free(p);
+    profile_release(m);
     if (m->graph_exec) cudaGraphExecDestroy(m->graph_exec);
     if (m->capture_stream) cudaStreamDestroy(m->capture_stream);
     if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
@@ -549,6 +551,33 @@ cwb_status cwb_force_selection(cwb_model* m, const int32_t* k_forced, int32_t co
     set_error("");
     if (!m || (count > 0 && !k_forced) || count < 0) { set_error("bad argument"); return CWB_EINVAL; }
     m->forced_host.assign(k_forced, k_forced + count);
+    return CWB_OK;
+}
+
+cwb_status cwb_profile(cwb_model* m, int32_t enable)
+{
+    set_error("");
+    if (!m) { set_error("model is NULL"); return CWB_EINVAL; }
+    DeviceGuard guard(m->device);
+    CWB_TRY(profile_collect(m));
+    for (int i = 0; i < 3; ++i) {
+        m->prof_ms[i] = 0.0;
+        m->prof_launches[i] = 0;
+    }
+    m->prof_on = enable != 0;
+    return CWB_OK;
+}
+
+cwb_status cwb_get_profile(cwb_model* m, double* ms, int64_t* launches, int32_t cap)
+{
+    set_error("");
+    if (!m || cap < 0) { set_error("bad argument"); return CWB_EINVAL; }
+    DeviceGuard guard(m->device);
+    CWB_TRY(profile_collect(m));
+    for (int i = 0; i < cap && i < 3; ++i) {
+        if (ms) ms[i] = m->prof_ms[i];
+        if (launches) launches[i] = m->prof_launches[i];
+    }
     return CWB_OK;
 }
 

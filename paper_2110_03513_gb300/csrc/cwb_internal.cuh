@@ -3,8 +3,10 @@
 // Device memory layout of one model (all owned by cwb_model, freed by cwb_free):
 //   ind      [B][n_pad]   uint8 or uint16 index vectors, one row per binning (learners on the
 //                         same feature with the same n_bins share a binning), rows train-first
-//   y, w     [n_pad]      FP32 targets and weights (w omitted when all ones)
-//   f, h, c  [n_pad]      FP32 primary model, momentum model, error-corrected residual
+//   y, w     [n_pad]      FP32 targets and weights (w omitted when all ones); y_lo holds the
+//                         low part of FP64 targets
+//   f, h     [n_pad][2]   primary and momentum model as compensated FP32 pairs (hi, lo)
+//   c        [n_pad]      FP32 error-corrected residual (ACWB)
 //   rw       [2][n_pad]   FP32 scatter inputs w*r (channel 0) and w*c (channel 1), zero past
 //                         the active rows
 //   zb       [K][S][4]    FP32 non-zero basis values at the design points (S = max n*)
@@ -19,6 +21,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "cwb.h"
@@ -108,7 +111,8 @@ struct cwb_model {
 
     // device buffers
     void* ind = nullptr;
-    float *y = nullptr, *w = nullptr, *f = nullptr, *h = nullptr, *c = nullptr, *rw = nullptr;
+    float *y = nullptr, *y_lo = nullptr, *w = nullptr, *c = nullptr, *rw = nullptr;
+    float *f = nullptr, *h = nullptr;     // [n_pad][2]: compensated hi, lo
     int32_t* perm = nullptr;              // new row -> original row (HCWB)
     float* zb = nullptr;
     double* zb64 = nullptr;
@@ -136,6 +140,12 @@ struct cwb_model {
     int32_t coef_valid_at = -1;
     int32_t done = 0;                     // iterations queued so far
     std::vector<int32_t> forced_host;     // pending host-side forced selections
+    // per-kernel timing (cwb_profile)
+    bool prof_on = false;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_pending;
+    std::vector<cudaEvent_t> prof_pool;
+    double prof_ms[3] = {0.0, 0.0, 0.0};
+    int64_t prof_launches[3] = {0, 0, 0};
     // CUDA graph of a fixed block of iterations
     cudaGraphExec_t graph_exec = nullptr;
     int graph_iters = 0;
@@ -175,6 +185,8 @@ cwb_status launch_final_update(cwb_model* m);
 cwb_status launch_initial_rows(cwb_model* m);
 cwb_status launch_aggregate(cwb_model* m);
 cwb_status read_device_error(cwb_model* m);
+cwb_status profile_collect(cwb_model* m);
+void profile_release(cwb_model* m);
 
 // Predict / fitted (cwb_api.cu)
 cwb_status launch_predict(const cwb_model* m, const void* Xnew, int x_dtype, int64_t n_new, float* out_dev);

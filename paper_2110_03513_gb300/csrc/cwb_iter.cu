@@ -35,9 +35,10 @@ struct RowArgs {
     const void* ind;
     int64_t n, n_tr, n_pad;
     const float* y;
+    const float* y_lo;    // low part of FP64 targets (NULL for FP32 targets)
     const float* w;
-    float* f;
-    float* h;
+    float* f;             // [n_pad][2] hi, lo
+    float* h;             // [n_pad][2] hi, lo (ACWB/HCWB)
     float* c;
     float* rw;
     const float* v;       // [2][S]
@@ -73,20 +74,74 @@ __device__ __forceinline__ void load_ind4<uint8_t>(const uint8_t* p, int64_t i, 
     out[3] = u >> 24;
 }
 
-__device__ __forceinline__ float neg_gradient(int loss, float y, float f)
+// ---- compensated ("double-float") arithmetic: a value is hi + lo, two FP32 numbers.
+// The models f and h and the per-iteration coefficients (1 - theta_m, theta_m,
+// nu, eta_m, m/(m+1)) are carried this way so that the only FP32 rounding left
+// in a residual is its own final rounding.  Error-free transforms: TwoSum
+// (Knuth) and the FMA product error.
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ DF fast_two_sum(float a, float b)
 {
-    if (loss == CWB_LOSS_L2) return y - f;
-    return y - 1.0f / (1.0f + expf(-f));
+    float s = a + b;
+    return {s, b - (s - a)};
 }
 
-__device__ __forceinline__ float loss_value(int loss, float y, float f)
+__device__ __forceinline__ DF two_sum(float a, float b)
+{
+    float s = a + b;
+    float bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+
+__device__ __forceinline__ DF df_add(DF a, DF b)
+{
+    DF s = two_sum(a.hi, b.hi);
+    return fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
+
+__device__ __forceinline__ DF df_mul(DF a, DF b)
+{
+    float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ DF df_mul_f(DF a, float b)
+{
+    float p = a.hi * b;
+    float e = fmaf(a.hi, b, -p);
+    e = fmaf(a.lo, b, e);
+    return fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ DF df_of(double x)
+{
+    float hi = (float)x;
+    return {hi, (float)(x - (double)hi)};
+}
+
+// r = -dL/df at f = g (L2: y - g; binomial: y - sigmoid(g), first order in g.lo).
+__device__ __forceinline__ float neg_gradient(int loss, float y, float ylo, DF g)
+{
+    if (loss == CWB_LOSS_L2) return ((y - g.hi) + ylo) - g.lo;
+    float sg = 1.0f / (1.0f + expf(-g.hi));
+    return (y - sg) - sg * (1.0f - sg) * g.lo;
+}
+
+__device__ __forceinline__ float loss_value(int loss, float y, float ylo, DF f)
 {
     if (loss == CWB_LOSS_L2) {
-        float e = y - f;
+        float e = ((y - f.hi) + ylo) - f.lo;
         return 0.5f * e * e;
     }
-    float lse = f > 0.0f ? f + log1pf(expf(-f)) : log1pf(expf(f));
-    return lse - y * f;
+    float lse = f.hi > 0.0f ? f.hi + log1pf(expf(-f.hi)) : log1pf(expf(f.hi));
+    float sg = 1.0f / (1.0f + expf(-f.hi));
+    return (lse - y * f.hi) + (sg - y) * f.lo;
 }
 
 __device__ __forceinline__ float get4(const float4& v, int t)
@@ -99,43 +154,63 @@ __device__ __forceinline__ void set4(float4& v, int t, float x)
     if (t == 0) v.x = x; else if (t == 1) v.y = x; else if (t == 2) v.z = x; else v.w = x;
 }
 
+__device__ __forceinline__ void load_df4(const float* p, int64_t i4, DF out[4])
+{
+    float4 a = *reinterpret_cast<const float4*>(p + 2 * i4);
+    float4 b = *reinterpret_cast<const float4*>(p + 2 * i4 + 4);
+    out[0] = {a.x, a.y};
+    out[1] = {a.z, a.w};
+    out[2] = {b.x, b.y};
+    out[3] = {b.z, b.w};
+}
+
+__device__ __forceinline__ void store_df4(float* p, int64_t i4, const DF v[4])
+{
+    *reinterpret_cast<float4*>(p + 2 * i4) = make_float4(v[0].hi, v[0].lo, v[1].hi, v[1].lo);
+    *reinterpret_cast<float4*>(p + 2 * i4 + 4) = make_float4(v[2].hi, v[2].lo, v[3].hi, v[3].lo);
+}
+
 template <int KIND, typename IndT>
 __global__ void __launch_bounds__(kRowThreads) k_rows(RowArgs a)
 {
     const DevState st = *a.state;
     const bool pend = (KIND != kRowsResid) && (st.m > st.m_applied);
     const int pm = st.pend_mode;
-    const float nu = (float)a.nu;
     const IndT* ind = static_cast<const IndT*>(a.ind);
     const IndT* ind_sel = (st.k_sel >= 0) ? ind + (int64_t)a.l_bin[st.k_sel] * a.n_pad : nullptr;
     const IndT* ind_cor = (st.k_cor >= 0) ? ind + (int64_t)a.l_bin[st.k_cor] * a.n_pad : nullptr;
     const float* v0 = a.v;
     const float* v1 = a.v + a.S;
+    const DF nu = df_of(a.nu);
 
-    // pending update of iteration st.m
-    float thp = 1.0f, etap = 0.0f;
+    // pending update of iteration st.m (Algorithm 1 line "f = f + nu b"; Algorithm 3: f = g + nu b, h += eta b_cor)
+    DF om_p = {1.0f, 0.0f}, th_p = {0.0f, 0.0f}, eta_p = {0.0f, 0.0f};
     if (pend && pm == kModeACWB) {
-        thp = (float)(2.0 / ((double)st.m + 1.0));
-        etap = (float)(a.gamma * a.nu * ((double)st.m + 1.0) * 0.5);
+        const double thm = 2.0 / ((double)st.m + 1.0);
+        om_p = df_of(1.0 - thm);
+        th_p = df_of(thm);
+        eta_p = df_of(a.gamma * a.nu / thm);
     }
     // residuals of iteration st.m + 1
     const int mode_n = st.mode;
     const int m_n = st.m + 1;
     const bool acwb_n = (mode_n == kModeACWB);
     const int64_t n_act = (acwb_n && a.hybrid) ? a.n_tr : a.n;
-    const float thn = (float)(2.0 / ((double)m_n + 1.0));
-    const float cmul = (float)((double)m_n / ((double)m_n + 1.0));
+    const double thn_d = 2.0 / ((double)m_n + 1.0);
+    const DF om_n = df_of(1.0 - thn_d), th_n = df_of(thn_d);
+    const DF cmul = df_of((double)m_n / ((double)m_n + 1.0));
     const bool first_acwb = (m_n == 1);
-    const bool need_bc = pend ? (pm == kModeACWB) : false;
+    const bool need_bc = pend && pm == kModeACWB;
     const bool need_bc_resid = (KIND != kRowsUpdate) && acwb_n && !first_acwb;
     const bool eval_risk = (KIND == kRowsUpdate) && a.hybrid && (!st.risk_valid || (pend && pm == kModeACWB));
 
     double risk_acc = 0.0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x * 4;
     for (int64_t i4 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; i4 < a.n_pad; i4 += stride) {
-        float4 f4 = *reinterpret_cast<const float4*>(a.f + i4);
-        float4 h4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (a.h) h4 = *reinterpret_cast<const float4*>(a.h + i4);
+        DF fv[4], hv[4];
+        load_df4(a.f, i4, fv);
+        if (a.h) load_df4(a.h, i4, hv);
+        else for (int t = 0; t < 4; ++t) hv[t] = {0.0f, 0.0f};
         float bc[4] = {0.f, 0.f, 0.f, 0.f};
         if ((need_bc || need_bc_resid) && ind_cor) {
             int kc[4];
@@ -148,33 +223,35 @@ __global__ void __launch_bounds__(kRowThreads) k_rows(RowArgs a)
             load_ind4<IndT>(ind_sel, i4, ks);
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
-                float b0 = __ldg(v0 + ks[t]);
-                float fv = get4(f4, t);
+                const float b0 = __ldg(v0 + ks[t]);
                 if (pm == kModeCWB) {
-                    fv = fv + nu * b0;
+                    fv[t] = df_add(fv[t], df_mul_f(nu, b0));
                 } else {
-                    float hv = get4(h4, t);
-                    float g = (1.0f - thp) * fv + thp * hv;
-                    fv = g + nu * b0;
-                    set4(h4, t, hv + etap * bc[t]);
+                    DF g = df_add(df_mul(fv[t], om_p), df_mul(hv[t], th_p));
+                    fv[t] = df_add(g, df_mul_f(nu, b0));
+                    hv[t] = df_add(hv[t], df_mul_f(eta_p, bc[t]));
                 }
-                set4(f4, t, fv);
             }
-            *reinterpret_cast<float4*>(a.f + i4) = f4;
-            if (pm == kModeACWB && a.h) *reinterpret_cast<float4*>(a.h + i4) = h4;
+            store_df4(a.f, i4, fv);
+            if (pm == kModeACWB && a.h) store_df4(a.h, i4, hv);
         }
         if (eval_risk) {
             if (i4 + 4 > a.n_tr && i4 < a.n) {
                 float4 y4 = *reinterpret_cast<const float4*>(a.y + i4);
+                float4 yl4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (a.y_lo) yl4 = *reinterpret_cast<const float4*>(a.y_lo + i4);
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
                     int64_t i = i4 + t;
-                    if (i >= a.n_tr && i < a.n) risk_acc += (double)loss_value(a.loss, get4(y4, t), get4(f4, t));
+                    if (i >= a.n_tr && i < a.n)
+                        risk_acc += (double)loss_value(a.loss, get4(y4, t), get4(yl4, t), fv[t]);
                 }
             }
         }
         if (KIND != kRowsUpdate) {
             float4 y4 = *reinterpret_cast<const float4*>(a.y + i4);
+            float4 yl4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (a.y_lo) yl4 = *reinterpret_cast<const float4*>(a.y_lo + i4);
             float4 w4 = make_float4(1.f, 1.f, 1.f, 1.f);
             if (a.w) w4 = *reinterpret_cast<const float4*>(a.w + i4);
             float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
@@ -184,13 +261,18 @@ __global__ void __launch_bounds__(kRowThreads) k_rows(RowArgs a)
             for (int t = 0; t < 4; ++t) {
                 int64_t i = i4 + t;
                 if (i >= n_act) continue;
-                float yv = get4(y4, t), wv = get4(w4, t);
+                float yv = get4(y4, t), ylo = get4(yl4, t), wv = get4(w4, t);
                 if (!acwb_n) {
-                    set4(r0, t, wv * neg_gradient(a.loss, yv, get4(f4, t)));
+                    set4(r0, t, wv * neg_gradient(a.loss, yv, ylo, fv[t]));
                 } else {
-                    float g = (1.0f - thn) * get4(f4, t) + thn * get4(h4, t);
-                    float r = neg_gradient(a.loss, yv, g);
-                    float cv = first_acwb ? r : r + cmul * (get4(c4, t) - bc[t]);
+                    DF g = df_add(df_mul(fv[t], om_n), df_mul(hv[t], th_n));
+                    float r = neg_gradient(a.loss, yv, ylo, g);
+                    float cv = r;
+                    if (!first_acwb) {
+                        DF ct = df_mul_f(cmul, get4(c4, t) - bc[t]);
+                        DF cs = df_add(ct, DF{r, 0.0f});
+                        cv = cs.hi + cs.lo;
+                    }
                     set4(c4, t, cv);
                     set4(r0, t, wv * r);
                     set4(r1, t, wv * cv);
@@ -584,6 +666,7 @@ RowArgs row_args(cwb_model* m)
     a.n_tr = m->n_tr;
     a.n_pad = m->n_pad;
     a.y = m->y;
+    a.y_lo = m->y_lo;
     a.w = m->w;
     a.f = m->f;
     a.h = m->h;
@@ -661,16 +744,59 @@ void launch_solve(cwb_model* m, cudaStream_t s)
     k_solve<<<m->K, kSolveThreads, 0, s>>>(a);
 }
 
+// Event pair around one launch when profiling (never while capturing a graph).
+struct ProfScope {
+    cwb_model* m;
+    cudaStream_t s;
+    int cls;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    static cudaEvent_t take(cwb_model* m)
+    {
+        if (!m->prof_pool.empty()) {
+            cudaEvent_t e = m->prof_pool.back();
+            m->prof_pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    ProfScope(cwb_model* mm, cudaStream_t ss, int c) : m(mm), s(ss), cls(c)
+    {
+        if (m->prof_on && s == m->stream) {
+            e0 = take(m);
+            e1 = take(m);
+            if (e0) cudaEventRecord(e0, s);
+        }
+    }
+    ~ProfScope()
+    {
+        if (e0 && e1) {
+            cudaEventRecord(e1, s);
+            m->prof_pending.push_back({cls, {e0, e1}});
+        }
+    }
+};
+
 void enqueue_iteration(cwb_model* m, cudaStream_t s)
 {
-    if (m->hybrid) {
-        launch_rows<kRowsUpdate>(m, s);
-        launch_rows<kRowsResid>(m, s);
-    } else {
-        launch_rows<kRowsFused>(m, s);
+    {
+        ProfScope p(m, s, 0);
+        if (m->hybrid) {
+            launch_rows<kRowsUpdate>(m, s);
+            launch_rows<kRowsResid>(m, s);
+        } else {
+            launch_rows<kRowsFused>(m, s);
+        }
     }
-    launch_scatter(m, s);
-    launch_solve(m, s);
+    {
+        ProfScope p(m, s, 1);
+        launch_scatter(m, s);
+    }
+    {
+        ProfScope p(m, s, 2);
+        launch_solve(m, s);
+    }
 }
 
 cwb_status set_scatter_attrs(cwb_model* m)
@@ -802,7 +928,7 @@ cwb_status launch_iterations(cwb_model* m, int32_t iters)
         m->forced_host.clear();
     }
     int32_t left = iters;
-    if (left >= kGraphIters) {
+    if (left >= kGraphIters && !m->prof_on) {
         if (!m->graph_exec) CWB_TRY(build_graph(m));
         while (left >= kGraphIters) {
             CWB_CUDA_TRY(cudaGraphLaunch(m->graph_exec, m->stream));
@@ -818,6 +944,7 @@ cwb_status launch_iterations(cwb_model* m, int32_t iters)
 
 cwb_status launch_final_update(cwb_model* m)
 {
+    ProfScope p(m, m->stream, 0);
     launch_rows<kRowsUpdate>(m, m->stream);
     CWB_CUDA_TRY(cudaGetLastError());
     return CWB_OK;
@@ -841,7 +968,32 @@ cwb_status launch_aggregate(cwb_model* m)
     return CWB_OK;
 }
 
-int rows_grid_size(const cwb_model* m) { return rows_grid(m); }
+cwb_status profile_collect(cwb_model* m)
+{
+    if (m->prof_pending.empty()) return CWB_OK;
+    CWB_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    for (auto& it : m->prof_pending) {
+        float ms = 0.0f;
+        CWB_CUDA_TRY(cudaEventElapsedTime(&ms, it.second.first, it.second.second));
+        m->prof_ms[it.first] += ms;
+        m->prof_launches[it.first] += 1;
+        m->prof_pool.push_back(it.second.first);
+        m->prof_pool.push_back(it.second.second);
+    }
+    m->prof_pending.clear();
+    return CWB_OK;
+}
+
+void profile_release(cwb_model* m)
+{
+    for (auto& it : m->prof_pending) {
+        cudaEventDestroy(it.second.first);
+        cudaEventDestroy(it.second.second);
+    }
+    m->prof_pending.clear();
+    for (cudaEvent_t e : m->prof_pool) cudaEventDestroy(e);
+    m->prof_pool.clear();
+}
 
 cwb_status read_device_error(cwb_model* m)
 {

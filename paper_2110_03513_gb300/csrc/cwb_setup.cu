@@ -42,11 +42,24 @@ __global__ void k_gather_to_f32(const T* __restrict__ src, const int32_t* __rest
     }
 }
 
-__global__ void k_gather_f64(const double* __restrict__ src, const int32_t* __restrict__ perm, int64_t n,
+template <typename T>
+__global__ void k_gather_f64(const T* __restrict__ src, const int32_t* __restrict__ perm, int64_t n,
                              double* __restrict__ dst)
 {
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
-        dst[q] = src[perm ? perm[q] : q];
+        dst[q] = (double)src[perm ? perm[q] : q];
+}
+
+// FP64 values as hi + lo FP32 pairs (lo omitted when NULL); zero past n.
+__global__ void k_split_f64(const double* __restrict__ src, int64_t n, int64_t n_pad, float* __restrict__ hi,
+                            float* __restrict__ lo)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n_pad; q += (int64_t)gridDim.x * blockDim.x) {
+        double v = q < n ? src[q] : 0.0;
+        float h = (float)v;
+        hi[q] = h;
+        if (lo) lo[q] = (float)(v - (double)h);
+    }
 }
 
 template <typename T>
@@ -612,14 +625,14 @@ __global__ void k_dro(DroArgs a)
 // Offset: loss-optimal constant over the fitting rows (L2: weighted mean,
 // binomial: logit of the weighted mean).
 
-__global__ void k_offset(const float* __restrict__ y, const double* __restrict__ w, int64_t n_fit, int loss,
+__global__ void k_offset(const double* __restrict__ y, const double* __restrict__ w, int64_t n_fit, int loss,
                          double* __restrict__ out /* [0] offset, [1] mean */)
 {
     __shared__ double s1[1024], s2[1024];
     double a = 0.0, b = 0.0;
     for (int64_t i = threadIdx.x; i < n_fit; i += blockDim.x) {
         double wi = w ? w[i] : 1.0;
-        a += wi * (double)y[i];
+        a += wi * y[i];
         b += wi;
     }
     s1[threadIdx.x] = a;
@@ -639,11 +652,15 @@ __global__ void k_offset(const float* __restrict__ y, const double* __restrict__
     }
 }
 
-__global__ void k_init_rows(int64_t n_pad, float offset, float* f, float* h, float* c, float* rw)
+__global__ void k_init_rows(int64_t n_pad, float off_hi, float off_lo, float* f, float* h, float* c, float* rw)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_pad; i += (int64_t)gridDim.x * blockDim.x) {
-        f[i] = offset;
-        if (h) h[i] = offset;
+        f[2 * i] = off_hi;
+        f[2 * i + 1] = off_lo;
+        if (h) {
+            h[2 * i] = off_hi;
+            h[2 * i + 1] = off_lo;
+        }
         if (c) c[i] = 0.0f;
         rw[i] = 0.0f;
         rw[n_pad + i] = 0.0f;
@@ -758,17 +775,21 @@ cwb_status setup_model(cwb_model* m, const void* X_in, int x_dtype, const void* 
     }
     if (wd) k_check_weights<<<g_rows, kThreads, 0, s>>>(wd, n, flags + 1);
 
-    // --- y, w in the fitting order
+    // --- y, w in the fitting order (FP64 copies kept for the offset and the counts)
+    double* y64 = nullptr;
+    CWB_TRY(tmp.get(&y64, (size_t)n, s));
+    if (x_dtype == CWB_F64) k_gather_f64<<<g_rows, kThreads, 0, s>>>((const double*)yd, m->perm, n, y64);
+    else k_gather_f64<<<g_rows, kThreads, 0, s>>>((const float*)yd, m->perm, n, y64);
     CWB_TRY(dev_alloc((void**)&m->y, sizeof(float) * n_pad, s));
-    if (x_dtype == CWB_F64) k_gather_to_f32<<<g_rows, kThreads, 0, s>>>((const double*)yd, m->perm, n, n_pad, m->y);
-    else k_gather_to_f32<<<g_rows, kThreads, 0, s>>>((const float*)yd, m->perm, n, n_pad, m->y);
+    if (x_dtype == CWB_F64) CWB_TRY(dev_alloc((void**)&m->y_lo, sizeof(float) * n_pad, s));
+    k_split_f64<<<g_rows, kThreads, 0, s>>>(y64, n, n_pad, m->y, m->y_lo);
     double* w64 = nullptr;
     if (wd) {
         m->weighted = true;
         CWB_TRY(tmp.get(&w64, (size_t)n, s));
         k_gather_f64<<<g_rows, kThreads, 0, s>>>(wd, m->perm, n, w64);
         CWB_TRY(dev_alloc((void**)&m->w, sizeof(float) * n_pad, s));
-        k_gather_to_f32<<<g_rows, kThreads, 0, s>>>(w64, nullptr, n, n_pad, m->w);
+        k_split_f64<<<g_rows, kThreads, 0, s>>>(w64, n, n_pad, m->w, nullptr);
     }
     CWB_CUDA_TRY(cudaGetLastError());
 
@@ -1012,7 +1033,7 @@ cwb_status setup_model(cwb_model* m, const void* X_in, int x_dtype, const void* 
     // --- offset and initial models
     double* off_d = nullptr;
     CWB_TRY(tmp.get(&off_d, 2, s));
-    k_offset<<<1, 1024, 0, s>>>(m->y, w64, m->n_tr, m->cfg.loss, off_d);
+    k_offset<<<1, 1024, 0, s>>>(y64, w64, m->n_tr, m->cfg.loss, off_d);
     double off_h[2] = {0.0, 0.0};
     CWB_CUDA_TRY(cudaMemcpyAsync(off_h, off_d, sizeof(off_h), cudaMemcpyDeviceToHost, s));
     CWB_CUDA_TRY(cudaStreamSynchronize(s));
@@ -1021,13 +1042,15 @@ cwb_status setup_model(cwb_model* m, const void* X_in, int x_dtype, const void* 
         return CWB_EINVAL;
     }
     m->offset = off_h[0];
-    CWB_TRY(dev_alloc((void**)&m->f, sizeof(float) * n_pad, s));
+    CWB_TRY(dev_alloc((void**)&m->f, sizeof(float) * 2 * n_pad, s));
     if (m->accel) {
-        CWB_TRY(dev_alloc((void**)&m->h, sizeof(float) * n_pad, s));
+        CWB_TRY(dev_alloc((void**)&m->h, sizeof(float) * 2 * n_pad, s));
         CWB_TRY(dev_alloc((void**)&m->c, sizeof(float) * n_pad, s));
     }
     CWB_TRY(dev_alloc((void**)&m->rw, sizeof(float) * 2 * n_pad, s));
-    k_init_rows<<<g_rows, kThreads, 0, s>>>(n_pad, (float)m->offset, m->f, m->h, m->c, m->rw);
+    const float off_hi = (float)m->offset;
+    const float off_lo = (float)(m->offset - (double)off_hi);
+    k_init_rows<<<g_rows, kThreads, 0, s>>>(n_pad, off_hi, off_lo, m->f, m->h, m->c, m->rw);
     CWB_CUDA_TRY(cudaGetLastError());
     CWB_CUDA_TRY(cudaStreamSynchronize(s));     // temporaries are released on return
     return CWB_OK;
