@@ -214,11 +214,20 @@ cwb_status cwb_profile(cwb_model* m, int32_t enable);
 /*
  * cwb_get_profile -- accumulated device time (ms) and launch counts per kernel
  * class since profiling was enabled: index 0 = row pass (update / pseudo
- * residuals), 1 = binMatVec scatter, 2 = solve / criterion / argmin.  `ms` and
+ * residuals), 1 = binMatVec scatter, 2 = solve / criterion / argmin, 3 = reduction
+ * of the per-cluster partial histograms.  `ms` and
  * `launches` hold `cap` entries (host memory, either may be NULL).  Synchronises
  * the model's stream.
  */
 cwb_status cwb_get_profile(cwb_model* m, double* ms, int64_t* launches, int32_t cap);
+
+/*
+ * cwb_get_residuals -- the scatter input of the most recent iteration, in the
+ * caller's row order: channel 0 = w * r (pseudo residuals), channel 1 = w * c
+ * (error-corrected residuals, ACWB/HCWB).  Rows outside the fitting set of that
+ * iteration read 0.  `out` holds n FP32 values in host memory.
+ */
+cwb_status cwb_get_residuals(const cwb_model* m, int32_t channel, float* out);
 
 /* cwb_synchronize -- wait for the model's queued work; reports device-side errors. */
 cwb_status cwb_synchronize(cwb_model* m);

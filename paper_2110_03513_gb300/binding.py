@@ -61,6 +61,7 @@ _SIGS = {
     "cwb_get_learner_matrices": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]),
     "cwb_get_bin_index": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     "cwb_force_selection": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
+    "cwb_get_residuals": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     "cwb_synchronize": (C.c_int, [C.c_void_p]),
     "cwb_profile": (C.c_int, [C.c_void_p, C.c_int32]),
     "cwb_get_profile": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
@@ -179,6 +180,10 @@ def cwb_get_bin_index(model, k: int, ind: np.ndarray):
 
 def cwb_force_selection(model, k_forced: np.ndarray):
     _check(load_library().cwb_force_selection(model, _ptr(k_forced), k_forced.size), "cwb_force_selection")
+
+
+def cwb_get_residuals(model, channel: int, out: np.ndarray):
+    _check(load_library().cwb_get_residuals(model, channel, _ptr(out)), "cwb_get_residuals")
 
 
 def cwb_synchronize(model):
@@ -334,10 +339,15 @@ class Model:
         cwb_profile(self.handle, 1 if enable else 0)
 
     def get_profile(self):
-        ms = np.zeros(3)
-        launches = np.zeros(3, dtype=np.int64)
+        ms = np.zeros(4)
+        launches = np.zeros(4, dtype=np.int64)
         cwb_get_profile(self.handle, ms, launches)
-        return {name: (float(ms[i]), int(launches[i])) for i, name in enumerate(("rows", "scatter", "solve"))}
+        return {name: (float(ms[i]), int(launches[i])) for i, name in enumerate(("rows", "scatter", "solve", "reduce"))}
+
+    def residuals(self, channel: int = 0) -> np.ndarray:
+        out = np.zeros(self.n, dtype=np.float32)
+        cwb_get_residuals(self.handle, channel, out)
+        return out
 
     def force_selection(self, ks):
         cwb_force_selection(self.handle, np.ascontiguousarray(ks, dtype=np.int32))

@@ -138,7 +138,7 @@ void free_model(cwb_model* m)
     if (m->stream) cudaStreamSynchronize(m->stream);
     void* bufs[] = {m->ind, m->y, m->y_lo, m->w, m->f, m->h, m->c, m->rw, m->perm, m->zb, m->zb64, m->zcol, m->crange, m->G,
                     m->P, m->lambda, m->l_bin, m->l_d, m->l_nstar, m->l_type, m->l_xmin, m->l_xmax, m->l_degree,
-                    m->l_nknots, m->l_feat, m->part, m->theta_it, m->q_it, m->v, m->state, m->risk_part, m->tr_k,
+                    m->l_nknots, m->l_feat, m->part, m->u, m->cluster_slot, m->slot_c0, m->theta_it, m->q_it, m->v, m->state, m->risk_part, m->tr_k,
                     m->tr_mode, m->tr_theta, m->tr_q, m->forced, m->coef};
     for (void* p : bufs) dev_free(p);
     profile_release(m);
@@ -259,7 +259,8 @@ cwb_status create_impl(const cwb_config* cfg, const void* X, int32_t x_dtype, in
         st = dev_alloc((void**)&m->part, sizeof(float) * std::max<size_t>(m->plan.part_floats, 1), m->stream);
         if (st == CWB_OK) st = dev_alloc((void**)&m->theta_it, sizeof(double) * 2 * K * D, m->stream);
         if (st == CWB_OK) st = dev_alloc((void**)&m->q_it, sizeof(double) * 2 * K, m->stream);
-        if (st == CWB_OK) st = dev_alloc((void**)&m->v, sizeof(float) * (2 * (size_t)S + 2 * (size_t)K * S), m->stream);
+        if (st == CWB_OK) st = dev_alloc((void**)&m->v, sizeof(float) * 2 * (size_t)S, m->stream);
+        if (st == CWB_OK) st = dev_alloc((void**)&m->u, sizeof(float) * 2 * (size_t)m->B * S, m->stream);
         if (st == CWB_OK) st = dev_alloc((void**)&m->state, sizeof(DevState), m->stream);
         if (st == CWB_OK) st = dev_alloc((void**)&m->coef, sizeof(double) * 2 * K * D, m->stream);
         if (st == CWB_OK) st = dev_alloc((void**)&l_feat, sizeof(int32_t) * K, m->stream);
@@ -440,7 +441,7 @@ cwb_status cwb_get_trace(const cwb_model* mc, int32_t* k_sel, int32_t* k_cor, in
         if (k_sel) k_sel[t] = tk[2 * t];
         if (k_cor) k_cor[t] = tk[2 * t + 1];
     }
-    if (switch_iter) *switch_iter = st.switch_iter;
+    if (switch_iter) *switch_iter = (st.switch_iter > 0 && st.switch_iter <= m->done) ? st.switch_iter : 0;
     if (done) *done = m->done;
     return read_device_error(m);
 }
@@ -546,6 +547,24 @@ cwb_status cwb_get_bin_index(const cwb_model* m, int32_t k, int32_t* ind)
     return CWB_OK;
 }
 
+cwb_status cwb_get_residuals(const cwb_model* m, int32_t channel, float* out)
+{
+    set_error("");
+    if (!m || !out || channel < 0 || channel > 1) { set_error("bad argument"); return CWB_EINVAL; }
+    DeviceGuard guard(m->device);
+    std::vector<float> raw(m->n);
+    std::vector<int32_t> perm;
+    CWB_CUDA_TRY(cudaMemcpyAsync(raw.data(), m->rw + (int64_t)channel * m->n_pad, sizeof(float) * m->n,
+                                 cudaMemcpyDeviceToHost, m->stream));
+    if (m->perm) {
+        perm.resize(m->n);
+        CWB_CUDA_TRY(cudaMemcpyAsync(perm.data(), m->perm, sizeof(int32_t) * m->n, cudaMemcpyDeviceToHost, m->stream));
+    }
+    CWB_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    for (int64_t q = 0; q < m->n; ++q) out[m->perm ? perm[q] : q] = raw[q];
+    return CWB_OK;
+}
+
 cwb_status cwb_force_selection(cwb_model* m, const int32_t* k_forced, int32_t count)
 {
     set_error("");
@@ -560,7 +579,7 @@ cwb_status cwb_profile(cwb_model* m, int32_t enable)
     if (!m) { set_error("model is NULL"); return CWB_EINVAL; }
     DeviceGuard guard(m->device);
     CWB_TRY(profile_collect(m));
-    for (int i = 0; i < 3; ++i) {
+    for (int i = 0; i < 4; ++i) {
         m->prof_ms[i] = 0.0;
         m->prof_launches[i] = 0;
     }
@@ -574,7 +593,7 @@ cwb_status cwb_get_profile(cwb_model* m, double* ms, int64_t* launches, int32_t 
     if (!m || cap < 0) { set_error("bad argument"); return CWB_EINVAL; }
     DeviceGuard guard(m->device);
     CWB_TRY(profile_collect(m));
-    for (int i = 0; i < cap && i < 3; ++i) {
+    for (int i = 0; i < cap && i < 4; ++i) {
         if (ms) ms[i] = m->prof_ms[i];
         if (launches) launches[i] = m->prof_launches[i];
     }

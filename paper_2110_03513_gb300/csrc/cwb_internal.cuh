@@ -13,10 +13,12 @@
 //   zcol     [K][S]       int32 first non-zero column of each design point
 //   crange   [K][D][2]    int32 contiguous bin range contributing to each column
 //   G, P     [2][K][D][D] FP64 Gram matrix and cached inverse per phase
-//   part     histogram partials written by the scatter kernel
+//   part     per-cluster histogram partials written by the scatter kernel
+//   u        [2][B][S]    histograms per binning (binMatVec intermediate u)
 //   trace    per iteration: mode, selected learners, FP64 fits, criteria
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -62,17 +64,22 @@ struct DevState {
     double risk_prev;
 };
 
-// Static description of the scatter decomposition.
+// Static description of the scatter decomposition (see k_scatter).
 struct ScatterPlan {
-    int f_lane;       // binnings handled side by side in a warp (lane-private histogram columns)
+    int f_lane;       // binnings side by side in a warp (lane-private histogram columns)
     int groups;       // ceil(B / f_lane)
-    int chunks;       // row chunks
-    int bin_ranges;   // bin sub-ranges (only when one feature's bins do not fit shared memory)
+    int bin_ranges;   // bin sub-ranges (only when one binning's bins do not fit shared memory)
     int nb_cta;       // bins held by one CTA
-    int nbins_pad;    // bins per partial histogram (>= max n*)
+    int nbins_pad;    // bin_ranges * nb_cta (>= max n*)
     int ch_stride;    // shared-memory floats between the two channels' histograms
+    int cmax;         // 1 (CWB) or 2 (ACWB/HCWB: residual and error-corrected residual)
+    int cs;           // thread-block cluster size
+    int clusters;     // clusters in the grid
+    int slots;        // groups * bin_ranges
+    int stages, nb_box, box_bytes, stage_rows;
+    uint32_t ind_off, r_off, hist_off, bar_off, stage_ind_bytes, stage_r_bytes;
     int threads;
-    size_t smem;      // dynamic shared memory bytes
+    size_t smem;      // dynamic shared memory bytes (incl. alignment slack)
     size_t part_floats;
 };
 
@@ -122,7 +129,11 @@ struct cwb_model {
     int32_t *l_bin = nullptr, *l_d = nullptr, *l_nstar = nullptr, *l_type = nullptr;
     double *l_xmin = nullptr, *l_xmax = nullptr;
     int32_t *l_degree = nullptr, *l_nknots = nullptr, *l_feat = nullptr;
-    float* part = nullptr;
+    float* part = nullptr;                // [clusters][cmax][nb_cta * f_lane]
+    float* u = nullptr;                   // [2][B][S] histograms per binning
+    int32_t* cluster_slot = nullptr;      // [clusters]
+    int32_t* slot_c0 = nullptr;           // [slots + 1]
+    CUtensorMap tmap;                     // 2D map of the index matrix [B][n_pad]
     double* theta_it = nullptr;           // [2][K][D]
     double* q_it = nullptr;               // [2][K]
     float* v = nullptr;                   // [2][S]
@@ -144,8 +155,8 @@ struct cwb_model {
     bool prof_on = false;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_pending;
     std::vector<cudaEvent_t> prof_pool;
-    double prof_ms[3] = {0.0, 0.0, 0.0};
-    int64_t prof_launches[3] = {0, 0, 0};
+    double prof_ms[4] = {0.0, 0.0, 0.0, 0.0};
+    int64_t prof_launches[4] = {0, 0, 0, 0};
     // CUDA graph of a fixed block of iterations
     cudaGraphExec_t graph_exec = nullptr;
     int graph_iters = 0;

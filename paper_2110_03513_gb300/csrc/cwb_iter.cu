@@ -17,6 +17,9 @@
 #include <algorithm>
 #include <string>
 
+#include <cooperative_groups.h>
+#include <cuda.h>
+
 #include "cwb_internal.cuh"
 
 namespace cwb {
@@ -25,7 +28,7 @@ namespace {
 
 constexpr int kRowThreads = 256;
 constexpr int kSolveThreads = 256;
-constexpr int kScatterThreads = 512;
+constexpr int kScatterThreads = 288;   // 8 consumer warps + 1 producer warp
 constexpr int kGraphIters = 32;
 
 enum { kRowsFused = 0, kRowsUpdate = 1, kRowsResid = 2 };
@@ -328,42 +331,112 @@ __global__ void __launch_bounds__(kRowThreads) k_rows(RowArgs a)
 }
 
 // ---------------------------------------------------------------------------
-// binMatVec scatter (Algorithm 2).  A CTA owns f_lane binnings x one row chunk
-// (x one bin range).  Lane l of a warp works on binning (l % f_lane), channel
-// and row set (l / f_lane); its histogram column lives at hist[ch][bin][lane's
-// binning], so lanes of one warp never share an address and, for f_lane = 32
-// (or 16 with two channels), never share a bank.
+// binMatVec scatter (Algorithm 2): u_b[l] = sum_{i: ind_b,i = l} w_i r_i.
+//
+// A thread-block cluster of `cs` CTAs owns one slot (F binnings x one bin range)
+// and a contiguous run of row tiles.  Inside a CTA one producer thread streams
+// tiles with TMA: a 2D tiled copy of the uint8/uint16 index matrix (box =
+// 128 bytes of rows x F binnings, 128B-swizzled) and a 1D bulk copy of the
+// matching residual rows, into a ring of `stages` shared-memory buffers guarded
+// by mbarriers.  Consumer warps give every lane its own binning (lane % F),
+// channel and row subset, read 16 bytes of indices from shared memory
+// (conflict-free thanks to the swizzle), the residuals as broadcasts, and add
+// into hist[channel][bin][lane's binning]: lanes of a warp never share an
+// address and, for F = 32 (or F = 16 with two channels), never share a bank.
+// At the end the cluster's histograms are summed through distributed shared
+// memory, each CTA reducing a slice of the bins, and written once per cluster.
+
+namespace cg = cooperative_groups;
 
 struct ScatterArgs {
     const DevState* state;
-    const void* ind;
-    int64_t n, n_tr, n_pad;
     const float* rw;
-    int B, f_lane, groups, chunks, nb_cta, nbins_pad, ch_stride, hybrid;
-    float* part;
+    int64_t n, n_tr, n_pad;
+    int B, F, bin_ranges, nb_cta, ch_stride;
+    int stage_rows, stages, nb_box, box_bytes, unit_rows;
+    int cs;
+    const int32_t* cluster_slot;   // [clusters]
+    const int32_t* slot_c0;        // [slots + 1]: first cluster of each slot
+    int hybrid;
+    uint32_t ind_off, r_off, hist_off, bar_off, stage_ind_bytes, stage_r_bytes;
+    float* part;                   // [clusters][cmax][nb_cta * F]
+    uint32_t* err;
 };
 
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase with the given parity; false once the deadline (SM clock) passed.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long deadline)
+{
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() > deadline) return false;
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_addr(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(dst)), "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz: a stuck pipeline reports an error
+
 template <typename IndT>
-__device__ __forceinline__ void load_ind16(const IndT* p, int64_t i, int out[16]);
+__device__ __forceinline__ void unpack16(uint4 raw, int out[16 / sizeof(IndT)]);
 
 template <>
-__device__ __forceinline__ void load_ind16<uint16_t>(const uint16_t* p, int64_t i, int out[16])
+__device__ __forceinline__ void unpack16<uint16_t>(uint4 raw, int out[8])
 {
-    const uint4* q = reinterpret_cast<const uint4*>(p + i);
-    uint4 a = __ldcs(q), b = __ldcs(q + 1);
-    uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
 #pragma unroll
-    for (int t = 0; t < 8; ++t) {
+    for (int t = 0; t < 4; ++t) {
         out[2 * t] = w[t] & 0xffff;
         out[2 * t + 1] = w[t] >> 16;
     }
 }
 
 template <>
-__device__ __forceinline__ void load_ind16<uint8_t>(const uint8_t* p, int64_t i, int out[16])
+__device__ __forceinline__ void unpack16<uint8_t>(uint4 raw, int out[16])
 {
-    uint4 a = __ldcs(reinterpret_cast<const uint4*>(p + i));
-    uint32_t w[4] = {a.x, a.y, a.z, a.w};
+    uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
         out[4 * t] = w[t] & 0xff;
@@ -374,53 +447,180 @@ __device__ __forceinline__ void load_ind16<uint8_t>(const uint8_t* p, int64_t i,
 }
 
 template <typename IndT, int CMAX>
-__global__ void __launch_bounds__(kScatterThreads) k_scatter(ScatterArgs a)
+__global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_constant__ CUtensorMap tmap, ScatterArgs a)
 {
-    extern __shared__ float hist[];
+    constexpr int U = 16 / sizeof(IndT);                   // rows per 16-byte unit
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int cl = blockIdx.x / a.cs;
+    const int slot = a.cluster_slot[cl];
+    const int g = slot / a.bin_ranges, br = slot % a.bin_ranges;
+    const int ncl = a.slot_c0[slot + 1] - a.slot_c0[slot];
+    const int cin = cl - a.slot_c0[slot];
+
     const int mode = a.state->mode;
     const int C = (CMAX == 2 && mode == kModeACWB) ? 2 : 1;
     const int64_t n_act = (mode == kModeACWB && a.hybrid) ? a.n_tr : a.n;
-    const int64_t n16 = (n_act + 15) & ~(int64_t)15;
-    const int F = a.f_lane;
-    const int chunk = blockIdx.x, g = blockIdx.y, br = blockIdx.z;
+    const int64_t tiles = (n_act + a.stage_rows - 1) / a.stage_rows;
+    const int64_t pieces = (int64_t)ncl * a.cs, piece = (int64_t)cin * a.cs + rank;
+    const int64_t t_lo = tiles * piece / pieces, t_hi = tiles * (piece + 1) / pieces;
+    const int ntiles = (int)(t_hi - t_lo);
+
+    const int F = a.F;
     const int b_lo = br * a.nb_cta;
-    const int nb = min(a.nb_cta, a.nbins_pad - b_lo);
+    float* hist = reinterpret_cast<float*>(smem + a.hist_off);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + a.bar_off);
+    uint64_t* empty = full + a.stages;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int W = (int)(blockDim.x >> 5) - 1;               // consumer warps; warp W produces
 
-    for (int i = threadIdx.x; i < CMAX * a.ch_stride; i += blockDim.x) hist[i] = 0.0f;
+    for (int i = tid; i < CMAX * a.ch_stride; i += blockDim.x) hist[i] = 0.0f;
+    if (tid == 0) {
+        for (int s = 0; s < a.stages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], W);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
     __syncthreads();
+    const long long deadline = clock64() + kWaitCycles;
 
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const int f = lane % F, q = lane / F;
-    const int ch = q % C, rs = q / C;
-    const int RS = 32 / (F * C);
-    const int bidx = g * F + f;
-    const bool active = bidx < a.B;
-    const IndT* row = static_cast<const IndT*>(a.ind) + (int64_t)(active ? bidx : 0) * a.n_pad;
-    const float* r = a.rw + (int64_t)ch * a.n_pad;
-    float* hc = hist + ch * a.ch_stride;
-
-    const int64_t csize = (((n16 + a.chunks - 1) / a.chunks) + 15) & ~(int64_t)15;
-    const int64_t lo = (int64_t)chunk * csize;
-    const int64_t hi = min(lo + csize, n16);
-    for (int64_t row0 = lo + (int64_t)warp * 16 * RS; row0 < hi; row0 += (int64_t)nwarps * 16 * RS) {
-        const int64_t i = row0 + 16 * rs;
-        if (active && i < hi) {
-            int idx[16];
-            load_ind16<IndT>(row, i, idx);
-            const float4* r4p = reinterpret_cast<const float4*>(r + i);
-            float4 r4[4] = {__ldg(r4p), __ldg(r4p + 1), __ldg(r4p + 2), __ldg(r4p + 3)};
-#pragma unroll
-            for (int t = 0; t < 16; ++t) {
-                unsigned bl = (unsigned)(idx[t] - b_lo);
-                if (bl < (unsigned)nb) atomicAdd(&hc[bl * F + f], get4(r4[t >> 2], t & 3));
+    if (warp == W) {
+        if (lane == 0) {
+            const uint32_t bytes = (uint32_t)(a.nb_box * F * 128 + C * a.stage_rows * 4);
+            const int box_rows = 128 / (int)sizeof(IndT);
+            int issued = 0;
+            bool ok = true;
+            for (int it = 0; it < ntiles; ++it) {
+                const int s = it % a.stages;
+                if (it >= a.stages && !mbar_wait(&empty[s], ((it / a.stages) - 1) & 1, deadline)) {
+                    ok = false;
+                    break;
+                }
+                const int64_t row0 = (t_lo + it) * a.stage_rows;
+                mbar_arrive_expect_tx(&full[s], bytes);
+                unsigned char* ind_dst = smem + a.ind_off + (size_t)s * a.stage_ind_bytes;
+                for (int b = 0; b < a.nb_box; ++b)
+                    tma_load_2d(ind_dst + (size_t)b * a.box_bytes, &tmap, (int)(row0 + b * box_rows), g * F, &full[s]);
+                float* r_dst = reinterpret_cast<float*>(smem + a.r_off + (size_t)s * a.stage_r_bytes);
+                for (int ch = 0; ch < C; ++ch)
+                    bulk_load(r_dst + ch * a.stage_rows, a.rw + ch * a.n_pad + row0, (uint32_t)a.stage_rows * 4, &full[s]);
+                ++issued;
             }
+            if (!ok) {
+                atomicOr(a.err, kErrTimeout);
+                // let copies already in flight land before the CTA retires
+                const long long d2 = clock64() + kWaitCycles;
+                for (int it = (issued > a.stages ? issued - a.stages : 0); it < issued; ++it)
+                    mbar_wait(&full[it % a.stages], (it / a.stages) & 1, d2);
+            }
+        }
+    } else {
+        const int q = lane / F;
+        const int f = lane % F;
+        const int ch = q % C, rs = q / C;
+        const int RS = 32 / (F * C);
+        const int bidx = g * F + f;
+        const bool active = bidx < a.B;
+        float* hc = hist + ch * a.ch_stride;
+        const int nunits = a.nb_box * 8;
+        for (int it = 0; it < ntiles; ++it) {
+            const int s = it % a.stages;
+            if (!mbar_wait(&full[s], (it / a.stages) & 1, deadline)) {
+                if (lane == 0) atomicOr(a.err, kErrTimeout);
+                break;
+            }
+            const unsigned char* ind_st = smem + a.ind_off + (size_t)s * a.stage_ind_bytes;
+            const float* r_st = reinterpret_cast<const float*>(smem + a.r_off + (size_t)s * a.stage_r_bytes) + ch * a.stage_rows;
+            for (int wi = warp; wi * RS < nunits; wi += W) {
+                const int u = wi * RS + rs;
+                if (active && u < nunits) {
+                    const int bx = u >> 3, j = u & 7;
+                    const uint4 raw = *reinterpret_cast<const uint4*>(ind_st + (size_t)bx * a.box_bytes + f * 128 +
+                                                                      ((j ^ (f & 7)) << 4));
+                    int idx[U];
+                    unpack16<IndT>(raw, idx);
+                    const float4* rp = reinterpret_cast<const float4*>(r_st + u * U);
+#pragma unroll
+                    for (int t4 = 0; t4 < U / 4; ++t4) {
+                        const float4 r4 = rp[t4];
+#pragma unroll
+                        for (int t = 0; t < 4; ++t) {
+                            const unsigned bl = (unsigned)(idx[4 * t4 + t] - b_lo);
+                            if (bl < (unsigned)a.nb_cta) atomicAdd(&hc[bl * F + f], get4(r4, t));
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);
         }
     }
     __syncthreads();
-    for (int c2 = 0; c2 < C; ++c2) {
-        float* dst = a.part + ((((int64_t)chunk * a.groups + g) * CMAX + c2) * a.nbins_pad + b_lo) * F;
-        const float* src = hist + c2 * a.ch_stride;
-        for (int i = threadIdx.x; i < nb * F; i += blockDim.x) dst[i] = src[i];
+    cluster.sync();
+    // sum the cluster's histograms (fixed rank order), each CTA one slice of the bins
+    const int per = (a.nb_cta + a.cs - 1) / a.cs;
+    const int l0 = min(a.nb_cta, rank * per), l1 = min(a.nb_cta, l0 + per);
+    for (int ch = 0; ch < C; ++ch) {
+        float* dst = a.part + ((int64_t)cl * CMAX + ch) * (int64_t)a.nb_cta * F;
+        for (int e = l0 * F + tid; e < l1 * F; e += blockDim.x) {
+            float acc = 0.0f;
+            for (int r = 0; r < a.cs; ++r) {
+                const float* h = cluster.map_shared_rank(hist, r);
+                acc += h[ch * a.ch_stride + e];
+            }
+            dst[e] = acc;
+        }
+    }
+    cluster.sync();
+}
+
+// u[ch][b][l]: compensated sum over the slot's clusters of the partial histograms,
+// transposed from [bin][binning] to binning-major through shared memory.
+__global__ void __launch_bounds__(256) k_reduce_partials(const DevState* __restrict__ state, const float* __restrict__ part,
+                                                         const int32_t* __restrict__ slot_c0, int B, int F, int bin_ranges,
+                                                         int nb_cta, int cmax, int S, float* __restrict__ u)
+{
+    __shared__ float tile[32][33];
+    const int mode = state->mode;
+    const int C = (cmax == 2 && mode == kModeACWB) ? 2 : 1;
+    const int ch = blockIdx.z;
+    if (ch >= C) return;
+    const int slot = blockIdx.y;
+    const int g = slot / bin_ranges, br = slot % bin_ranges;
+    const int c0 = slot_c0[slot], c1 = slot_c0[slot + 1];
+    const int bin0 = blockIdx.x * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;    // 32 x 8
+    for (int f0 = 0; f0 < F; f0 += 32) {
+        // load: rows = bins (ty + 8k), columns = binnings (tx)
+        for (int k = 0; k < 4; ++k) {
+            const int lb = bin0 + ty + 8 * k;
+            const int f = f0 + tx;
+            float s = 0.0f, comp = 0.0f;
+            if (lb < nb_cta && f < F) {
+                for (int c = c0; c < c1; ++c) {
+                    const float y = __ldcg(part + ((int64_t)c * cmax + ch) * (int64_t)nb_cta * F + (int64_t)lb * F + f) - comp;
+                    const float t = s + y;
+                    comp = (t - s) - y;
+                    s = t;
+                }
+            }
+            tile[ty + 8 * k][tx] = s;
+        }
+        __syncthreads();
+        // store: rows = binnings (ty + 8k), columns = bins (tx)
+        for (int k = 0; k < 4; ++k) {
+            const int f = f0 + ty + 8 * k;
+            const int b = g * F + f;
+            const int lb = bin0 + tx;
+            if (f < F && b < B && lb < nb_cta) {
+                const int l = br * nb_cta + lb;
+                if (l < S) u[((int64_t)ch * B + b) * S + l] = tile[tx][ty + 8 * k];
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -429,10 +629,8 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter(ScatterArgs a)
 
 struct SolveArgs {
     DevState* state;
-    int K, D, S;
-    int f_lane, groups, chunks, nbins_pad, cmax;
-    const float* part;
-    float* u;                 // [2][K][S] scratch
+    int K, D, S, B;
+    const float* u;           // [2][B][S] histograms per binning
     const float* zb;
     const int32_t* zcol;
     const int32_t* crange;
@@ -460,38 +658,21 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(SolveArgs a)
     const int mode = st.mode;
     const int C = (mode == kModeACWB) ? 2 : 1;
     const int ph = (mode == kModeACWB) ? 0 : st.phase;
-    const int b = a.l_bin[k], d = a.l_d[k], nst = a.l_nstar[k];
-    const int F = a.f_lane;
-    const int g = b / F, f = b % F;
+    const int b = a.l_bin[k], d = a.l_d[k];
     __shared__ double s_s[kMaxD], th_s[kMaxD], term[kMaxD];
     __shared__ bool is_last;
-    const int64_t chunk_stride = (int64_t)a.groups * a.cmax * a.nbins_pad * F;
     const double* Pk = a.P + ((int64_t)ph * a.K + k) * a.D * a.D;
     const double* Gk = a.G + ((int64_t)ph * a.K + k) * a.D * a.D;
 
     for (int ch = 0; ch < C; ++ch) {
-        float* u = a.u + ((int64_t)ch * a.K + k) * a.S;
-        // 1. u_l: compensated sum of the per-chunk partial histograms
-        const float* p0 = a.part + ((int64_t)g * a.cmax + ch) * a.nbins_pad * F + f;
-        for (int l = tid; l < nst; l += blockDim.x) {
-            float s = 0.0f, comp = 0.0f;
-            const float* p = p0 + (int64_t)l * F;
-            for (int c = 0; c < a.chunks; ++c) {
-                float y = __ldcg(p + c * chunk_stride) - comp;
-                float t = s + y;
-                comp = (t - s) - y;
-                s = t;
-            }
-            u[l] = s;
-        }
-        __syncthreads();
+        const float* u = a.u + ((int64_t)ch * a.B + b) * a.S;
         // 2. s = Z^b^T u over each column's contiguous bin range (warp tree sums)
         for (int j = warp; j < d; j += blockDim.x / 32) {
             const int lo = a.crange[((int64_t)k * a.D + j) * 2], hi = a.crange[((int64_t)k * a.D + j) * 2 + 1];
             float acc = 0.0f;
             for (int l = lo + lane; l < hi; l += 32) {
                 int c0 = a.zcol[(int64_t)k * a.S + l];
-                acc += a.zb[((int64_t)k * a.S + l) * kMaxNnz + (j - c0)] * u[l];
+                acc += a.zb[((int64_t)k * a.S + l) * kMaxNnz + (j - c0)] * __ldcg(u + l);
             }
             for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
             if (lane == 0) s_s[j] = (double)acc;
@@ -693,37 +874,89 @@ void launch_rows(cwb_model* m, cudaStream_t s)
     else k_rows<KIND, uint16_t><<<g, kRowThreads, 0, s>>>(a);
 }
 
-void launch_scatter(cwb_model* m, cudaStream_t s)
+template <typename IndT, int CMAX>
+cudaError_t launch_scatter_t(cwb_model* m, cudaStream_t s, const ScatterArgs& a)
 {
     const ScatterPlan& P = m->plan;
-    ScatterArgs a{m->state, m->ind, m->n, m->n_tr, m->n_pad, m->rw, m->B, P.f_lane, P.groups, P.chunks,
-                  P.nb_cta, P.nbins_pad, P.ch_stride, m->hybrid ? 1 : 0, m->part};
-    dim3 grid(P.chunks, P.groups, P.bin_ranges);
-    const bool two = m->accel;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(P.clusters * P.cs, 1, 1);
+    cfg.blockDim = dim3(P.threads, 1, 1);
+    cfg.dynamicSmemBytes = P.smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = P.cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_scatter<IndT, CMAX>, m->tmap, a);
+}
+
+ScatterArgs scatter_args(cwb_model* m)
+{
+    const ScatterPlan& P = m->plan;
+    ScatterArgs a;
+    a.state = m->state;
+    a.rw = m->rw;
+    a.n = m->n;
+    a.n_tr = m->n_tr;
+    a.n_pad = m->n_pad;
+    a.B = m->B;
+    a.F = P.f_lane;
+    a.bin_ranges = P.bin_ranges;
+    a.nb_cta = P.nb_cta;
+    a.ch_stride = P.ch_stride;
+    a.stage_rows = P.stage_rows;
+    a.stages = P.stages;
+    a.nb_box = P.nb_box;
+    a.box_bytes = P.box_bytes;
+    a.unit_rows = 16 / m->ind_bytes;
+    a.cs = P.cs;
+    a.cluster_slot = m->cluster_slot;
+    a.slot_c0 = m->slot_c0;
+    a.hybrid = m->hybrid ? 1 : 0;
+    a.ind_off = P.ind_off;
+    a.r_off = P.r_off;
+    a.hist_off = P.hist_off;
+    a.bar_off = P.bar_off;
+    a.stage_ind_bytes = P.stage_ind_bytes;
+    a.stage_r_bytes = P.stage_r_bytes;
+    a.part = m->part;
+    a.err = &m->state->err;
+    return a;
+}
+
+void launch_scatter(cwb_model* m, cudaStream_t s)
+{
+    const ScatterArgs a = scatter_args(m);
+    const bool two = m->plan.cmax == 2;
     if (m->ind_bytes == 1) {
-        if (two) k_scatter<uint8_t, 2><<<grid, P.threads, P.smem, s>>>(a);
-        else k_scatter<uint8_t, 1><<<grid, P.threads, P.smem, s>>>(a);
+        if (two) launch_scatter_t<uint8_t, 2>(m, s, a);
+        else launch_scatter_t<uint8_t, 1>(m, s, a);
     } else {
-        if (two) k_scatter<uint16_t, 2><<<grid, P.threads, P.smem, s>>>(a);
-        else k_scatter<uint16_t, 1><<<grid, P.threads, P.smem, s>>>(a);
+        if (two) launch_scatter_t<uint16_t, 2>(m, s, a);
+        else launch_scatter_t<uint16_t, 1>(m, s, a);
     }
+}
+
+void launch_reduce(cwb_model* m, cudaStream_t s)
+{
+    const ScatterPlan& P = m->plan;
+    dim3 grid((P.nb_cta + 31) / 32, P.slots, P.cmax);
+    k_reduce_partials<<<grid, 256, 0, s>>>(m->state, m->part, m->slot_c0, m->B, P.f_lane, P.bin_ranges, P.nb_cta,
+                                           P.cmax, m->nstar_max, m->u);
 }
 
 void launch_solve(cwb_model* m, cudaStream_t s)
 {
-    const ScatterPlan& P = m->plan;
     SolveArgs a;
     a.state = m->state;
     a.K = m->K;
     a.D = m->d_max;
     a.S = m->nstar_max;
-    a.f_lane = P.f_lane;
-    a.groups = P.groups;
-    a.chunks = P.chunks;
-    a.nbins_pad = P.nbins_pad;
-    a.cmax = m->accel ? 2 : 1;
-    a.part = m->part;
-    a.u = m->v + 2 * (int64_t)m->nstar_max;    // scratch lives after the two update tables
+    a.B = m->B;
+    a.u = m->u;
     a.zb = m->zb;
     a.zcol = m->zcol;
     a.crange = m->crange;
@@ -794,70 +1027,196 @@ void enqueue_iteration(cwb_model* m, cudaStream_t s)
         launch_scatter(m, s);
     }
     {
+        ProfScope p(m, s, 3);
+        launch_reduce(m, s);
+    }
+    {
         ProfScope p(m, s, 2);
         launch_solve(m, s);
     }
 }
 
-cwb_status set_scatter_attrs(cwb_model* m)
+template <typename IndT, int CMAX>
+cwb_status prepare_scatter_kernel(cwb_model* m, int cs, int* active_clusters)
 {
-    const int smem = (int)m->plan.smem;
-    if (m->ind_bytes == 1) {
-        CWB_CUDA_TRY(cudaFuncSetAttribute(k_scatter<uint8_t, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        CWB_CUDA_TRY(cudaFuncSetAttribute(k_scatter<uint8_t, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    } else {
-        CWB_CUDA_TRY(cudaFuncSetAttribute(k_scatter<uint16_t, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        CWB_CUDA_TRY(cudaFuncSetAttribute(k_scatter<uint16_t, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    const ScatterPlan& P = m->plan;
+    CWB_CUDA_TRY(cudaFuncSetAttribute(k_scatter<IndT, CMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs * 64, 1, 1);
+    cfg.blockDim = dim3(P.threads, 1, 1);
+    cfg.dynamicSmemBytes = P.smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    cudaError_t e = cudaOccupancyMaxActiveClusters(&n, k_scatter<IndT, CMAX>, &cfg);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        n = 0;
     }
+    *active_clusters = n;
     return CWB_OK;
+}
+
+cwb_status active_clusters_for(cwb_model* m, int cs, int* n)
+{
+    if (m->ind_bytes == 1) {
+        if (m->plan.cmax == 2) return prepare_scatter_kernel<uint8_t, 2>(m, cs, n);
+        return prepare_scatter_kernel<uint8_t, 1>(m, cs, n);
+    }
+    if (m->plan.cmax == 2) return prepare_scatter_kernel<uint16_t, 2>(m, cs, n);
+    return prepare_scatter_kernel<uint16_t, 1>(m, cs, n);
+}
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        cudaGetLastError();
+    }
+    return fn;
 }
 
 }  // namespace
 
 cwb_status plan_scatter(cwb_model* m)
 {
-    int optin = 0, per_sm = 0;
+    int optin = 0, sms = num_sms(m->device);
     CWB_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, m->device));
-    CWB_CUDA_TRY(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, m->device));
-    const int budget = std::min(optin, 200 * 1024);
+    const int budget = optin - 1024 - 512;          // alignment slack and mbarriers
     const int cmax = m->accel ? 2 : 1;
+    const int elem = m->ind_bytes;
     const int nbins = m->nstar_max;
     const int B = m->B;
     int pow2B = 1;
     while (pow2B < B) pow2B <<= 1;
     ScatterPlan P{};
+    P.cmax = cmax;
+    P.stage_rows = 256;
+    P.nb_box = P.stage_rows / (128 / elem);
     P.bin_ranges = 1;
+    auto ch_stride_for = [&](int nb, int F) {
+        int base = nb * F;
+        int pad = (cmax == 2) ? ((16 - base % 32) + 32) % 32 : 0;
+        return base + pad;
+    };
+    auto hist_bytes = [&](int nb, int F) { return ((cmax * ch_stride_for(nb, F) * 4 + 1023) / 1024) * 1024; };
+    auto stage_bytes = [&](int F) { return P.nb_box * std::max(1024, 128 * F) + cmax * P.stage_rows * 4; };
     P.f_lane = 0;
     for (int F = 32; F >= 1; F >>= 1) {
         if (F * cmax > 32 || F > pow2B) continue;
-        int64_t bytes = (int64_t)cmax * ((int64_t)nbins * F + 32) * 4;
-        if (bytes <= budget) {
+        if (hist_bytes(nbins, F) + 3 * stage_bytes(F) <= budget) {
             P.f_lane = F;
             break;
         }
     }
     if (P.f_lane == 0) {
         P.f_lane = 1;
-        int64_t need = (int64_t)cmax * ((int64_t)nbins + 32) * 4;
-        P.bin_ranges = (int)((need + budget - 1) / budget);
+        while (hist_bytes((nbins + P.bin_ranges - 1) / P.bin_ranges, 1) + 3 * stage_bytes(1) > budget) ++P.bin_ranges;
     }
+    const int F = P.f_lane;
     P.nb_cta = (nbins + P.bin_ranges - 1) / P.bin_ranges;
     P.nbins_pad = P.nb_cta * P.bin_ranges;
-    int base = P.nb_cta * P.f_lane;
-    int pad = (cmax == 2) ? ((16 - base % 32) + 32) % 32 : 0;
-    P.ch_stride = base + pad;
-    P.smem = (size_t)cmax * P.ch_stride * sizeof(float);
-    P.groups = (B + P.f_lane - 1) / P.f_lane;
+    P.ch_stride = ch_stride_for(P.nb_cta, F);
+    P.box_bytes = std::max(1024, 128 * F);
+    P.stage_ind_bytes = (uint32_t)(P.nb_box * P.box_bytes);
+    P.stage_r_bytes = (uint32_t)(cmax * P.stage_rows * 4);
+    const int hb = hist_bytes(P.nb_cta, F);
+    P.stages = std::min(8, (budget - hb) / stage_bytes(F));
+    P.ind_off = 0;
+    P.r_off = P.ind_off + (uint32_t)P.stages * P.stage_ind_bytes;
+    P.hist_off = ((P.r_off + (uint32_t)P.stages * P.stage_r_bytes + 1023) / 1024) * 1024;
+    P.bar_off = P.hist_off + (uint32_t)hb;
+    P.smem = (size_t)P.bar_off + 2 * 8 * P.stages + 1024;
+    P.groups = (B + F - 1) / F;
+    P.slots = P.groups * P.bin_ranges;
     P.threads = kScatterThreads;
-    int by_smem = (int)(per_sm / (P.smem + 1024));
-    int ctas_per_sm = std::max(1, std::min(by_smem, 2048 / P.threads));
-    int target = num_sms(m->device) * ctas_per_sm;
-    int chunks = std::max(1, target / (P.groups * P.bin_ranges));
-    int64_t max_chunks = std::max<int64_t>(1, m->n_pad / 256);
-    P.chunks = (int)std::min<int64_t>(chunks, max_chunks);
-    P.part_floats = (size_t)P.chunks * P.groups * cmax * P.nbins_pad * P.f_lane;
     m->plan = P;
-    return set_scatter_attrs(m);
+
+    // cluster size: the largest that keeps (nearly) every SM busy
+    int best_cs = 1, best_used = 0;
+    for (int cs : {8, 4, 2, 1}) {
+        int act = 0;
+        CWB_TRY(active_clusters_for(m, cs, &act));
+        int used = act * cs;
+        if (used > best_used + sms / 50) {
+            best_used = used;
+            best_cs = cs;
+        }
+    }
+    if (best_used == 0) {
+        set_error("the scatter kernel does not fit on this device");
+        return CWB_ECUDA;
+    }
+    P.cs = best_cs;
+    // clusters per slot in proportion to the binnings the slot holds (at least one each)
+    int total = std::max(best_used / best_cs, P.slots);
+    std::vector<int> per(P.slots, 1);
+    int given = P.slots;
+    std::vector<double> wts(P.slots);
+    double wsum = 0.0;
+    for (int sl = 0; sl < P.slots; ++sl) {
+        int g = sl / P.bin_ranges;
+        wts[sl] = std::min(F, B - g * F);
+        wsum += wts[sl];
+    }
+    for (int sl = 0; sl < P.slots && given < total; ++sl) {
+        int extra = (int)((double)(total - P.slots) * wts[sl] / wsum);
+        extra = std::min(extra, total - given);
+        per[sl] += extra;
+        given += extra;
+    }
+    for (int sl = 0; given < total; sl = (sl + 1) % P.slots) {
+        per[sl] += 1;
+        given += 1;
+    }
+    std::vector<int32_t> slot_c0(P.slots + 1, 0), cl_slot;
+    for (int sl = 0; sl < P.slots; ++sl) {
+        slot_c0[sl + 1] = slot_c0[sl] + per[sl];
+        for (int c = 0; c < per[sl]; ++c) cl_slot.push_back(sl);
+    }
+    P.clusters = (int)cl_slot.size();
+    P.part_floats = (size_t)P.clusters * cmax * P.nb_cta * F;
+    m->plan = P;
+    CWB_TRY(dev_alloc((void**)&m->cluster_slot, sizeof(int32_t) * cl_slot.size(), m->stream));
+    CWB_TRY(dev_alloc((void**)&m->slot_c0, sizeof(int32_t) * slot_c0.size(), m->stream));
+    CWB_CUDA_TRY(cudaMemcpyAsync(m->cluster_slot, cl_slot.data(), sizeof(int32_t) * cl_slot.size(),
+                                 cudaMemcpyHostToDevice, m->stream));
+    CWB_CUDA_TRY(cudaMemcpyAsync(m->slot_c0, slot_c0.data(), sizeof(int32_t) * slot_c0.size(), cudaMemcpyHostToDevice,
+                                 m->stream));
+    CWB_CUDA_TRY(cudaStreamSynchronize(m->stream));
+
+    // tensor map of the index matrix: [B][n_pad] elements, boxes of 128 bytes x F rows, 128B swizzle
+    EncodeTiledFn enc = encode_tiled_fn();
+    if (!enc) {
+        set_error("cuTensorMapEncodeTiled is not available from the driver");
+        return CWB_ECUDA;
+    }
+    cuuint64_t dims[2] = {(cuuint64_t)m->n_pad, (cuuint64_t)B};
+    cuuint64_t strides[1] = {(cuuint64_t)m->n_pad * elem};
+    cuuint32_t box[2] = {(cuuint32_t)(128 / elem), (cuuint32_t)F};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(&m->tmap, elem == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, m->ind,
+                     dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed with code " + std::to_string((int)r));
+        return CWB_ECUDA;
+    }
+    return CWB_OK;
 }
 
 cwb_status ensure_trace(cwb_model* m, int32_t need)

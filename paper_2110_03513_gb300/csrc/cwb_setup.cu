@@ -461,13 +461,6 @@ __device__ void dev_jacobi_eigenvalues(double* A, int d, int ld, double* ev)
     for (int i = 0; i < d; ++i) ev[i] = A[i * ld + i];
 }
 
-__device__ double dev_df_from_eigen(const double* ev, int d, double lambda)
-{
-    double s = 0.0;
-    for (int i = 0; i < d; ++i) s += 1.0 / (1.0 + lambda * ev[i]);
-    return s;
-}
-
 // df1(lambda) = tr((G + lambda K)^-1 G) by its definition (used when G is singular).
 __device__ bool dev_df_direct(const double* G, const double* Kp, int d, int ld, double lambda, double* A, double* L,
                               double* col, double* out)
@@ -499,9 +492,26 @@ struct DroArgs {
     int phases;
 };
 
-// Per learner and phase: penalty K = D^T D, lambda with df1(lambda) = df via the
-// Demmler-Reinsch orthogonalisation (G = L L^T, eigenvalues s_i of L^-1 K L^-T,
-// df1 = sum 1/(1 + lambda s_i)), then P = (G + lambda K)^-1.
+// Per learner and phase: penalty K = D^T D, then lambda with df1(lambda) = df
+// (App. A.2) by a Demmler-Reinsch orthogonalisation set up on the well
+// conditioned matrix C = G + c K (c = tr G / tr K): with C = L L^T the
+// eigenvalues t_i of L^-1 G L^-T lie in [0, 1] and the generalised eigenvalues
+// of (K, G) are s_i = (1 - t_i) / (c t_i), so
+//   df1(lambda) = sum_i 1 / (1 + lambda s_i) = sum_i c t_i / (c t_i + lambda (1 - t_i)).
+// (Factorising G itself loses the small s_i when tail bins are nearly empty.)
+// The root found on that curve is then polished on the definition
+// tr((G + lambda K)^-1 G) with fresh factorisations.  Finally P = (G + lambda K)^-1.
+__device__ double dev_df_dro(const double* t, int d, double c, double lambda)
+{
+    double s = 0.0;
+    for (int i = 0; i < d; ++i) {
+        const double ct = c * t[i];
+        const double den = ct + lambda * (1.0 - t[i]);
+        s += den > 0.0 ? ct / den : 0.0;
+    }
+    return s;
+}
+
 __global__ void k_dro(DroArgs a)
 {
     const int k = blockIdx.x, ph = blockIdx.y;
@@ -518,12 +528,12 @@ __global__ void k_dro(DroArgs a)
     const double* Gs = a.G + ((int64_t)ph * a.K + k) * a.D * a.D;
     for (int i = 0; i < d; ++i)
         for (int j = 0; j < d; ++j) G[i * ld + j] = Gs[i * a.D + j];
-    // penalty: difference matrix of the requested order, K = D^T D
     for (int i = 0; i < d * d; ++i) Kp[i] = 0.0;
     const bool pspline = a.l_type[k] == CWB_BL_PSPLINE;
     int status = 0;
     double lam = 0.0;
     if (pspline) {
+        // difference matrix of the requested order (in M), K = D^T D
         const int ord = a.l_diff[k];
         for (int i = 0; i < d * d; ++i) M[i] = 0.0;
         for (int i = 0; i < d; ++i) M[i * ld + i] = 1.0;
@@ -540,64 +550,65 @@ __global__ void k_dro(DroArgs a)
                 Kp[p * ld + q] = s;
             }
         const double df = a.l_df[k];
+        double trg = 0.0, trk = 0.0;
+        for (int i = 0; i < d; ++i) { trg += G[i * ld + i]; trk += Kp[i * ld + i]; }
+        const double c = trg / trk;
         if (!(df > 0.0)) {
             lam = a.l_lambda[k];
-        } else if (df >= (double)d) {
-            lam = 0.0;
         } else {
-            double trg = 0.0, trk = 0.0;
-            for (int i = 0; i < d; ++i) { trg += G[i * ld + i]; trk += Kp[i * ld + i]; }
-            double c = log10(trg / trk);
-            double lo = c - 20.0, hi = c + 20.0;
-            if (dev_cholesky(G, d, ld, L)) {
-                // M = L^-1 K L^-T: solve L X = K column by column, then L M = X^T
-                for (int j = 0; j < d; ++j) {
+            for (int i = 0; i < d * d; ++i) A[i] = G[i] + c * Kp[i];
+            if (!dev_cholesky(A, d, ld, L)) {
+                status = 1;
+            } else {
+                // M = L^-1 G L^-T: solve L X = G column by column (X in A), then L M = X^T
+                for (int j = 0; j < d; ++j)
                     for (int i = 0; i < d; ++i) {
-                        double t = Kp[i * ld + j];
+                        double t = G[i * ld + j];
                         for (int q = 0; q < i; ++q) t -= L[i * ld + q] * A[q * ld + j];
                         A[i * ld + j] = t / L[i * ld + i];
                     }
-                }
-                for (int j = 0; j < d; ++j) {
+                for (int j = 0; j < d; ++j)
                     for (int i = 0; i < d; ++i) {
-                        double t = A[j * ld + i];          // (X^T)[i][j] = X[j][i]
+                        double t = A[j * ld + i];
                         for (int q = 0; q < i; ++q) t -= L[i * ld + q] * M[q * ld + j];
                         M[i * ld + j] = t / L[i * ld + i];
                     }
-                }
-                for (int i = 0; i < d; ++i)                 // symmetrise rounding
+                for (int i = 0; i < d; ++i)
                     for (int j = i + 1; j < d; ++j) {
                         double s = 0.5 * (M[i * ld + j] + M[j * ld + i]);
                         M[i * ld + j] = s;
                         M[j * ld + i] = s;
                     }
                 dev_jacobi_eigenvalues(M, d, ld, ev);
-                for (int i = 0; i < d; ++i) ev[i] = fmax(ev[i], 0.0);
-                if (dev_df_from_eigen(ev, d, pow(10.0, hi)) > df) {
-                    status = 2;
-                } else if (dev_df_from_eigen(ev, d, pow(10.0, lo)) < df) {
-                    lam = pow(10.0, lo);
+                for (int i = 0; i < d; ++i) ev[i] = fmin(fmax(ev[i], 0.0), 1.0);
+                const double full = dev_df_dro(ev, d, c, 0.0);
+                if (df >= full) {
+                    lam = 0.0;
                 } else {
-                    for (int it = 0; it < 400 && hi - lo >= 1e-15; ++it) {
-                        double mid = 0.5 * (lo + hi);
-                        if (dev_df_from_eigen(ev, d, pow(10.0, mid)) > df) lo = mid; else hi = mid;
+                    const double center = log10(c);
+                    double lo = center - 20.0, hi = center + 20.0;
+                    if (dev_df_dro(ev, d, c, pow(10.0, hi)) > df) {
+                        status = 2;
+                    } else {
+                        for (int it = 0; it < 400 && hi - lo >= 1e-15; ++it) {
+                            double mid = 0.5 * (lo + hi);
+                            if (dev_df_dro(ev, d, c, pow(10.0, mid)) > df) lo = mid; else hi = mid;
+                        }
+                        // polish on the definition in a narrow bracket around the root
+                        double x0 = 0.5 * (lo + hi), v;
+                        double blo = x0 - 1e-3, bhi = x0 + 1e-3;
+                        bool ok_lo = dev_df_direct(G, Kp, d, ld, pow(10.0, blo), A, L, col, &v) && v > df;
+                        bool ok_hi = dev_df_direct(G, Kp, d, ld, pow(10.0, bhi), A, L, col, &v) && v < df;
+                        if (ok_lo && ok_hi) {
+                            for (int it = 0; it < 80 && bhi - blo >= 1e-15; ++it) {
+                                double mid = 0.5 * (blo + bhi);
+                                if (!dev_df_direct(G, Kp, d, ld, pow(10.0, mid), A, L, col, &v)) break;
+                                if (v > df) blo = mid; else bhi = mid;
+                            }
+                            x0 = 0.5 * (blo + bhi);
+                        }
+                        lam = pow(10.0, x0);
                     }
-                    lam = pow(10.0, 0.5 * (lo + hi));
-                }
-            } else {
-                // singular G: root search on the definition, fresh factorisation per step
-                double v;
-                if (!dev_df_direct(G, Kp, d, ld, pow(10.0, hi), A, L, col, &v) || v > df) {
-                    status = 2;
-                } else if (dev_df_direct(G, Kp, d, ld, pow(10.0, lo), A, L, col, &v) && v < df) {
-                    lam = pow(10.0, lo);
-                } else {
-                    for (int it = 0; it < 400 && hi - lo >= 1e-15; ++it) {
-                        double mid = 0.5 * (lo + hi);
-                        if (!dev_df_direct(G, Kp, d, ld, pow(10.0, mid), A, L, col, &v)) { lo = mid; continue; }
-                        if (v > df) lo = mid; else hi = mid;
-                    }
-                    lam = pow(10.0, 0.5 * (lo + hi));
                 }
             }
         }

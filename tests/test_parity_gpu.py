@@ -108,6 +108,24 @@ def test_setup_matches_oracle(cwb, n_bins, n):
     model.free()
 
 
+def test_lambda_on_sparse_tail_bins(cwb):
+    """N(0,1) features: nearly empty tail bins make Z^T Z ill conditioned; lambda must still match."""
+    data = S.sim_binomial_hybrid(seed=30, n=40_000, p=8, n_informative=3)
+    specs = [dict(feature=j, n_bins=-1) for j in range(8)]
+    model = cwb.Model(data.X, data.y, _specs_to_gpu(cwb, specs), loss=1, iterations=1, device=0)
+    for k in range(8):
+        x = data.X[k].astype(np.float64)
+        ind, z = O.bin_equidistant(x, O.isqrt(x.size))
+        G_ref = O.bin_matmat(ind, O.bspline_basis(z, x.min(), x.max(), 3, 20))
+        lam = O.lambda_for_df(G_ref, O.penalty(24, 2), 5.0)
+        info = model.learner_info(k)
+        assert abs(info.lam - lam) <= 1e-9 * lam, (k, info.lam, lam)
+        G, P = model.matrices(k)
+        P_ref = O.spd_inverse(G_ref + lam * O.penalty(24, 2))
+        assert rel_err(P, P_ref) < 1e-8
+    model.free()
+
+
 def test_exact_binning_setup(cwb):
     data = S.sim_small_exact(seed=0, n=3000, p=3)
     X = np.round(data.X * 400) / 400          # repeated values
