@@ -288,6 +288,7 @@ cwb_status create_impl(const cwb_config* cfg, const void* X, int32_t x_dtype, in
             if (e == cudaSuccess) e = cudaMemsetAsync(m->coef, 0, sizeof(double) * 2 * K * D, m->stream);
             if (e != cudaSuccess) st = cuda_status(e, "state init");
         }
+        if (st == CWB_OK) st = scatter_count_pass(m);
         if (st == CWB_OK) st = ensure_trace(m, std::max(cfg->iterations, 1));
         if (st == CWB_OK) st = launch_initial_rows(m);
         if (st == CWB_OK) {

@@ -62,6 +62,8 @@ struct DevState {
     uint32_t ticket_solve;
     uint32_t pad0;
     double risk_prev;
+    uint32_t rmax_bits[2];  // max |w r| and max |w c| of the current iteration (FP32 bits), reset by k_solve
+    int32_t cnt_log2[2];    // ceil(log2(largest per-cluster bin count)): [0] all rows, [1] HCWB training rows
 };
 
 // Static description of the scatter decomposition (see k_scatter).
@@ -81,6 +83,7 @@ struct ScatterPlan {
     int threads;
     size_t smem;      // dynamic shared memory bytes (incl. alignment slack)
     size_t part_floats;
+    bool int_acc;     // exact fixed-point int32 histograms (false: FP32 atomics for heavily skewed bins)
 };
 
 struct HostBinning {
@@ -190,6 +193,7 @@ cwb_status setup_model(cwb_model* m, const void* X, int x_dtype, const void* y, 
 
 // Iterations (cwb_iter.cu)
 cwb_status plan_scatter(cwb_model* m);
+cwb_status scatter_count_pass(cwb_model* m);
 cwb_status ensure_trace(cwb_model* m, int32_t cap);
 cwb_status launch_iterations(cwb_model* m, int32_t iters);
 cwb_status launch_final_update(cwb_model* m);

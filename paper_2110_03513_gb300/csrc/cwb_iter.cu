@@ -16,6 +16,7 @@
 
 #include <algorithm>
 #include <string>
+#include <type_traits>
 
 #include <cooperative_groups.h>
 #include <cuda.h>
@@ -208,6 +209,8 @@ __global__ void __launch_bounds__(kRowThreads) k_rows(RowArgs a)
     const bool eval_risk = (KIND == kRowsUpdate) && a.hybrid && (!st.risk_valid || (pend && pm == kModeACWB));
 
     double risk_acc = 0.0;
+    float rmax0 = 0.0f, rmax1 = 0.0f;
+    bool nonfinite = false;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x * 4;
     for (int64_t i4 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; i4 < a.n_pad; i4 += stride) {
         DF fv[4], hv[4];
@@ -281,6 +284,13 @@ __global__ void __launch_bounds__(kRowThreads) k_rows(RowArgs a)
                     set4(r1, t, wv * cv);
                 }
             }
+            const float m0 = fmaxf(fmaxf(fabsf(r0.x), fabsf(r0.y)), fmaxf(fabsf(r0.z), fabsf(r0.w)));
+            const float m1 = fmaxf(fmaxf(fabsf(r1.x), fabsf(r1.y)), fmaxf(fabsf(r1.z), fabsf(r1.w)));
+            if (!(fabsf(r0.x) + fabsf(r0.y) + fabsf(r0.z) + fabsf(r0.w) + fabsf(r1.x) + fabsf(r1.y) + fabsf(r1.z) +
+                  fabsf(r1.w) <= 3.0e38f))
+                nonfinite = true;
+            rmax0 = fmaxf(rmax0, m0);
+            rmax1 = fmaxf(rmax1, m1);
             *reinterpret_cast<float4*>(a.rw + i4) = r0;
             if (acwb_n) {
                 *reinterpret_cast<float4*>(a.rw + a.n_pad + i4) = r1;
@@ -292,6 +302,18 @@ __global__ void __launch_bounds__(kRowThreads) k_rows(RowArgs a)
     // block partial of the validation risk, then the last block finishes the iteration bookkeeping
     __shared__ double red[kRowThreads];
     __shared__ bool is_last;
+    if (KIND != kRowsUpdate) {
+        // largest |scatter input| per channel: sets the fixed-point scale of the histograms
+        for (int o = 16; o > 0; o >>= 1) {
+            rmax0 = fmaxf(rmax0, __shfl_xor_sync(0xffffffffu, rmax0, o));
+            rmax1 = fmaxf(rmax1, __shfl_xor_sync(0xffffffffu, rmax1, o));
+        }
+        if (__any_sync(0xffffffffu, nonfinite) && (threadIdx.x & 31) == 0) atomicOr(&a.state->err, kErrNonFinite);
+        if ((threadIdx.x & 31) == 0) {
+            atomicMax(&a.state->rmax_bits[0], __float_as_uint(rmax0));
+            if (acwb_n) atomicMax(&a.state->rmax_bits[1], __float_as_uint(rmax1));
+        }
+    }
     red[threadIdx.x] = risk_acc;
     __syncthreads();
     for (int s = kRowThreads / 2; s > 0; s >>= 1) {
@@ -359,8 +381,9 @@ struct ScatterArgs {
     const int32_t* slot_c0;        // [slots + 1]: first cluster of each slot
     int hybrid;
     uint32_t ind_off, r_off, hist_off, bar_off, stage_ind_bytes, stage_r_bytes;
-    float* part;                   // [clusters][cmax][nb_cta * F]
+    float* part;                   // [clusters][cmax][nb_cta * F] (int32 fixed point or FP32)
     uint32_t* err;
+    int64_t count_rows;            // >= 0: counting pass over this many rows (every row adds 1)
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -446,10 +469,22 @@ __device__ __forceinline__ void unpack16<uint8_t>(uint4 raw, int out[16])
     }
 }
 
-template <typename IndT, int CMAX>
+// Fixed-point exponent of a histogram channel: values are w r * 2^s rounded to
+// int32.  With max|w r| < 2^e and at most 2^c rows of one cluster in one bin,
+// s = 30 - c - e keeps every cluster sum below 2^30 in magnitude.
+__device__ __forceinline__ int fixed_scale(uint32_t rmax_bits, int cnt_log2)
+{
+    if (rmax_bits == 0) return 100;
+    const int E = (int)((rmax_bits >> 23) & 0xff);
+    const int e = (E == 0) ? -126 : E - 126;
+    return max(-120, min(100, 30 - cnt_log2 - e));
+}
+
+template <typename IndT, int CMAX, bool INT_ACC>
 __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_constant__ CUtensorMap tmap, ScatterArgs a)
 {
     constexpr int U = 16 / sizeof(IndT);                   // rows per 16-byte unit
+    using Acc = typename std::conditional<INT_ACC, int, float>::type;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     cg::cluster_group cluster = cg::this_cluster();
@@ -460,9 +495,11 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
     const int ncl = a.slot_c0[slot + 1] - a.slot_c0[slot];
     const int cin = cl - a.slot_c0[slot];
 
+    const bool counting = a.count_rows >= 0;
     const int mode = a.state->mode;
-    const int C = (CMAX == 2 && mode == kModeACWB) ? 2 : 1;
-    const int64_t n_act = (mode == kModeACWB && a.hybrid) ? a.n_tr : a.n;
+    const int C = (!counting && CMAX == 2 && mode == kModeACWB) ? 2 : 1;
+    const bool train_rows = a.hybrid && mode == kModeACWB;
+    const int64_t n_act = counting ? a.count_rows : (train_rows ? a.n_tr : a.n);
     const int64_t tiles = (n_act + a.stage_rows - 1) / a.stage_rows;
     const int64_t pieces = (int64_t)ncl * a.cs, piece = (int64_t)cin * a.cs + rank;
     const int64_t t_lo = tiles * piece / pieces, t_hi = tiles * (piece + 1) / pieces;
@@ -470,16 +507,18 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
 
     const int F = a.F;
     const int b_lo = br * a.nb_cta;
-    float* hist = reinterpret_cast<float*>(smem + a.hist_off);
+    Acc* hist = reinterpret_cast<Acc*>(smem + a.hist_off);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + a.bar_off);
-    uint64_t* empty = full + a.stages;
+    uint64_t* ready = full + a.stages;
+    uint64_t* empty = ready + a.stages;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int W = (int)(blockDim.x >> 5) - 1;               // consumer warps; warp W produces
 
-    for (int i = tid; i < CMAX * a.ch_stride; i += blockDim.x) hist[i] = 0.0f;
+    for (int i = tid; i < CMAX * a.ch_stride; i += blockDim.x) hist[i] = Acc(0);
     if (tid == 0) {
         for (int s = 0; s < a.stages; ++s) {
             mbar_init(&full[s], 1);
+            mbar_init(&ready[s], 1);
             mbar_init(&empty[s], W);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -488,34 +527,71 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
     const long long deadline = clock64() + kWaitCycles;
 
     if (warp == W) {
-        if (lane == 0) {
-            const uint32_t bytes = (uint32_t)(a.nb_box * F * 128 + C * a.stage_rows * 4);
-            const int box_rows = 128 / (int)sizeof(IndT);
-            int issued = 0;
-            bool ok = true;
-            for (int it = 0; it < ntiles; ++it) {
-                const int s = it % a.stages;
-                if (it >= a.stages && !mbar_wait(&empty[s], ((it / a.stages) - 1) & 1, deadline)) {
+        // producer warp: lane 0 issues the copies, all lanes convert residual tiles to fixed point
+        float scale[2] = {1.0f, 1.0f};
+        if (INT_ACC && !counting) {
+            const int cidx = train_rows ? 1 : 0;
+            for (int ch = 0; ch < C; ++ch)
+                scale[ch] = ldexpf(1.0f, fixed_scale(a.state->rmax_bits[ch], a.state->cnt_log2[cidx]));
+        }
+        const uint32_t bytes = (uint32_t)(a.nb_box * F * 128 + C * a.stage_rows * 4);
+        const int box_rows = 128 / (int)sizeof(IndT);
+        const int lag = a.stages - 1;
+        int issued = 0;
+        bool ok = true;
+        for (int it = 0; it < ntiles + lag && ok; ++it) {
+            if (it < ntiles) {
+                if (lane == 0) {
+                    const int s = it % a.stages;
+                    if (it >= a.stages && !mbar_wait(&empty[s], ((it / a.stages) - 1) & 1, deadline)) {
+                        ok = false;
+                    } else {
+                        const int64_t row0 = (t_lo + it) * a.stage_rows;
+                        mbar_arrive_expect_tx(&full[s], bytes);
+                        unsigned char* ind_dst = smem + a.ind_off + (size_t)s * a.stage_ind_bytes;
+                        for (int b = 0; b < a.nb_box; ++b)
+                            tma_load_2d(ind_dst + (size_t)b * a.box_bytes, &tmap, (int)(row0 + b * box_rows), g * F,
+                                        &full[s]);
+                        float* r_dst = reinterpret_cast<float*>(smem + a.r_off + (size_t)s * a.stage_r_bytes);
+                        for (int ch = 0; ch < C; ++ch)
+                            bulk_load(r_dst + ch * a.stage_rows, a.rw + ch * a.n_pad + row0,
+                                      (uint32_t)a.stage_rows * 4, &full[s]);
+                        ++issued;
+                    }
+                }
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (!ok) break;
+            }
+            const int jt = it - lag;
+            if (jt >= 0) {
+                const int s = jt % a.stages;
+                if (!__all_sync(0xffffffffu, mbar_wait(&full[s], (jt / a.stages) & 1, deadline))) {
                     ok = false;
                     break;
                 }
-                const int64_t row0 = (t_lo + it) * a.stage_rows;
-                mbar_arrive_expect_tx(&full[s], bytes);
-                unsigned char* ind_dst = smem + a.ind_off + (size_t)s * a.stage_ind_bytes;
-                for (int b = 0; b < a.nb_box; ++b)
-                    tma_load_2d(ind_dst + (size_t)b * a.box_bytes, &tmap, (int)(row0 + b * box_rows), g * F, &full[s]);
-                float* r_dst = reinterpret_cast<float*>(smem + a.r_off + (size_t)s * a.stage_r_bytes);
-                for (int ch = 0; ch < C; ++ch)
-                    bulk_load(r_dst + ch * a.stage_rows, a.rw + ch * a.n_pad + row0, (uint32_t)a.stage_rows * 4, &full[s]);
-                ++issued;
+                if (INT_ACC) {
+                    float* rt = reinterpret_cast<float*>(smem + a.r_off + (size_t)s * a.stage_r_bytes);
+                    int* qt = reinterpret_cast<int*>(rt);
+                    const int64_t row0 = (t_lo + jt) * a.stage_rows;
+                    for (int i = lane; i < C * a.stage_rows; i += 32) {
+                        const int ch = i / a.stage_rows;
+                        int q;
+                        if (counting) q = (row0 + (i % a.stage_rows) < n_act) ? 1 : 0;
+                        else q = __float2int_rn(rt[i] * scale[ch]);
+                        qt[i] = q;
+                    }
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&ready[s]);
             }
-            if (!ok) {
-                atomicOr(a.err, kErrTimeout);
-                // let copies already in flight land before the CTA retires
-                const long long d2 = clock64() + kWaitCycles;
-                for (int it = (issued > a.stages ? issued - a.stages : 0); it < issued; ++it)
-                    mbar_wait(&full[it % a.stages], (it / a.stages) & 1, d2);
-            }
+        }
+        if (!ok && lane == 0) {
+            atomicOr(a.err, kErrTimeout);
+            // let copies already in flight land before the CTA retires
+            const long long d2 = clock64() + kWaitCycles;
+            for (int it = (issued > a.stages ? issued - a.stages : 0); it < issued; ++it)
+                mbar_wait(&full[it % a.stages], (it / a.stages) & 1, d2);
         }
     } else {
         const int q = lane / F;
@@ -524,16 +600,16 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
         const int RS = 32 / (F * C);
         const int bidx = g * F + f;
         const bool active = bidx < a.B;
-        float* hc = hist + ch * a.ch_stride;
+        Acc* hc = hist + ch * a.ch_stride;
         const int nunits = a.nb_box * 8;
         for (int it = 0; it < ntiles; ++it) {
             const int s = it % a.stages;
-            if (!mbar_wait(&full[s], (it / a.stages) & 1, deadline)) {
+            if (!__all_sync(0xffffffffu, mbar_wait(&ready[s], (it / a.stages) & 1, deadline))) {
                 if (lane == 0) atomicOr(a.err, kErrTimeout);
                 break;
             }
             const unsigned char* ind_st = smem + a.ind_off + (size_t)s * a.stage_ind_bytes;
-            const float* r_st = reinterpret_cast<const float*>(smem + a.r_off + (size_t)s * a.stage_r_bytes) + ch * a.stage_rows;
+            const Acc* r_st = reinterpret_cast<const Acc*>(smem + a.r_off + (size_t)s * a.stage_r_bytes) + ch * a.stage_rows;
             for (int wi = warp; wi * RS < nunits; wi += W) {
                 const int u = wi * RS + rs;
                 if (active && u < nunits) {
@@ -542,14 +618,20 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
                                                                       ((j ^ (f & 7)) << 4));
                     int idx[U];
                     unpack16<IndT>(raw, idx);
-                    const float4* rp = reinterpret_cast<const float4*>(r_st + u * U);
 #pragma unroll
                     for (int t4 = 0; t4 < U / 4; ++t4) {
-                        const float4 r4 = rp[t4];
+                        Acc rv[4];
+                        if (INT_ACC) {
+                            const int4 r4 = reinterpret_cast<const int4*>(r_st + u * U)[t4];
+                            rv[0] = r4.x; rv[1] = r4.y; rv[2] = r4.z; rv[3] = r4.w;
+                        } else {
+                            const float4 r4 = reinterpret_cast<const float4*>(r_st + u * U)[t4];
+                            rv[0] = r4.x; rv[1] = r4.y; rv[2] = r4.z; rv[3] = r4.w;
+                        }
 #pragma unroll
                         for (int t = 0; t < 4; ++t) {
                             const unsigned bl = (unsigned)(idx[4 * t4 + t] - b_lo);
-                            if (bl < (unsigned)a.nb_cta) atomicAdd(&hc[bl * F + f], get4(r4, t));
+                            if (bl < (unsigned)a.nb_cta) atomicAdd(&hc[bl * F + f], rv[t]);
                         }
                     }
                 }
@@ -564,11 +646,11 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
     const int per = (a.nb_cta + a.cs - 1) / a.cs;
     const int l0 = min(a.nb_cta, rank * per), l1 = min(a.nb_cta, l0 + per);
     for (int ch = 0; ch < C; ++ch) {
-        float* dst = a.part + ((int64_t)cl * CMAX + ch) * (int64_t)a.nb_cta * F;
+        Acc* dst = reinterpret_cast<Acc*>(a.part) + ((int64_t)cl * CMAX + ch) * (int64_t)a.nb_cta * F;
         for (int e = l0 * F + tid; e < l1 * F; e += blockDim.x) {
-            float acc = 0.0f;
+            Acc acc = Acc(0);
             for (int r = 0; r < a.cs; ++r) {
-                const float* h = cluster.map_shared_rank(hist, r);
+                const Acc* h = cluster.map_shared_rank(hist, r);
                 acc += h[ch * a.ch_stride + e];
             }
             dst[e] = acc;
@@ -577,11 +659,13 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
     cluster.sync();
 }
 
-// u[ch][b][l]: compensated sum over the slot's clusters of the partial histograms,
-// transposed from [bin][binning] to binning-major through shared memory.
+// u[ch][b][l]: sum over the slot's clusters of the partial histograms (exact int64
+// sum of the fixed-point partials, or a compensated FP32 sum), transposed from
+// [bin][binning] to binning-major through shared memory.
+template <bool INT_ACC>
 __global__ void __launch_bounds__(256) k_reduce_partials(const DevState* __restrict__ state, const float* __restrict__ part,
                                                          const int32_t* __restrict__ slot_c0, int B, int F, int bin_ranges,
-                                                         int nb_cta, int cmax, int S, float* __restrict__ u)
+                                                         int nb_cta, int cmax, int S, int hybrid, float* __restrict__ u)
 {
     __shared__ float tile[32][33];
     const int mode = state->mode;
@@ -593,34 +677,61 @@ __global__ void __launch_bounds__(256) k_reduce_partials(const DevState* __restr
     const int c0 = slot_c0[slot], c1 = slot_c0[slot + 1];
     const int bin0 = blockIdx.x * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;    // 32 x 8
-    for (int f0 = 0; f0 < F; f0 += 32) {
-        // load: rows = bins (ty + 8k), columns = binnings (tx)
-        for (int k = 0; k < 4; ++k) {
-            const int lb = bin0 + ty + 8 * k;
-            const int f = f0 + tx;
-            float s = 0.0f, comp = 0.0f;
-            if (lb < nb_cta && f < F) {
+    int sc = 0;
+    if (INT_ACC) sc = fixed_scale(state->rmax_bits[ch], state->cnt_log2[(hybrid && mode == kModeACWB) ? 1 : 0]);
+    for (int k = 0; k < 4; ++k) {
+        const int lb = bin0 + ty + 8 * k;
+        const int f = tx;
+        float val = 0.0f;
+        if (lb < nb_cta && f < F) {
+            const int64_t off = (int64_t)lb * F + f;
+            if (INT_ACC) {
+                const int* pi = reinterpret_cast<const int*>(part);
+                long long acc = 0;
+                for (int c = c0; c < c1; ++c) acc += __ldcg(pi + ((int64_t)c * cmax + ch) * (int64_t)nb_cta * F + off);
+                val = (float)ldexp((double)acc, -sc);
+            } else {
+                float s = 0.0f, comp = 0.0f;
                 for (int c = c0; c < c1; ++c) {
-                    const float y = __ldcg(part + ((int64_t)c * cmax + ch) * (int64_t)nb_cta * F + (int64_t)lb * F + f) - comp;
+                    const float y = __ldcg(part + ((int64_t)c * cmax + ch) * (int64_t)nb_cta * F + off) - comp;
                     const float t = s + y;
                     comp = (t - s) - y;
                     s = t;
                 }
-            }
-            tile[ty + 8 * k][tx] = s;
-        }
-        __syncthreads();
-        // store: rows = binnings (ty + 8k), columns = bins (tx)
-        for (int k = 0; k < 4; ++k) {
-            const int f = f0 + ty + 8 * k;
-            const int b = g * F + f;
-            const int lb = bin0 + tx;
-            if (f < F && b < B && lb < nb_cta) {
-                const int l = br * nb_cta + lb;
-                if (l < S) u[((int64_t)ch * B + b) * S + l] = tile[tx][ty + 8 * k];
+                val = s;
             }
         }
+        tile[ty + 8 * k][tx] = val;
+    }
+    __syncthreads();
+    for (int k = 0; k < 4; ++k) {
+        const int f = ty + 8 * k;
+        const int b = g * F + f;
+        const int lb = bin0 + tx;
+        if (f < F && b < B && lb < nb_cta) {
+            const int l = br * nb_cta + lb;
+            if (l < S) u[((int64_t)ch * B + b) * S + l] = tile[tx][ty + 8 * k];
+        }
+    }
+}
+
+// ceil(log2(largest bin count of any cluster)) from a counting pass of the scatter.
+__global__ void k_count_max(const int* __restrict__ part, int clusters, int cmax, int nbf, DevState* state, int idx)
+{
+    __shared__ int red[1024];
+    int mx = 0;
+    for (int64_t c = 0; c < clusters; ++c)
+        for (int e = threadIdx.x; e < nbf; e += blockDim.x) mx = max(mx, part[(c * cmax) * (int64_t)nbf + e]);
+    red[threadIdx.x] = mx;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] = max(red[threadIdx.x], red[threadIdx.x + s]);
         __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        int l = 0;
+        while ((1 << l) < red[0] && l < 30) ++l;
+        state->cnt_log2[idx] = l;
     }
 }
 
@@ -797,6 +908,8 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(SolveArgs a)
         S->k_cor = (C == 2) ? best_k[1] : -1;
         S->pend_mode = mode;
         S->m = st.m + 1;
+        S->rmax_bits[0] = 0u;
+        S->rmax_bits[1] = 0u;
         S->ticket_solve = 0;
     }
 }
@@ -874,7 +987,7 @@ void launch_rows(cwb_model* m, cudaStream_t s)
     else k_rows<KIND, uint16_t><<<g, kRowThreads, 0, s>>>(a);
 }
 
-template <typename IndT, int CMAX>
+template <typename IndT, int CMAX, bool INT_ACC>
 cudaError_t launch_scatter_t(cwb_model* m, cudaStream_t s, const ScatterArgs& a)
 {
     const ScatterPlan& P = m->plan;
@@ -890,7 +1003,7 @@ cudaError_t launch_scatter_t(cwb_model* m, cudaStream_t s, const ScatterArgs& a)
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_scatter<IndT, CMAX>, m->tmap, a);
+    return cudaLaunchKernelEx(&cfg, k_scatter<IndT, CMAX, INT_ACC>, m->tmap, a);
 }
 
 ScatterArgs scatter_args(cwb_model* m)
@@ -924,28 +1037,36 @@ ScatterArgs scatter_args(cwb_model* m)
     a.stage_r_bytes = P.stage_r_bytes;
     a.part = m->part;
     a.err = &m->state->err;
+    a.count_rows = -1;
     return a;
+}
+
+cudaError_t launch_scatter_args(cwb_model* m, cudaStream_t s, const ScatterArgs& a, bool int_acc)
+{
+    const bool two = m->plan.cmax == 2;
+    if (m->ind_bytes == 1) {
+        if (two) return int_acc ? launch_scatter_t<uint8_t, 2, true>(m, s, a) : launch_scatter_t<uint8_t, 2, false>(m, s, a);
+        return int_acc ? launch_scatter_t<uint8_t, 1, true>(m, s, a) : launch_scatter_t<uint8_t, 1, false>(m, s, a);
+    }
+    if (two) return int_acc ? launch_scatter_t<uint16_t, 2, true>(m, s, a) : launch_scatter_t<uint16_t, 2, false>(m, s, a);
+    return int_acc ? launch_scatter_t<uint16_t, 1, true>(m, s, a) : launch_scatter_t<uint16_t, 1, false>(m, s, a);
 }
 
 void launch_scatter(cwb_model* m, cudaStream_t s)
 {
-    const ScatterArgs a = scatter_args(m);
-    const bool two = m->plan.cmax == 2;
-    if (m->ind_bytes == 1) {
-        if (two) launch_scatter_t<uint8_t, 2>(m, s, a);
-        else launch_scatter_t<uint8_t, 1>(m, s, a);
-    } else {
-        if (two) launch_scatter_t<uint16_t, 2>(m, s, a);
-        else launch_scatter_t<uint16_t, 1>(m, s, a);
-    }
+    launch_scatter_args(m, s, scatter_args(m), m->plan.int_acc);
 }
 
 void launch_reduce(cwb_model* m, cudaStream_t s)
 {
     const ScatterPlan& P = m->plan;
     dim3 grid((P.nb_cta + 31) / 32, P.slots, P.cmax);
-    k_reduce_partials<<<grid, 256, 0, s>>>(m->state, m->part, m->slot_c0, m->B, P.f_lane, P.bin_ranges, P.nb_cta,
-                                           P.cmax, m->nstar_max, m->u);
+    if (P.int_acc)
+        k_reduce_partials<true><<<grid, 256, 0, s>>>(m->state, m->part, m->slot_c0, m->B, P.f_lane, P.bin_ranges,
+                                                     P.nb_cta, P.cmax, m->nstar_max, m->hybrid ? 1 : 0, m->u);
+    else
+        k_reduce_partials<false><<<grid, 256, 0, s>>>(m->state, m->part, m->slot_c0, m->B, P.f_lane, P.bin_ranges,
+                                                      P.nb_cta, P.cmax, m->nstar_max, m->hybrid ? 1 : 0, m->u);
 }
 
 void launch_solve(cwb_model* m, cudaStream_t s)
@@ -1040,7 +1161,8 @@ template <typename IndT, int CMAX>
 cwb_status prepare_scatter_kernel(cwb_model* m, int cs, int* active_clusters)
 {
     const ScatterPlan& P = m->plan;
-    CWB_CUDA_TRY(cudaFuncSetAttribute(k_scatter<IndT, CMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem));
+    CWB_CUDA_TRY(cudaFuncSetAttribute(k_scatter<IndT, CMAX, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem));
+    CWB_CUDA_TRY(cudaFuncSetAttribute(k_scatter<IndT, CMAX, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cs * 64, 1, 1);
     cfg.blockDim = dim3(P.threads, 1, 1);
@@ -1053,7 +1175,7 @@ cwb_status prepare_scatter_kernel(cwb_model* m, int cs, int* active_clusters)
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int n = 0;
-    cudaError_t e = cudaOccupancyMaxActiveClusters(&n, k_scatter<IndT, CMAX>, &cfg);
+    cudaError_t e = cudaOccupancyMaxActiveClusters(&n, k_scatter<IndT, CMAX, true>, &cfg);
     if (e != cudaSuccess) {
         cudaGetLastError();
         n = 0;
@@ -1140,7 +1262,7 @@ cwb_status plan_scatter(cwb_model* m)
     P.r_off = P.ind_off + (uint32_t)P.stages * P.stage_ind_bytes;
     P.hist_off = ((P.r_off + (uint32_t)P.stages * P.stage_r_bytes + 1023) / 1024) * 1024;
     P.bar_off = P.hist_off + (uint32_t)hb;
-    P.smem = (size_t)P.bar_off + 2 * 8 * P.stages + 1024;
+    P.smem = (size_t)P.bar_off + 3 * 8 * P.stages + 1024;
     P.groups = (B + F - 1) / F;
     P.slots = P.groups * P.bin_ranges;
     P.threads = kScatterThreads;
@@ -1216,6 +1338,33 @@ cwb_status plan_scatter(cwb_model* m)
         set_error("cuTensorMapEncodeTiled failed with code " + std::to_string((int)r));
         return CWB_ECUDA;
     }
+    return CWB_OK;
+}
+
+// Counting pass of the scatter (every row adds 1): the largest bin count any
+// cluster accumulates bounds the fixed-point scale; extreme skew (> 8192 rows of
+// one cluster in one bin) selects the FP32 accumulation instead.
+cwb_status scatter_count_pass(cwb_model* m)
+{
+    const ScatterPlan& P = m->plan;
+    const int passes = m->hybrid ? 2 : 1;
+    for (int idx = 0; idx < passes; ++idx) {
+        ScatterArgs a = scatter_args(m);
+        a.count_rows = idx == 1 ? m->n_tr : m->n;
+        CWB_CUDA_TRY(launch_scatter_args(m, m->stream, a, true));
+        k_count_max<<<1, 1024, 0, m->stream>>>(reinterpret_cast<const int*>(m->part), P.clusters, P.cmax,
+                                               P.nb_cta * P.f_lane, m->state, idx);
+        CWB_CUDA_TRY(cudaGetLastError());
+    }
+    DevState st;
+    CWB_CUDA_TRY(cudaMemcpyAsync(&st, m->state, sizeof(st), cudaMemcpyDeviceToHost, m->stream));
+    CWB_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    if (st.err) {
+        set_error("scatter counting pass failed (device error flag " + std::to_string(st.err) + ")");
+        return CWB_ECUDA;
+    }
+    const int worst = std::max(st.cnt_log2[0], passes > 1 ? st.cnt_log2[1] : 0);
+    m->plan.int_acc = worst <= 13;
     return CWB_OK;
 }
 
