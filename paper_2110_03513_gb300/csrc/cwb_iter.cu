@@ -485,8 +485,10 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
 {
     constexpr int U = 16 / sizeof(IndT);                   // rows per 16-byte unit
     using Acc = typename std::conditional<INT_ACC, int, float>::type;
-    extern __shared__ unsigned char smem_raw[];
-    unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // 1024-byte alignment for the swizzled TMA boxes; offsetting the shared array itself keeps
+    // every access below in the shared state space (no generic addressing)
+    unsigned char* smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
     const int cl = blockIdx.x / a.cs;
