@@ -138,7 +138,7 @@ void free_model(cwb_model* m)
     if (m->stream) cudaStreamSynchronize(m->stream);
     void* bufs[] = {m->ind, m->y, m->y_lo, m->w, m->f, m->h, m->c, m->rw, m->perm, m->zb, m->zb64, m->zcol, m->crange, m->G,
                     m->P, m->lambda, m->l_bin, m->l_d, m->l_nstar, m->l_type, m->l_xmin, m->l_xmax, m->l_degree,
-                    m->l_nknots, m->l_feat, m->part, m->u, m->cluster_slot, m->slot_c0, m->theta_it, m->q_it, m->v, m->state, m->risk_part, m->tr_k,
+                    m->l_nknots, m->l_feat, m->part, m->u, m->cluster_slot, m->slot_c0, m->theta_it, m->q_it, m->v, m->state, m->risk_part, m->blk_max, m->tr_k,
                     m->tr_mode, m->tr_theta, m->tr_q, m->forced, m->coef};
     for (void* p : bufs) dev_free(p);
     profile_release(m);
@@ -269,6 +269,7 @@ cwb_status create_impl(const cwb_config* cfg, const void* X, int32_t x_dtype, in
             int sms = 0;
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
             st = dev_alloc((void**)&m->risk_part, sizeof(double) * (size_t)std::max(sms, 1) * 8, m->stream);
+            if (st == CWB_OK) st = dev_alloc((void**)&m->blk_max, sizeof(float) * 2 * (size_t)std::max(sms, 1) * 8, m->stream);
         }
         if (st == CWB_OK) {
             cudaError_t e = cudaMemcpyAsync(l_feat, feat.data(), sizeof(int32_t) * K, cudaMemcpyHostToDevice, m->stream);

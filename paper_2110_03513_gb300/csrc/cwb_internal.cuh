@@ -79,7 +79,7 @@ struct ScatterPlan {
     int clusters;     // clusters in the grid
     int slots;        // groups * bin_ranges
     int stages, nb_box, box_bytes, stage_rows;
-    uint32_t ind_off, r_off, hist_off, bar_off, stage_ind_bytes, stage_r_bytes;
+    uint32_t ind_off, r_off, q_off, hist_off, bar_off, stage_ind_bytes, stage_r_bytes;
     int threads;
     size_t smem;      // dynamic shared memory bytes (incl. alignment slack)
     size_t part_floats;
@@ -142,6 +142,7 @@ struct cwb_model {
     float* v = nullptr;                   // [2][S]
     cwb::DevState* state = nullptr;
     double* risk_part = nullptr;
+    float* blk_max = nullptr;             // [rows grid][2]
     int risk_blocks = 0;
     // trace
     int32_t trace_cap = 0;

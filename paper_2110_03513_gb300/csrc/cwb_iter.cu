@@ -53,6 +53,7 @@ struct RowArgs {
     int hybrid;
     int patience;
     double* risk_part;
+    float* blk_max;       // [grid][2] per-block max |scatter input|
 };
 
 template <typename IndT>
@@ -302,16 +303,30 @@ __global__ void __launch_bounds__(kRowThreads) k_rows(RowArgs a)
     // block partial of the validation risk, then the last block finishes the iteration bookkeeping
     __shared__ double red[kRowThreads];
     __shared__ bool is_last;
+    __shared__ float wmax[2][kRowThreads / 32];
+    __shared__ bool bad_blk;
+    if (threadIdx.x == 0) bad_blk = false;
     if (KIND != kRowsUpdate) {
         // largest |scatter input| per channel: sets the fixed-point scale of the histograms
         for (int o = 16; o > 0; o >>= 1) {
             rmax0 = fmaxf(rmax0, __shfl_xor_sync(0xffffffffu, rmax0, o));
             rmax1 = fmaxf(rmax1, __shfl_xor_sync(0xffffffffu, rmax1, o));
         }
-        if (__any_sync(0xffffffffu, nonfinite) && (threadIdx.x & 31) == 0) atomicOr(&a.state->err, kErrNonFinite);
+        const bool anybad = __any_sync(0xffffffffu, nonfinite);
         if ((threadIdx.x & 31) == 0) {
-            atomicMax(&a.state->rmax_bits[0], __float_as_uint(rmax0));
-            if (acwb_n) atomicMax(&a.state->rmax_bits[1], __float_as_uint(rmax1));
+            wmax[0][threadIdx.x >> 5] = rmax0;
+            wmax[1][threadIdx.x >> 5] = rmax1;
+        }
+        __syncthreads();
+        if (anybad && (threadIdx.x & 31) == 0) bad_blk = true;
+        if (threadIdx.x == 0) {
+            float b0 = 0.0f, b1 = 0.0f;
+            for (int w = 0; w < kRowThreads / 32; ++w) {
+                b0 = fmaxf(b0, wmax[0][w]);
+                b1 = fmaxf(b1, wmax[1][w]);
+            }
+            a.blk_max[2 * blockIdx.x] = b0;
+            a.blk_max[2 * blockIdx.x + 1] = b1;
         }
     }
     red[threadIdx.x] = risk_acc;
@@ -321,6 +336,7 @@ __global__ void __launch_bounds__(kRowThreads) k_rows(RowArgs a)
         __syncthreads();
     }
     if (threadIdx.x == 0) {
+        if (bad_blk) atomicOr(&a.state->err, kErrNonFinite);
         if (a.risk_part) a.risk_part[blockIdx.x] = red[0];
         __threadfence();
         unsigned t = atomicAdd(&a.state->ticket_rows, 1u);
@@ -341,6 +357,15 @@ __global__ void __launch_bounds__(kRowThreads) k_rows(RowArgs a)
                 S->counter = (risk > S->risk_prev) ? S->counter + 1 : 0;
                 S->risk_prev = risk;
             }
+        }
+        if (KIND != kRowsUpdate) {
+            float b0 = 0.0f, b1 = 0.0f;
+            for (int b = 0; b < (int)gridDim.x; ++b) {
+                b0 = fmaxf(b0, __ldcg(a.blk_max + 2 * b));
+                b1 = fmaxf(b1, __ldcg(a.blk_max + 2 * b + 1));
+            }
+            S->rmax_bits[0] = __float_as_uint(b0);
+            S->rmax_bits[1] = acwb_n ? __float_as_uint(b1) : 0u;
         }
         if (KIND == kRowsUpdate && a.hybrid && S->mode == kModeACWB && S->counter >= a.patience) {
             S->mode = kModeCWB;
@@ -380,7 +405,7 @@ struct ScatterArgs {
     const int32_t* cluster_slot;   // [clusters]
     const int32_t* slot_c0;        // [slots + 1]: first cluster of each slot
     int hybrid;
-    uint32_t ind_off, r_off, hist_off, bar_off, stage_ind_bytes, stage_r_bytes;
+    uint32_t ind_off, r_off, q_off, hist_off, bar_off, stage_ind_bytes, stage_r_bytes;
     float* part;                   // [clusters][cmax][nb_cta * F] (int32 fixed point or FP32)
     uint32_t* err;
     int64_t count_rows;            // >= 0: counting pass over this many rows (every row adds 1)
@@ -572,8 +597,10 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
                     break;
                 }
                 if (INT_ACC) {
-                    float* rt = reinterpret_cast<float*>(smem + a.r_off + (size_t)s * a.stage_r_bytes);
-                    int* qt = reinterpret_cast<int*>(rt);
+                    // fixed-point copy into a separate buffer: the TMA landing zone only ever
+                    // sees async-proxy writes and generic reads
+                    const float* rt = reinterpret_cast<const float*>(smem + a.r_off + (size_t)s * a.stage_r_bytes);
+                    int* qt = reinterpret_cast<int*>(smem + a.q_off + (size_t)s * a.stage_r_bytes);
                     const int64_t row0 = (t_lo + jt) * a.stage_rows;
                     for (int i = lane; i < C * a.stage_rows; i += 32) {
                         const int ch = i / a.stage_rows;
@@ -582,7 +609,6 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
                         else q = __float2int_rn(rt[i] * scale[ch]);
                         qt[i] = q;
                     }
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&ready[s]);
@@ -611,7 +637,8 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
                 break;
             }
             const unsigned char* ind_st = smem + a.ind_off + (size_t)s * a.stage_ind_bytes;
-            const Acc* r_st = reinterpret_cast<const Acc*>(smem + a.r_off + (size_t)s * a.stage_r_bytes) + ch * a.stage_rows;
+            const Acc* r_st = reinterpret_cast<const Acc*>(smem + (INT_ACC ? a.q_off : a.r_off) + (size_t)s * a.stage_r_bytes) +
+                              ch * a.stage_rows;
             for (int wi = warp; wi * RS < nunits; wi += W) {
                 const int u = wi * RS + rs;
                 if (active && u < nunits) {
@@ -662,14 +689,16 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
 }
 
 // u[ch][b][l]: sum over the slot's clusters of the partial histograms (exact int64
-// sum of the fixed-point partials, or a compensated FP32 sum), transposed from
-// [bin][binning] to binning-major through shared memory.
+// sum of the fixed-point partials, or a compensated FP32 sum).  A block covers 64
+// consecutive [bin][binning] entries of one slot and channel; its four thread rows
+// split the clusters and meet in shared memory.
 template <bool INT_ACC>
 __global__ void __launch_bounds__(256) k_reduce_partials(const DevState* __restrict__ state, const float* __restrict__ part,
                                                          const int32_t* __restrict__ slot_c0, int B, int F, int bin_ranges,
                                                          int nb_cta, int cmax, int S, int hybrid, float* __restrict__ u)
 {
-    __shared__ float tile[32][33];
+    __shared__ long long acc_i[4][64];
+    __shared__ float acc_f[4][64];
     const int mode = state->mode;
     const int C = (cmax == 2 && mode == kModeACWB) ? 2 : 1;
     const int ch = blockIdx.z;
@@ -677,43 +706,49 @@ __global__ void __launch_bounds__(256) k_reduce_partials(const DevState* __restr
     const int slot = blockIdx.y;
     const int g = slot / bin_ranges, br = slot % bin_ranges;
     const int c0 = slot_c0[slot], c1 = slot_c0[slot + 1];
-    const int bin0 = blockIdx.x * 32;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;    // 32 x 8
-    int sc = 0;
-    if (INT_ACC) sc = fixed_scale(state->rmax_bits[ch], state->cnt_log2[(hybrid && mode == kModeACWB) ? 1 : 0]);
-    for (int k = 0; k < 4; ++k) {
-        const int lb = bin0 + ty + 8 * k;
-        const int f = tx;
-        float val = 0.0f;
-        if (lb < nb_cta && f < F) {
-            const int64_t off = (int64_t)lb * F + f;
-            if (INT_ACC) {
-                const int* pi = reinterpret_cast<const int*>(part);
-                long long acc = 0;
-                for (int c = c0; c < c1; ++c) acc += __ldcg(pi + ((int64_t)c * cmax + ch) * (int64_t)nb_cta * F + off);
-                val = (float)ldexp((double)acc, -sc);
-            } else {
-                float s = 0.0f, comp = 0.0f;
-                for (int c = c0; c < c1; ++c) {
-                    const float y = __ldcg(part + ((int64_t)c * cmax + ch) * (int64_t)nb_cta * F + off) - comp;
-                    const float t = s + y;
-                    comp = (t - s) - y;
-                    s = t;
-                }
-                val = s;
+    const int nbf = nb_cta * F;
+    const int e = blockIdx.x * 64 + (threadIdx.x & 63);
+    const int part_row = threadIdx.x >> 6;          // 0..3
+    if (INT_ACC) {
+        const int* pi = reinterpret_cast<const int*>(part);
+        long long acc = 0;
+        if (e < nbf) {
+            int c = c0 + part_row;
+            for (; c + 12 < c1; c += 16) {
+                const int v0 = __ldcg(pi + ((int64_t)c * cmax + ch) * nbf + e);
+                const int v1 = __ldcg(pi + ((int64_t)(c + 4) * cmax + ch) * nbf + e);
+                const int v2 = __ldcg(pi + ((int64_t)(c + 8) * cmax + ch) * nbf + e);
+                const int v3 = __ldcg(pi + ((int64_t)(c + 12) * cmax + ch) * nbf + e);
+                acc += (long long)v0 + v1 + v2 + v3;
             }
+            for (; c < c1; c += 4) acc += __ldcg(pi + ((int64_t)c * cmax + ch) * nbf + e);
         }
-        tile[ty + 8 * k][tx] = val;
+        acc_i[part_row][threadIdx.x & 63] = acc;
+    } else {
+        float s = 0.0f, comp = 0.0f;
+        if (e < nbf)
+            for (int c = c0 + part_row; c < c1; c += 4) {
+                const float y = __ldcg(part + ((int64_t)c * cmax + ch) * nbf + e) - comp;
+                const float t = s + y;
+                comp = (t - s) - y;
+                s = t;
+            }
+        acc_f[part_row][threadIdx.x & 63] = s;
     }
     __syncthreads();
-    for (int k = 0; k < 4; ++k) {
-        const int f = ty + 8 * k;
-        const int b = g * F + f;
-        const int lb = bin0 + tx;
-        if (f < F && b < B && lb < nb_cta) {
-            const int l = br * nb_cta + lb;
-            if (l < S) u[((int64_t)ch * B + b) * S + l] = tile[tx][ty + 8 * k];
+    if (threadIdx.x < 64 && e < nbf) {
+        float val;
+        if (INT_ACC) {
+            const long long tot = acc_i[0][threadIdx.x] + acc_i[1][threadIdx.x] + acc_i[2][threadIdx.x] + acc_i[3][threadIdx.x];
+            const int sc = fixed_scale(state->rmax_bits[ch], state->cnt_log2[(hybrid && mode == kModeACWB) ? 1 : 0]);
+            val = (float)ldexp((double)tot, -sc);
+        } else {
+            val = (acc_f[0][threadIdx.x] + acc_f[1][threadIdx.x]) + (acc_f[2][threadIdx.x] + acc_f[3][threadIdx.x]);
         }
+        const int lb = e / F, f = e % F;
+        const int b = g * F + f;
+        const int l = br * nb_cta + lb;
+        if (b < B && l < S) u[((int64_t)ch * B + b) * S + l] = val;
     }
 }
 
@@ -949,7 +984,7 @@ int num_sms(int device)
 int rows_grid(const cwb_model* m)
 {
     int64_t g = (m->n_pad / 4 + kRowThreads - 1) / kRowThreads;
-    int64_t cap = (int64_t)num_sms(m->device) * 8;
+    int64_t cap = (int64_t)num_sms(m->device) * 4;
     return (int)std::max<int64_t>(1, std::min(g, cap));
 }
 
@@ -977,6 +1012,7 @@ RowArgs row_args(cwb_model* m)
     a.hybrid = m->hybrid ? 1 : 0;
     a.patience = m->cfg.patience;
     a.risk_part = m->risk_part;
+    a.blk_max = m->blk_max;
     return a;
 }
 
@@ -1033,6 +1069,7 @@ ScatterArgs scatter_args(cwb_model* m)
     a.hybrid = m->hybrid ? 1 : 0;
     a.ind_off = P.ind_off;
     a.r_off = P.r_off;
+    a.q_off = P.q_off;
     a.hist_off = P.hist_off;
     a.bar_off = P.bar_off;
     a.stage_ind_bytes = P.stage_ind_bytes;
@@ -1062,7 +1099,7 @@ void launch_scatter(cwb_model* m, cudaStream_t s)
 void launch_reduce(cwb_model* m, cudaStream_t s)
 {
     const ScatterPlan& P = m->plan;
-    dim3 grid((P.nb_cta + 31) / 32, P.slots, P.cmax);
+    dim3 grid((P.nb_cta * P.f_lane + 63) / 64, P.slots, P.cmax);
     if (P.int_acc)
         k_reduce_partials<true><<<grid, 256, 0, s>>>(m->state, m->part, m->slot_c0, m->B, P.f_lane, P.bin_ranges,
                                                      P.nb_cta, P.cmax, m->nstar_max, m->hybrid ? 1 : 0, m->u);
@@ -1238,7 +1275,7 @@ cwb_status plan_scatter(cwb_model* m)
         return base + pad;
     };
     auto hist_bytes = [&](int nb, int F) { return ((cmax * ch_stride_for(nb, F) * 4 + 1023) / 1024) * 1024; };
-    auto stage_bytes = [&](int F) { return P.nb_box * std::max(1024, 128 * F) + cmax * P.stage_rows * 4; };
+    auto stage_bytes = [&](int F) { return P.nb_box * std::max(1024, 128 * F) + 2 * cmax * P.stage_rows * 4; };
     P.f_lane = 0;
     for (int F = 32; F >= 1; F >>= 1) {
         if (F * cmax > 32 || F > pow2B) continue;
@@ -1262,7 +1299,8 @@ cwb_status plan_scatter(cwb_model* m)
     P.stages = std::min(8, (budget - hb) / stage_bytes(F));
     P.ind_off = 0;
     P.r_off = P.ind_off + (uint32_t)P.stages * P.stage_ind_bytes;
-    P.hist_off = ((P.r_off + (uint32_t)P.stages * P.stage_r_bytes + 1023) / 1024) * 1024;
+    P.q_off = P.r_off + (uint32_t)P.stages * P.stage_r_bytes;
+    P.hist_off = ((P.q_off + (uint32_t)P.stages * P.stage_r_bytes + 1023) / 1024) * 1024;
     P.bar_off = P.hist_off + (uint32_t)hb;
     P.smem = (size_t)P.bar_off + 3 * 8 * P.stages + 1024;
     P.groups = (B + F - 1) / F;
