@@ -381,17 +381,19 @@ __global__ void __launch_bounds__(kRowThreads) k_rows(RowArgs a)
 // binMatVec scatter (Algorithm 2): u_b[l] = sum_{i: ind_b,i = l} w_i r_i.
 //
 // A thread-block cluster of `cs` CTAs owns one slot (F binnings x one bin range)
-// and a contiguous run of row tiles.  Inside a CTA one producer thread streams
-// tiles with TMA: a 2D tiled copy of the uint8/uint16 index matrix (box =
-// 128 bytes of rows x F binnings, 128B-swizzled) and a 1D bulk copy of the
-// matching residual rows, into a ring of `stages` shared-memory buffers guarded
-// by mbarriers.  Consumer warps give every lane its own binning (lane % F),
-// channel and row subset, read 16 bytes of indices from shared memory
-// (conflict-free thanks to the swizzle), the residuals as broadcasts, and add
-// into hist[channel][bin][lane's binning]: lanes of a warp never share an
-// address and, for F = 32 (or F = 16 with two channels), never share a bank.
-// At the end the cluster's histograms are summed through distributed shared
-// memory, each CTA reducing a slice of the bins, and written once per cluster.
+// and a contiguous run of 256-row tiles.  Inside a CTA one producer warp streams
+// tiles with TMA: a 2D tiled copy of the uint8/uint16 index matrix (box = the
+// tile's 256 rows x F binnings, one contiguous row per binning) and a 1D bulk
+// copy of the matching residual rows, into a ring of `stages` shared-memory
+// buffers guarded by mbarriers; it then converts the residual tile to fixed
+// point (see fixed_scale).  Consumer warps give every lane its own binning
+// (lane % F), channel and row subset; lanes start at different 16-byte units
+// of their rows so a warp's reads cover all banks, and they add into
+// hist[channel][bin][lane's binning] with int32 shared-memory atomics: lanes of
+// a warp never share an address and, for F = 32 (or F = 16 with two channels),
+// never share a bank.  At the end the cluster's histograms are summed through
+// distributed shared memory, each CTA reducing a slice of the bins, and written
+// once per cluster.
 
 namespace cg = cooperative_groups;
 
@@ -561,8 +563,7 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
             for (int ch = 0; ch < C; ++ch)
                 scale[ch] = ldexpf(1.0f, fixed_scale(a.state->rmax_bits[ch], a.state->cnt_log2[cidx]));
         }
-        const uint32_t bytes = (uint32_t)(a.nb_box * F * 128 + C * a.stage_rows * 4);
-        const int box_rows = 128 / (int)sizeof(IndT);
+        const uint32_t bytes = (uint32_t)(F * a.stage_rows * (int)sizeof(IndT) + C * a.stage_rows * 4);
         const int lag = a.stages - 1;
         int issued = 0;
         bool ok = true;
@@ -576,9 +577,7 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
                         const int64_t row0 = (t_lo + it) * a.stage_rows;
                         mbar_arrive_expect_tx(&full[s], bytes);
                         unsigned char* ind_dst = smem + a.ind_off + (size_t)s * a.stage_ind_bytes;
-                        for (int b = 0; b < a.nb_box; ++b)
-                            tma_load_2d(ind_dst + (size_t)b * a.box_bytes, &tmap, (int)(row0 + b * box_rows), g * F,
-                                        &full[s]);
+                        tma_load_2d(ind_dst, &tmap, (int)row0, g * F, &full[s]);
                         float* r_dst = reinterpret_cast<float*>(smem + a.r_off + (size_t)s * a.stage_r_bytes);
                         for (int ch = 0; ch < C; ++ch)
                             bulk_load(r_dst + ch * a.stage_rows, a.rw + ch * a.n_pad + row0,
@@ -629,7 +628,8 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
         const int bidx = g * F + f;
         const bool active = bidx < a.B;
         Acc* hc = hist + ch * a.ch_stride;
-        const int nunits = a.nb_box * 8;
+        const int row_bytes = a.stage_rows * (int)sizeof(IndT);   // one binning's rows of a tile
+        const int nunits = row_bytes / 16;
         for (int it = 0; it < ntiles; ++it) {
             const int s = it % a.stages;
             if (!__all_sync(0xffffffffu, mbar_wait(&ready[s], (it / a.stages) & 1, deadline))) {
@@ -642,19 +642,20 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
             for (int wi = warp; wi * RS < nunits; wi += W) {
                 const int u = wi * RS + rs;
                 if (active && u < nunits) {
-                    const int bx = u >> 3, j = u & 7;
-                    const uint4 raw = *reinterpret_cast<const uint4*>(ind_st + (size_t)bx * a.box_bytes + f * 128 +
-                                                                      ((j ^ (f & 7)) << 4));
+                    // lanes start at different 16-byte units of their rows (rotation by the lane's
+                    // binning) so the 32 reads of a warp spread over all banks
+                    const int pos = (u + f) & (nunits - 1);
+                    const uint4 raw = *reinterpret_cast<const uint4*>(ind_st + (size_t)f * row_bytes + (pos << 4));
                     int idx[U];
                     unpack16<IndT>(raw, idx);
 #pragma unroll
                     for (int t4 = 0; t4 < U / 4; ++t4) {
                         Acc rv[4];
                         if (INT_ACC) {
-                            const int4 r4 = reinterpret_cast<const int4*>(r_st + u * U)[t4];
+                            const int4 r4 = reinterpret_cast<const int4*>(r_st + pos * U)[t4];
                             rv[0] = r4.x; rv[1] = r4.y; rv[2] = r4.z; rv[3] = r4.w;
                         } else {
-                            const float4 r4 = reinterpret_cast<const float4*>(r_st + u * U)[t4];
+                            const float4 r4 = reinterpret_cast<const float4*>(r_st + pos * U)[t4];
                             rv[0] = r4.x; rv[1] = r4.y; rv[2] = r4.z; rv[3] = r4.w;
                         }
 #pragma unroll
@@ -1267,7 +1268,7 @@ cwb_status plan_scatter(cwb_model* m)
     ScatterPlan P{};
     P.cmax = cmax;
     P.stage_rows = 256;
-    P.nb_box = P.stage_rows / (128 / elem);
+    P.nb_box = 1;
     P.bin_ranges = 1;
     auto ch_stride_for = [&](int nb, int F) {
         int base = nb * F;
@@ -1275,7 +1276,7 @@ cwb_status plan_scatter(cwb_model* m)
         return base + pad;
     };
     auto hist_bytes = [&](int nb, int F) { return ((cmax * ch_stride_for(nb, F) * 4 + 1023) / 1024) * 1024; };
-    auto stage_bytes = [&](int F) { return P.nb_box * std::max(1024, 128 * F) + 2 * cmax * P.stage_rows * 4; };
+    auto stage_bytes = [&](int F) { return ((F * P.stage_rows * elem + 127) / 128) * 128 + 2 * cmax * P.stage_rows * 4; };
     P.f_lane = 0;
     for (int F = 32; F >= 1; F >>= 1) {
         if (F * cmax > 32 || F > pow2B) continue;
@@ -1292,8 +1293,8 @@ cwb_status plan_scatter(cwb_model* m)
     P.nb_cta = (nbins + P.bin_ranges - 1) / P.bin_ranges;
     P.nbins_pad = P.nb_cta * P.bin_ranges;
     P.ch_stride = ch_stride_for(P.nb_cta, F);
-    P.box_bytes = std::max(1024, 128 * F);
-    P.stage_ind_bytes = (uint32_t)(P.nb_box * P.box_bytes);
+    P.box_bytes = ((F * P.stage_rows * elem + 127) / 128) * 128;
+    P.stage_ind_bytes = (uint32_t)P.box_bytes;
     P.stage_r_bytes = (uint32_t)(cmax * P.stage_rows * 4);
     const int hb = hist_bytes(P.nb_cta, F);
     P.stages = std::min(8, (budget - hb) / stage_bytes(F));
@@ -1361,7 +1362,7 @@ cwb_status plan_scatter(cwb_model* m)
                                  m->stream));
     CWB_CUDA_TRY(cudaStreamSynchronize(m->stream));
 
-    // tensor map of the index matrix: [B][n_pad] elements, boxes of 128 bytes x F rows, 128B swizzle
+    // tensor map of the index matrix: [B][n_pad] elements, boxes of one tile's rows x F binnings
     EncodeTiledFn enc = encode_tiled_fn();
     if (!enc) {
         set_error("cuTensorMapEncodeTiled is not available from the driver");
@@ -1369,10 +1370,10 @@ cwb_status plan_scatter(cwb_model* m)
     }
     cuuint64_t dims[2] = {(cuuint64_t)m->n_pad, (cuuint64_t)B};
     cuuint64_t strides[1] = {(cuuint64_t)m->n_pad * elem};
-    cuuint32_t box[2] = {(cuuint32_t)(128 / elem), (cuuint32_t)F};
+    cuuint32_t box[2] = {(cuuint32_t)P.stage_rows, (cuuint32_t)F};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = enc(&m->tmap, elem == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, m->ind,
-                     dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         set_error("cuTensorMapEncodeTiled failed with code " + std::to_string((int)r));
