@@ -70,6 +70,7 @@ struct DevState {
 struct ScatterPlan {
     int f_lane;       // binnings side by side in a warp (lane-private histogram columns)
     int groups;       // ceil(B / f_lane)
+    int fe;           // binnings per group actually streamed (balanced, <= f_lane)
     int bin_ranges;   // bin sub-ranges (only when one binning's bins do not fit shared memory)
     int nb_cta;       // bins held by one CTA
     int nbins_pad;    // bin_ranges * nb_cta (>= max n*)

@@ -29,7 +29,7 @@ namespace {
 
 constexpr int kRowThreads = 256;
 constexpr int kSolveThreads = 256;
-constexpr int kScatterThreads = 288;   // 8 consumer warps + 1 producer warp
+constexpr int kScatterThreads = 320;   // 8 consumer warps + 1 loader warp + 1 converter warp
 constexpr int kGraphIters = 32;
 
 enum { kRowsFused = 0, kRowsUpdate = 1, kRowsResid = 2 };
@@ -401,7 +401,7 @@ struct ScatterArgs {
     const DevState* state;
     const float* rw;
     int64_t n, n_tr, n_pad;
-    int B, F, bin_ranges, nb_cta, ch_stride;
+    int B, F, FE, bin_ranges, nb_cta, ch_stride;
     int stage_rows, stages, nb_box, box_bytes, unit_rows;
     int cs;
     const int32_t* cluster_slot;   // [clusters]
@@ -511,10 +511,11 @@ template <typename IndT, int CMAX, bool INT_ACC>
 __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_constant__ CUtensorMap tmap, ScatterArgs a)
 {
     constexpr int U = 16 / sizeof(IndT);                   // rows per 16-byte unit
+    constexpr int UN = sizeof(IndT) == 2 ? 4 : 2;          // units in flight per lane
     using Acc = typename std::conditional<INT_ACC, int, float>::type;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    // 1024-byte alignment for the swizzled TMA boxes; offsetting the shared array itself keeps
-    // every access below in the shared state space (no generic addressing)
+    // 1024-byte alignment of the ring; offsetting the shared array itself keeps every
+    // access below in the shared state space (no generic addressing)
     unsigned char* smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
@@ -534,14 +535,16 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
     const int64_t t_lo = tiles * piece / pieces, t_hi = tiles * (piece + 1) / pieces;
     const int ntiles = (int)(t_hi - t_lo);
 
-    const int F = a.F;
+    const int F = a.F;                  // lanes per channel and row set (power of two)
+    const int FE = a.FE;                // binnings of this group held in the ring (<= F)
     const int b_lo = br * a.nb_cta;
+    const int row_bytes = a.stage_rows * (int)sizeof(IndT);
     Acc* hist = reinterpret_cast<Acc*>(smem + a.hist_off);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + a.bar_off);
     uint64_t* ready = full + a.stages;
     uint64_t* empty = ready + a.stages;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int W = (int)(blockDim.x >> 5) - 1;               // consumer warps; warp W produces
+    const int W = (int)(blockDim.x >> 5) - 2;               // consumer warps; warp W loads, warp W+1 converts
 
     for (int i = tid; i < CMAX * a.ch_stride; i += blockDim.x) hist[i] = Acc(0);
     if (tid == 0) {
@@ -556,112 +559,117 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
     const long long deadline = clock64() + kWaitCycles;
 
     if (warp == W) {
-        // producer warp: lane 0 issues the copies, all lanes convert residual tiles to fixed point
-        float scale[2] = {1.0f, 1.0f};
-        if (INT_ACC && !counting) {
-            const int cidx = train_rows ? 1 : 0;
-            for (int ch = 0; ch < C; ++ch)
-                scale[ch] = ldexpf(1.0f, fixed_scale(a.state->rmax_bits[ch], a.state->cnt_log2[cidx]));
-        }
-        const uint32_t bytes = (uint32_t)(F * a.stage_rows * (int)sizeof(IndT) + C * a.stage_rows * 4);
-        const int lag = a.stages - 1;
-        int issued = 0;
-        bool ok = true;
-        for (int it = 0; it < ntiles + lag && ok; ++it) {
-            if (it < ntiles) {
-                if (lane == 0) {
-                    const int s = it % a.stages;
-                    if (it >= a.stages && !mbar_wait(&empty[s], ((it / a.stages) - 1) & 1, deadline)) {
-                        ok = false;
-                    } else {
-                        const int64_t row0 = (t_lo + it) * a.stage_rows;
-                        mbar_arrive_expect_tx(&full[s], bytes);
-                        unsigned char* ind_dst = smem + a.ind_off + (size_t)s * a.stage_ind_bytes;
-                        tma_load_2d(ind_dst, &tmap, (int)row0, g * F, &full[s]);
-                        float* r_dst = reinterpret_cast<float*>(smem + a.r_off + (size_t)s * a.stage_r_bytes);
-                        for (int ch = 0; ch < C; ++ch)
-                            bulk_load(r_dst + ch * a.stage_rows, a.rw + ch * a.n_pad + row0,
-                                      (uint32_t)a.stage_rows * 4, &full[s]);
-                        ++issued;
-                    }
-                }
-                ok = __shfl_sync(0xffffffffu, ok, 0);
-                if (!ok) break;
-            }
-            const int jt = it - lag;
-            if (jt >= 0) {
-                const int s = jt % a.stages;
-                if (!__all_sync(0xffffffffu, mbar_wait(&full[s], (jt / a.stages) & 1, deadline))) {
+        // loader: one 2D TMA box (the tile's rows x FE binnings) and C residual rows per tile
+        if (lane == 0) {
+            const uint32_t bytes = (uint32_t)(FE * row_bytes + C * a.stage_rows * 4);
+            int issued = 0;
+            bool ok = true;
+            for (int it = 0; it < ntiles; ++it) {
+                const int s = it % a.stages;
+                if (it >= a.stages && !mbar_wait(&empty[s], ((it / a.stages) - 1) & 1, deadline)) {
                     ok = false;
                     break;
                 }
-                if (INT_ACC) {
-                    // fixed-point copy into a separate buffer: the TMA landing zone only ever
-                    // sees async-proxy writes and generic reads
-                    const float* rt = reinterpret_cast<const float*>(smem + a.r_off + (size_t)s * a.stage_r_bytes);
-                    int* qt = reinterpret_cast<int*>(smem + a.q_off + (size_t)s * a.stage_r_bytes);
-                    const int64_t row0 = (t_lo + jt) * a.stage_rows;
-                    for (int i = lane; i < C * a.stage_rows; i += 32) {
-                        const int ch = i / a.stage_rows;
-                        int q;
-                        if (counting) q = (row0 + (i % a.stage_rows) < n_act) ? 1 : 0;
-                        else q = __float2int_rn(rt[i] * scale[ch]);
-                        qt[i] = q;
-                    }
-                }
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&ready[s]);
+                const int64_t row0 = (t_lo + it) * a.stage_rows;
+                mbar_arrive_expect_tx(&full[s], bytes);
+                tma_load_2d(smem + a.ind_off + (size_t)s * a.stage_ind_bytes, &tmap, (int)row0, g * FE, &full[s]);
+                float* r_dst = reinterpret_cast<float*>(smem + a.r_off + (size_t)s * a.stage_r_bytes);
+                for (int ch = 0; ch < C; ++ch)
+                    bulk_load(r_dst + ch * a.stage_rows, a.rw + ch * a.n_pad + row0, (uint32_t)a.stage_rows * 4,
+                              &full[s]);
+                ++issued;
+            }
+            if (!ok) {
+                atomicOr(a.err, kErrTimeout);
+                // let copies already in flight land before the CTA retires
+                const long long d2 = clock64() + kWaitCycles;
+                for (int it = (issued > a.stages ? issued - a.stages : 0); it < issued; ++it)
+                    mbar_wait(&full[it % a.stages], (it / a.stages) & 1, d2);
             }
         }
-        if (!ok && lane == 0) {
-            atomicOr(a.err, kErrTimeout);
-            // let copies already in flight land before the CTA retires
-            const long long d2 = clock64() + kWaitCycles;
-            for (int it = (issued > a.stages ? issued - a.stages : 0); it < issued; ++it)
-                mbar_wait(&full[it % a.stages], (it / a.stages) & 1, d2);
+    } else if (warp == W + 1) {
+        // converter: residual tile -> fixed point (or a plain hand-over for FP32 accumulation)
+        float scale[2] = {1.0f, 1.0f};
+        if (INT_ACC && !counting) {
+            const int cidx = train_rows ? 1 : 0;
+            scale[0] = ldexpf(1.0f, fixed_scale(a.state->rmax_bits[0], a.state->cnt_log2[cidx]));
+            if (C == 2) scale[1] = ldexpf(1.0f, fixed_scale(a.state->rmax_bits[1], a.state->cnt_log2[cidx]));
+        }
+        for (int jt = 0; jt < ntiles; ++jt) {
+            const int s = jt % a.stages;
+            if (!__all_sync(0xffffffffu, mbar_wait(&full[s], (jt / a.stages) & 1, deadline))) {
+                if (lane == 0) atomicOr(a.err, kErrTimeout);
+                break;
+            }
+            if (INT_ACC) {
+                // fixed-point copy into a separate buffer: the TMA landing zone only ever sees
+                // async-proxy writes and generic reads
+                const float* rt = reinterpret_cast<const float*>(smem + a.r_off + (size_t)s * a.stage_r_bytes);
+                int* qt = reinterpret_cast<int*>(smem + a.q_off + (size_t)s * a.stage_r_bytes);
+                const int64_t row0 = (t_lo + jt) * a.stage_rows;
+                for (int i = lane; i < C * a.stage_rows; i += 32) {
+                    const int ch = i / a.stage_rows;
+                    int q;
+                    if (counting) q = (row0 + (i % a.stage_rows) < n_act) ? 1 : 0;
+                    else q = __float2int_rn(rt[i] * (ch ? scale[1] : scale[0]));
+                    qt[i] = q;
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ready[s]);
         }
     } else {
         const int q = lane / F;
         const int f = lane % F;
         const int ch = q % C, rs = q / C;
         const int RS = 32 / (F * C);
-        const int bidx = g * F + f;
-        const bool active = bidx < a.B;
-        Acc* hc = hist + ch * a.ch_stride;
-        const int row_bytes = a.stage_rows * (int)sizeof(IndT);   // one binning's rows of a tile
+        const bool active = f < FE && g * FE + f < a.B;
+        Acc* hf = hist + ch * a.ch_stride + f;
         const int nunits = row_bytes / 16;
+        const int step = UN * RS;
         for (int it = 0; it < ntiles; ++it) {
             const int s = it % a.stages;
             if (!__all_sync(0xffffffffu, mbar_wait(&ready[s], (it / a.stages) & 1, deadline))) {
                 if (lane == 0) atomicOr(a.err, kErrTimeout);
                 break;
             }
-            const unsigned char* ind_st = smem + a.ind_off + (size_t)s * a.stage_ind_bytes;
-            const Acc* r_st = reinterpret_cast<const Acc*>(smem + (INT_ACC ? a.q_off : a.r_off) + (size_t)s * a.stage_r_bytes) +
-                              ch * a.stage_rows;
-            for (int wi = warp; wi * RS < nunits; wi += W) {
-                const int u = wi * RS + rs;
-                if (active && u < nunits) {
-                    // lanes start at different 16-byte units of their rows (rotation by the lane's
-                    // binning) so the 32 reads of a warp spread over all banks
-                    const int pos = (u + f) & (nunits - 1);
-                    const uint4 raw = *reinterpret_cast<const uint4*>(ind_st + (size_t)f * row_bytes + (pos << 4));
-                    int idx[U];
-                    unpack16<IndT>(raw, idx);
+            const unsigned char* ind_row = smem + a.ind_off + (size_t)s * a.stage_ind_bytes + (size_t)f * row_bytes;
+            const Acc* r_st =
+                reinterpret_cast<const Acc*>(smem + (INT_ACC ? a.q_off : a.r_off) + (size_t)s * a.stage_r_bytes) +
+                ch * a.stage_rows;
+            if (active) {
+#pragma unroll 1
+                for (int u0 = warp * step; u0 < nunits; u0 += W * step) {
+                    uint4 raw[UN];
+                    Acc rv[UN][U];
+                    bool live[UN];
 #pragma unroll
-                    for (int t4 = 0; t4 < U / 4; ++t4) {
-                        Acc rv[4];
-                        if (INT_ACC) {
-                            const int4 r4 = reinterpret_cast<const int4*>(r_st + pos * U)[t4];
-                            rv[0] = r4.x; rv[1] = r4.y; rv[2] = r4.z; rv[3] = r4.w;
-                        } else {
-                            const float4 r4 = reinterpret_cast<const float4*>(r_st + pos * U)[t4];
-                            rv[0] = r4.x; rv[1] = r4.y; rv[2] = r4.z; rv[3] = r4.w;
+                    for (int k = 0; k < UN; ++k) {
+                        // lanes start at different 16-byte units of their rows (rotation by the
+                        // lane's binning) so the reads of a warp spread over all banks
+                        live[k] = u0 + k * RS + rs < nunits;
+                        const int pos = (u0 + k * RS + rs + f) & (nunits - 1);
+                        raw[k] = *reinterpret_cast<const uint4*>(ind_row + (pos << 4));
+#pragma unroll
+                        for (int t4 = 0; t4 < U / 4; ++t4) {
+                            if (INT_ACC) {
+                                const int4 r4 = reinterpret_cast<const int4*>(r_st + pos * U)[t4];
+                                rv[k][4 * t4] = r4.x; rv[k][4 * t4 + 1] = r4.y; rv[k][4 * t4 + 2] = r4.z; rv[k][4 * t4 + 3] = r4.w;
+                            } else {
+                                const float4 r4 = reinterpret_cast<const float4*>(r_st + pos * U)[t4];
+                                rv[k][4 * t4] = r4.x; rv[k][4 * t4 + 1] = r4.y; rv[k][4 * t4 + 2] = r4.z; rv[k][4 * t4 + 3] = r4.w;
+                            }
                         }
+                    }
 #pragma unroll
-                        for (int t = 0; t < 4; ++t) {
-                            const unsigned bl = (unsigned)(idx[4 * t4 + t] - b_lo);
-                            if (bl < (unsigned)a.nb_cta) atomicAdd(&hc[bl * F + f], rv[t]);
+                    for (int k = 0; k < UN; ++k) {
+                        if (!live[k]) continue;
+                        int idx[U];
+                        unpack16<IndT>(raw[k], idx);
+#pragma unroll
+                        for (int t = 0; t < U; ++t) {
+                            const unsigned bl = (unsigned)(idx[t] - b_lo);
+                            if (bl < (unsigned)a.nb_cta) atomicAdd(hf + bl * F, rv[k][t]);
                         }
                     }
                 }
@@ -1056,6 +1064,7 @@ ScatterArgs scatter_args(cwb_model* m)
     a.n_pad = m->n_pad;
     a.B = m->B;
     a.F = P.f_lane;
+    a.FE = P.fe;
     a.bin_ranges = P.bin_ranges;
     a.nb_cta = P.nb_cta;
     a.ch_stride = P.ch_stride;
@@ -1290,21 +1299,22 @@ cwb_status plan_scatter(cwb_model* m)
         while (hist_bytes((nbins + P.bin_ranges - 1) / P.bin_ranges, 1) + 3 * stage_bytes(1) > budget) ++P.bin_ranges;
     }
     const int F = P.f_lane;
+    P.groups = (B + F - 1) / F;
+    P.fe = (B + P.groups - 1) / P.groups;          // binnings per group, balanced across groups
     P.nb_cta = (nbins + P.bin_ranges - 1) / P.bin_ranges;
     P.nbins_pad = P.nb_cta * P.bin_ranges;
     P.ch_stride = ch_stride_for(P.nb_cta, F);
-    P.box_bytes = ((F * P.stage_rows * elem + 127) / 128) * 128;
+    P.box_bytes = ((P.fe * P.stage_rows * elem + 127) / 128) * 128;
     P.stage_ind_bytes = (uint32_t)P.box_bytes;
     P.stage_r_bytes = (uint32_t)(cmax * P.stage_rows * 4);
     const int hb = hist_bytes(P.nb_cta, F);
-    P.stages = std::min(8, (budget - hb) / stage_bytes(F));
+    P.stages = std::min(8, (budget - hb) / stage_bytes(P.fe));
     P.ind_off = 0;
     P.r_off = P.ind_off + (uint32_t)P.stages * P.stage_ind_bytes;
     P.q_off = P.r_off + (uint32_t)P.stages * P.stage_r_bytes;
     P.hist_off = ((P.q_off + (uint32_t)P.stages * P.stage_r_bytes + 1023) / 1024) * 1024;
     P.bar_off = P.hist_off + (uint32_t)hb;
     P.smem = (size_t)P.bar_off + 3 * 8 * P.stages + 1024;
-    P.groups = (B + F - 1) / F;
     P.slots = P.groups * P.bin_ranges;
     P.threads = kScatterThreads;
     m->plan = P;
@@ -1325,27 +1335,10 @@ cwb_status plan_scatter(cwb_model* m)
         return CWB_ECUDA;
     }
     P.cs = best_cs;
-    // clusters per slot in proportion to the binnings the slot holds (at least one each)
+    // clusters spread evenly over the slots (groups hold balanced numbers of binnings)
     int total = std::max(best_used / best_cs, P.slots);
-    std::vector<int> per(P.slots, 1);
-    int given = P.slots;
-    std::vector<double> wts(P.slots);
-    double wsum = 0.0;
-    for (int sl = 0; sl < P.slots; ++sl) {
-        int g = sl / P.bin_ranges;
-        wts[sl] = std::min(F, B - g * F);
-        wsum += wts[sl];
-    }
-    for (int sl = 0; sl < P.slots && given < total; ++sl) {
-        int extra = (int)((double)(total - P.slots) * wts[sl] / wsum);
-        extra = std::min(extra, total - given);
-        per[sl] += extra;
-        given += extra;
-    }
-    for (int sl = 0; given < total; sl = (sl + 1) % P.slots) {
-        per[sl] += 1;
-        given += 1;
-    }
+    std::vector<int> per(P.slots, total / P.slots);
+    for (int sl = 0; sl < total % P.slots; ++sl) per[sl] += 1;
     std::vector<int32_t> slot_c0(P.slots + 1, 0), cl_slot;
     for (int sl = 0; sl < P.slots; ++sl) {
         slot_c0[sl + 1] = slot_c0[sl] + per[sl];
@@ -1370,7 +1363,7 @@ cwb_status plan_scatter(cwb_model* m)
     }
     cuuint64_t dims[2] = {(cuuint64_t)m->n_pad, (cuuint64_t)B};
     cuuint64_t strides[1] = {(cuuint64_t)m->n_pad * elem};
-    cuuint32_t box[2] = {(cuuint32_t)P.stage_rows, (cuuint32_t)F};
+    cuuint32_t box[2] = {(cuuint32_t)P.stage_rows, (cuuint32_t)P.fe};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = enc(&m->tmap, elem == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, m->ind,
                      dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
