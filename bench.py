@@ -265,6 +265,7 @@ def run_ours(args):
         clocks = sampler.stop() if rank == 0 else None
         prof = model.get_profile()
         model.profile(False)
+        plan = model.scatter_plan()
         step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = sum(step_ms)
     if dist:
@@ -293,7 +294,7 @@ def run_ours(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "kernel": "k_scatter",
                          "peak_source": f"{peak_kind} hbm_gbs"},
-            "gpu_launches": launches, "clocks": clocks}
+            "gpu_launches": launches, "clocks": clocks, "scatter_plan": plan}
 
     if not args.skip_e2e:
         line["e2e"] = run_e2e(cwb, data, stream, dev, local)

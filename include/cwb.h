@@ -229,6 +229,15 @@ cwb_status cwb_get_profile(cwb_model* m, double* ms, int64_t* launches, int32_t 
  */
 cwb_status cwb_get_residuals(const cwb_model* m, int32_t channel, float* out);
 
+/*
+ * cwb_get_scatter_plan -- the decomposition chosen for the binMatVec scatter, for
+ * tuning and reports.  values (host int32, `cap` entries) receive in order:
+ * binnings per warp (lane-private columns), binnings per group, groups, bin ranges,
+ * bins per CTA, cluster size, clusters, pipeline stages, threads per CTA,
+ * dynamic shared memory bytes, 1 if histograms use exact int32 fixed point.
+ */
+cwb_status cwb_get_scatter_plan(const cwb_model* m, int32_t* values, int32_t cap);
+
 /* cwb_synchronize -- wait for the model's queued work; reports device-side errors. */
 cwb_status cwb_synchronize(cwb_model* m);
 

@@ -62,6 +62,7 @@ _SIGS = {
     "cwb_get_bin_index": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     "cwb_force_selection": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
     "cwb_get_residuals": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
+    "cwb_get_scatter_plan": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
     "cwb_synchronize": (C.c_int, [C.c_void_p]),
     "cwb_profile": (C.c_int, [C.c_void_p, C.c_int32]),
     "cwb_get_profile": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
@@ -184,6 +185,16 @@ def cwb_force_selection(model, k_forced: np.ndarray):
 
 def cwb_get_residuals(model, channel: int, out: np.ndarray):
     _check(load_library().cwb_get_residuals(model, channel, _ptr(out)), "cwb_get_residuals")
+
+
+_PLAN_KEYS = ("f_lane", "binnings_per_group", "groups", "bin_ranges", "bins_per_cta", "cluster_size", "clusters",
+              "stages", "threads", "smem_bytes", "int_fixed_point")
+
+
+def cwb_get_scatter_plan(model) -> dict:
+    vals = np.zeros(len(_PLAN_KEYS), dtype=np.int32)
+    _check(load_library().cwb_get_scatter_plan(model, _ptr(vals), vals.size), "cwb_get_scatter_plan")
+    return {k: int(v) for k, v in zip(_PLAN_KEYS, vals)}
 
 
 def cwb_synchronize(model):
@@ -348,6 +359,9 @@ class Model:
         out = np.zeros(self.n, dtype=np.float32)
         cwb_get_residuals(self.handle, channel, out)
         return out
+
+    def scatter_plan(self) -> dict:
+        return cwb_get_scatter_plan(self.handle)
 
     def force_selection(self, ks):
         cwb_force_selection(self.handle, np.ascontiguousarray(ks, dtype=np.int32))

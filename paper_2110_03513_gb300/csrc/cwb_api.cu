@@ -602,6 +602,17 @@ cwb_status cwb_get_profile(cwb_model* m, double* ms, int64_t* launches, int32_t 
     return CWB_OK;
 }
 
+cwb_status cwb_get_scatter_plan(const cwb_model* m, int32_t* values, int32_t cap)
+{
+    set_error("");
+    if (!m || (cap > 0 && !values)) { set_error("bad argument"); return CWB_EINVAL; }
+    const ScatterPlan& P = m->plan;
+    const int32_t v[11] = {P.f_lane, P.fe, P.groups, P.bin_ranges, P.nb_cta, P.cs, P.clusters, P.stages, P.threads,
+                           (int32_t)P.smem, P.int_acc ? 1 : 0};
+    for (int i = 0; i < cap && i < 11; ++i) values[i] = v[i];
+    return CWB_OK;
+}
+
 const char* cwb_last_error(void) { return g_last_error.c_str(); }
 
 void cwb_free(cwb_model* m)

@@ -507,7 +507,7 @@ __device__ __forceinline__ int fixed_scale(uint32_t rmax_bits, int cnt_log2)
     return max(-120, min(100, 30 - cnt_log2 - e));
 }
 
-template <typename IndT, int CMAX, bool INT_ACC>
+template <typename IndT, int CMAX, bool INT_ACC, bool RANGED>
 __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_constant__ CUtensorMap tmap, ScatterArgs a)
 {
     constexpr int U = 16 / sizeof(IndT);                   // rows per 16-byte unit
@@ -625,6 +625,7 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
         const int RS = 32 / (F * C);
         const bool active = f < FE && g * FE + f < a.B;
         Acc* hf = hist + ch * a.ch_stride + f;
+        const int fsh = __ffs(F) - 1;                     // F is a power of two
         const int nunits = row_bytes / 16;
         const int step = UN * RS;
         for (int it = 0; it < ntiles; ++it) {
@@ -668,8 +669,12 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
                         unpack16<IndT>(raw[k], idx);
 #pragma unroll
                         for (int t = 0; t < U; ++t) {
-                            const unsigned bl = (unsigned)(idx[t] - b_lo);
-                            if (bl < (unsigned)a.nb_cta) atomicAdd(hf + bl * F, rv[k][t]);
+                            if (RANGED) {
+                                const unsigned bl = (unsigned)(idx[t] - b_lo);
+                                if (bl < (unsigned)a.nb_cta) atomicAdd(hf + (bl << fsh), rv[k][t]);
+                            } else {
+                                atomicAdd(hf + (idx[t] << fsh), rv[k][t]);
+                            }
                         }
                     }
                 }
@@ -1050,7 +1055,8 @@ cudaError_t launch_scatter_t(cwb_model* m, cudaStream_t s, const ScatterArgs& a)
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_scatter<IndT, CMAX, INT_ACC>, m->tmap, a);
+    if (P.bin_ranges > 1) return cudaLaunchKernelEx(&cfg, k_scatter<IndT, CMAX, INT_ACC, true>, m->tmap, a);
+    return cudaLaunchKernelEx(&cfg, k_scatter<IndT, CMAX, INT_ACC, false>, m->tmap, a);
 }
 
 ScatterArgs scatter_args(cwb_model* m)
@@ -1210,8 +1216,10 @@ template <typename IndT, int CMAX>
 cwb_status prepare_scatter_kernel(cwb_model* m, int cs, int* active_clusters)
 {
     const ScatterPlan& P = m->plan;
-    CWB_CUDA_TRY(cudaFuncSetAttribute(k_scatter<IndT, CMAX, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem));
-    CWB_CUDA_TRY(cudaFuncSetAttribute(k_scatter<IndT, CMAX, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem));
+    CWB_CUDA_TRY(cudaFuncSetAttribute(k_scatter<IndT, CMAX, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem));
+    CWB_CUDA_TRY(cudaFuncSetAttribute(k_scatter<IndT, CMAX, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem));
+    CWB_CUDA_TRY(cudaFuncSetAttribute(k_scatter<IndT, CMAX, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem));
+    CWB_CUDA_TRY(cudaFuncSetAttribute(k_scatter<IndT, CMAX, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cs * 64, 1, 1);
     cfg.blockDim = dim3(P.threads, 1, 1);
@@ -1224,7 +1232,7 @@ cwb_status prepare_scatter_kernel(cwb_model* m, int cs, int* active_clusters)
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int n = 0;
-    cudaError_t e = cudaOccupancyMaxActiveClusters(&n, k_scatter<IndT, CMAX, true>, &cfg);
+    cudaError_t e = cudaOccupancyMaxActiveClusters(&n, k_scatter<IndT, CMAX, true, false>, &cfg);
     if (e != cudaSuccess) {
         cudaGetLastError();
         n = 0;
