@@ -12,6 +12,7 @@
 //   zb       [K][S][4]    FP32 non-zero basis values at the design points (S = max n*)
 //   zcol     [K][S]       int32 first non-zero column of each design point
 //   crange   [K][D][2]    int32 contiguous bin range contributing to each column
+//   ztab     [K][4 S]     FP32 the same design stored column by column (toff: column offsets)
 //   G, P     [2][K][D][D] FP64 Gram matrix and cached inverse per phase
 //   part     per-cluster histogram partials written by the scatter kernel
 //   u        [2][B][S]    histograms per binning (binMatVec intermediate u)
@@ -129,6 +130,8 @@ struct cwb_model {
     double* zb64 = nullptr;
     int32_t* zcol = nullptr;
     int32_t* crange = nullptr;
+    int32_t* toff = nullptr;              // [K][D] offset of column j in ztab
+    float* ztab = nullptr;                // [K][4 S] column-major reduced design
     double *G = nullptr, *P = nullptr, *lambda = nullptr;
     int32_t *l_bin = nullptr, *l_d = nullptr, *l_nstar = nullptr, *l_type = nullptr;
     double *l_xmin = nullptr, *l_xmax = nullptr;

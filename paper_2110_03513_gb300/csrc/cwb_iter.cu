@@ -343,13 +343,37 @@ __global__ void __launch_bounds__(kRowThreads) k_rows(RowArgs a)
         is_last = (t == gridDim.x - 1);
     }
     __syncthreads();
-    if (is_last && threadIdx.x == 0) {
-        __threadfence();
+    if (!is_last) return;
+    __threadfence();
+    // last block: block-parallel, fixed-order reductions of the per-block partials
+    __shared__ float mx[2][kRowThreads];
+    {
+        float b0 = 0.0f, b1 = 0.0f;
+        double rs = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += kRowThreads) {
+            if (KIND != kRowsUpdate) {
+                b0 = fmaxf(b0, __ldcg(a.blk_max + 2 * b));
+                b1 = fmaxf(b1, __ldcg(a.blk_max + 2 * b + 1));
+            }
+            if (eval_risk) rs += __ldcg(a.risk_part + b);
+        }
+        mx[0][threadIdx.x] = b0;
+        mx[1][threadIdx.x] = b1;
+        red[threadIdx.x] = rs;
+    }
+    __syncthreads();
+    for (int s = kRowThreads / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            mx[0][threadIdx.x] = fmaxf(mx[0][threadIdx.x], mx[0][threadIdx.x + s]);
+            mx[1][threadIdx.x] = fmaxf(mx[1][threadIdx.x], mx[1][threadIdx.x + s]);
+            red[threadIdx.x] += red[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
         DevState* S = a.state;
         if (eval_risk) {
-            double sum = 0.0;
-            for (int b = 0; b < (int)gridDim.x; ++b) sum += __ldcg(a.risk_part + b);
-            double risk = sum / (double)(a.n - a.n_tr);
+            double risk = red[0] / (double)(a.n - a.n_tr);
             if (!S->risk_valid) {
                 S->risk_prev = risk;
                 S->risk_valid = 1;
@@ -359,13 +383,8 @@ __global__ void __launch_bounds__(kRowThreads) k_rows(RowArgs a)
             }
         }
         if (KIND != kRowsUpdate) {
-            float b0 = 0.0f, b1 = 0.0f;
-            for (int b = 0; b < (int)gridDim.x; ++b) {
-                b0 = fmaxf(b0, __ldcg(a.blk_max + 2 * b));
-                b1 = fmaxf(b1, __ldcg(a.blk_max + 2 * b + 1));
-            }
-            S->rmax_bits[0] = __float_as_uint(b0);
-            S->rmax_bits[1] = acwb_n ? __float_as_uint(b1) : 0u;
+            S->rmax_bits[0] = __float_as_uint(mx[0][0]);
+            S->rmax_bits[1] = acwb_n ? __float_as_uint(mx[1][0]) : 0u;
         }
         if (KIND == kRowsUpdate && a.hybrid && S->mode == kModeACWB && S->counter >= a.patience) {
             S->mode = kModeCWB;
@@ -685,18 +704,46 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
     }
     __syncthreads();
     cluster.sync();
-    // sum the cluster's histograms (fixed rank order), each CTA one slice of the bins
-    const int per = (a.nb_cta + a.cs - 1) / a.cs;
-    const int l0 = min(a.nb_cta, rank * per), l1 = min(a.nb_cta, l0 + per);
+    // sum the cluster's histograms (fixed rank order), each CTA one slice of the bins, four
+    // 16-byte words per thread in flight; slices start on 16-byte boundaries
+    const int per = ((a.nb_cta * F + a.cs - 1) / a.cs + 3) & ~3;
+    const int e0 = min(a.nb_cta * F, rank * per), e1 = min(a.nb_cta * F, e0 + per);
     for (int ch = 0; ch < C; ++ch) {
         Acc* dst = reinterpret_cast<Acc*>(a.part) + ((int64_t)cl * CMAX + ch) * (int64_t)a.nb_cta * F;
-        for (int e = l0 * F + tid; e < l1 * F; e += blockDim.x) {
-            Acc acc = Acc(0);
+        const int nvec = (e1 - e0) / 4;
+        for (int v0 = tid; v0 < nvec; v0 += 4 * blockDim.x) {
+            Acc acc[4][4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+#pragma unroll
+                for (int t = 0; t < 4; ++t) acc[k][t] = Acc(0);
             for (int r = 0; r < a.cs; ++r) {
-                const Acc* h = cluster.map_shared_rank(hist, r);
-                acc += h[ch * a.ch_stride + e];
+                const Acc* h = cluster.map_shared_rank(hist, r) + ch * a.ch_stride + e0;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int v = v0 + k * blockDim.x;
+                    if (v < nvec) {
+                        if (INT_ACC) {
+                            const int4 x = reinterpret_cast<const int4*>(h)[v];
+                            acc[k][0] += x.x; acc[k][1] += x.y; acc[k][2] += x.z; acc[k][3] += x.w;
+                        } else {
+                            const float4 x = reinterpret_cast<const float4*>(h)[v];
+                            acc[k][0] += x.x; acc[k][1] += x.y; acc[k][2] += x.z; acc[k][3] += x.w;
+                        }
+                    }
+                }
             }
-            dst[e] = acc;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int v = v0 + k * blockDim.x;
+                if (v < nvec)
+                    for (int t = 0; t < 4; ++t) dst[e0 + 4 * v + t] = acc[k][t];
+            }
+        }
+        for (int e = e0 + 4 * nvec + tid; e < e1; e += blockDim.x) {
+            Acc x = Acc(0);
+            for (int r = 0; r < a.cs; ++r) x += cluster.map_shared_rank(hist, r)[ch * a.ch_stride + e];
+            dst[e] = x;
         }
     }
     cluster.sync();
@@ -796,6 +843,8 @@ struct SolveArgs {
     const float* zb;
     const int32_t* zcol;
     const int32_t* crange;
+    const int32_t* toff;
+    const float* ztab;
     const int32_t* l_bin;
     const int32_t* l_d;
     const int32_t* l_nstar;
@@ -821,48 +870,74 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(SolveArgs a)
     const int C = (mode == kModeACWB) ? 2 : 1;
     const int ph = (mode == kModeACWB) ? 0 : st.phase;
     const int b = a.l_bin[k], d = a.l_d[k];
-    __shared__ double s_s[kMaxD], th_s[kMaxD], term[kMaxD];
+    const int D = a.D;
+    extern __shared__ double dsm[];                     // P and G of this learner (d x d each)
+    double* Ps = dsm;
+    double* Gs = dsm + (size_t)D * D;
+    __shared__ double s_s[2][kMaxD], th_s[2][kMaxD], term[2][kMaxD];
     __shared__ bool is_last;
-    const double* Pk = a.P + ((int64_t)ph * a.K + k) * a.D * a.D;
-    const double* Gk = a.G + ((int64_t)ph * a.K + k) * a.D * a.D;
-
-    for (int ch = 0; ch < C; ++ch) {
-        const float* u = a.u + ((int64_t)ch * a.B + b) * a.S;
-        // 2. s = Z^b^T u over each column's contiguous bin range (warp tree sums)
-        for (int j = warp; j < d; j += blockDim.x / 32) {
-            const int lo = a.crange[((int64_t)k * a.D + j) * 2], hi = a.crange[((int64_t)k * a.D + j) * 2 + 1];
-            float acc = 0.0f;
-            for (int l = lo + lane; l < hi; l += 32) {
-                int c0 = a.zcol[(int64_t)k * a.S + l];
-                acc += a.zb[((int64_t)k * a.S + l) * kMaxNnz + (j - c0)] * __ldcg(u + l);
-            }
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (lane == 0) s_s[j] = (double)acc;
-        }
-        __syncthreads();
-        // 3. theta = P s (FP64)
-        if (tid < d) {
-            double t = 0.0;
-            for (int i = 0; i < d; ++i) t += Pk[tid * a.D + i] * s_s[i];
-            th_s[tid] = t;
-        }
-        __syncthreads();
-        // 4. Q = theta^T G theta - 2 theta^T s (FP64)
-        if (tid < d) {
-            double gt = 0.0;
-            for (int i = 0; i < d; ++i) gt += Gk[tid * a.D + i] * th_s[i];
-            term[tid] = th_s[tid] * (gt - 2.0 * s_s[tid]);
-        }
-        __syncthreads();
-        if (tid < a.D) a.theta_it[((int64_t)ch * a.K + k) * a.D + tid] = tid < d ? th_s[tid] : 0.0;
-        if (tid == 0) {
-            double q = 0.0;
-            for (int j = 0; j < d; ++j) q += term[j];
-            a.q_it[(int64_t)ch * a.K + k] = q;
-        }
-        __syncthreads();
+    // stage P and G (independent of the histograms: their loads overlap the s sums below)
+    const double* Pk = a.P + ((int64_t)ph * a.K + k) * D * D;
+    const double* Gk = a.G + ((int64_t)ph * a.K + k) * D * D;
+    for (int e = tid; e < d * d; e += blockDim.x) {
+        const int i = e / d, j = e % d;
+        Ps[e] = __ldg(Pk + i * D + j);
+        Gs[e] = __ldg(Gk + i * D + j);
     }
-
+    // s = Z^b^T u for every channel: warp per column, lanes over the column's contiguous bin range
+    const float* zt = a.ztab + (int64_t)k * kMaxNnz * a.S;
+    const float* u0 = a.u + (int64_t)b * a.S;
+    const float* u1 = a.u + ((int64_t)a.B + b) * a.S;
+    for (int j = warp; j < d; j += blockDim.x / 32) {
+        const int lo = a.crange[((int64_t)k * D + j) * 2], hi = a.crange[((int64_t)k * D + j) * 2 + 1];
+        const float* zc = zt + a.toff[(int64_t)k * D + j] - lo;
+        float acc0 = 0.0f, acc1 = 0.0f;
+#pragma unroll 4
+        for (int l = lo + lane; l < hi; l += 32) {
+            const float z = __ldg(zc + l);
+            acc0 = fmaf(z, __ldcg(u0 + l), acc0);
+            if (C == 2) acc1 = fmaf(z, __ldcg(u1 + l), acc1);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            acc0 += __shfl_xor_sync(0xffffffffu, acc0, o);
+            acc1 += __shfl_xor_sync(0xffffffffu, acc1, o);
+        }
+        if (lane == 0) {
+            s_s[0][j] = (double)acc0;
+            s_s[1][j] = (double)acc1;
+        }
+    }
+    __syncthreads();
+    // theta = P s (FP64); thread (ch, i)
+    if (tid < C * kMaxD) {
+        const int ch = tid / kMaxD, i = tid % kMaxD;
+        if (i < d) {
+            double t = 0.0;
+            for (int jj = 0; jj < d; ++jj) t += Ps[i * d + jj] * s_s[ch][jj];
+            th_s[ch][i] = t;
+        }
+    }
+    __syncthreads();
+    // Q = theta^T G theta - 2 theta^T s (FP64)
+    if (tid < C * kMaxD) {
+        const int ch = tid / kMaxD, i = tid % kMaxD;
+        if (i < d) {
+            double gt = 0.0;
+            for (int jj = 0; jj < d; ++jj) gt += Gs[i * d + jj] * th_s[ch][jj];
+            term[ch][i] = th_s[ch][i] * (gt - 2.0 * s_s[ch][i]);
+        }
+    }
+    __syncthreads();
+    if (tid < C * D) {
+        const int ch = tid / D, i = tid % D;
+        a.theta_it[((int64_t)ch * a.K + k) * D + i] = i < d ? th_s[ch][i] : 0.0;
+    }
+    if (tid < C) {
+        double q = 0.0;
+        for (int jj = 0; jj < d; ++jj) q += term[tid][jj];
+        a.q_it[(int64_t)tid * a.K + k] = q;
+    }
+    __syncthreads();
     if (tid == 0) {
         __threadfence();
         unsigned t = atomicAdd(&a.state->ticket_solve, 1u);
@@ -876,7 +951,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(SolveArgs a)
     __shared__ double cand_q[2 * kSolveThreads];
     __shared__ int cand_k[2 * kSolveThreads];
     __shared__ int best_k[2];
-    __shared__ float th32[kMaxD];
+    __shared__ float th32[2][kMaxD];
     __shared__ uint32_t bad;
     if (tid == 0) bad = 0;
     __syncthreads();
@@ -927,25 +1002,30 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(SolveArgs a)
             }
         }
         __syncthreads();
+    }
+    // update tables v[ch] = Z^b theta of the winners (FP32)
+    for (int e = tid; e < C * D; e += blockDim.x) {
+        const int ch = e / D, i = e % D;
+        const double tv = __ldcg(a.theta_it + ((int64_t)ch * a.K + best_k[ch]) * D + i);
+        th32[ch][i] = (float)tv;
+        if (trace_ok) a.tr_theta[((int64_t)2 * it + ch) * D + i] = tv;
+    }
+    __syncthreads();
+    for (int ch = 0; ch < C; ++ch) {
         const int kb = best_k[ch];
-        if (tid < a.D) {
-            double tv = __ldcg(a.theta_it + ((int64_t)ch * a.K + kb) * a.D + tid);
-            th32[tid] = (float)tv;
-            if (trace_ok) a.tr_theta[((int64_t)2 * it + ch) * a.D + tid] = tv;
-        }
-        __syncthreads();
         const int nstb = a.l_nstar[kb];
         for (int l = tid; l < nstb; l += blockDim.x) {
             const int c0 = a.zcol[(int64_t)kb * a.S + l];
-            const float* z = a.zb + ((int64_t)kb * a.S + l) * kMaxNnz;
+            const float4 z = reinterpret_cast<const float4*>(a.zb)[(int64_t)kb * a.S + l];
             float acc = 0.0f;
-#pragma unroll
-            for (int t = 0; t < kMaxNnz; ++t)
-                if (c0 + t < a.D) acc += z[t] * th32[c0 + t];
+            if (c0 < D) acc = fmaf(z.x, th32[ch][c0], acc);
+            if (c0 + 1 < D) acc = fmaf(z.y, th32[ch][c0 + 1], acc);
+            if (c0 + 2 < D) acc = fmaf(z.z, th32[ch][c0 + 2], acc);
+            if (c0 + 3 < D) acc = fmaf(z.w, th32[ch][c0 + 3], acc);
             a.v[(int64_t)ch * a.S + l] = acc;
         }
-        __syncthreads();
     }
+    __syncthreads();
     if (tid == 0) {
         DevState* S = a.state;
         if (trace_ok) {
@@ -959,8 +1039,6 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(SolveArgs a)
         S->k_cor = (C == 2) ? best_k[1] : -1;
         S->pend_mode = mode;
         S->m = st.m + 1;
-        S->rmax_bits[0] = 0u;
-        S->rmax_bits[1] = 0u;
         S->ticket_solve = 0;
     }
 }
@@ -998,7 +1076,7 @@ int num_sms(int device)
 int rows_grid(const cwb_model* m)
 {
     int64_t g = (m->n_pad / 4 + kRowThreads - 1) / kRowThreads;
-    int64_t cap = (int64_t)num_sms(m->device) * 4;
+    int64_t cap = (int64_t)num_sms(m->device) * 2;
     return (int)std::max<int64_t>(1, std::min(g, cap));
 }
 
@@ -1124,6 +1202,8 @@ void launch_reduce(cwb_model* m, cudaStream_t s)
                                                       P.nb_cta, P.cmax, m->nstar_max, m->hybrid ? 1 : 0, m->u);
 }
 
+size_t solve_smem(const cwb_model* m) { return sizeof(double) * 2 * (size_t)m->d_max * m->d_max; }
+
 void launch_solve(cwb_model* m, cudaStream_t s)
 {
     SolveArgs a;
@@ -1136,6 +1216,8 @@ void launch_solve(cwb_model* m, cudaStream_t s)
     a.zb = m->zb;
     a.zcol = m->zcol;
     a.crange = m->crange;
+    a.toff = m->toff;
+    a.ztab = m->ztab;
     a.l_bin = m->l_bin;
     a.l_d = m->l_d;
     a.l_nstar = m->l_nstar;
@@ -1150,7 +1232,7 @@ void launch_solve(cwb_model* m, cudaStream_t s)
     a.tr_q = m->tr_q;
     a.forced = m->forced;
     a.trace_cap = m->trace_cap;
-    k_solve<<<m->K, kSolveThreads, 0, s>>>(a);
+    k_solve<<<m->K, kSolveThreads, solve_smem(m), s>>>(a);
 }
 
 // Event pair around one launch when profiling (never while capturing a graph).
@@ -1273,6 +1355,7 @@ EncodeTiledFn encode_tiled_fn()
 
 cwb_status plan_scatter(cwb_model* m)
 {
+    CWB_CUDA_TRY(cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)solve_smem(m)));
     int optin = 0, sms = num_sms(m->device);
     CWB_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, m->device));
     const int budget = optin - 1024 - 512;          // alignment slack and mbarriers

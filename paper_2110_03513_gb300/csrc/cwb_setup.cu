@@ -364,6 +364,29 @@ __global__ void k_col_ranges(int S, int D, const int32_t* __restrict__ l_nstar, 
     }
 }
 
+// Column-major copy of the reduced design for the per-iteration s = Z^b^T u: column j's
+// values over its contiguous bin range are stored contiguously at ztab[k][toff[k][j] ...].
+__global__ void k_build_ztab(int S, int D, const int32_t* __restrict__ l_d, const float* __restrict__ zb,
+                             const int32_t* __restrict__ zcol, const int32_t* __restrict__ crange,
+                             int32_t* __restrict__ toff, float* __restrict__ ztab)
+{
+    const int k = blockIdx.x;
+    const int d = l_d[k];
+    for (int j = threadIdx.x; j < D; j += blockDim.x) {
+        int off = 0;
+        for (int jj = 0; jj < j && jj < d; ++jj)
+            off += crange[((int64_t)k * D + jj) * 2 + 1] - crange[((int64_t)k * D + jj) * 2];
+        toff[(int64_t)k * D + j] = off;
+        if (j >= d) continue;
+        const int lo = crange[((int64_t)k * D + j) * 2], hi = crange[((int64_t)k * D + j) * 2 + 1];
+        float* out = ztab + (int64_t)k * kMaxNnz * S + off;
+        for (int l = lo; l < hi; ++l) {
+            const int t = j - zcol[(int64_t)k * S + l];
+            out[l - lo] = (t >= 0 && t < kMaxNnz) ? zb[((int64_t)k * S + l) * kMaxNnz + t] : 0.0f;
+        }
+    }
+}
+
 // G = Z^b^T diag(cnt) Z^b (binMatMat, Algorithm 2), FP64, bins visited in order.
 __global__ void k_gram(int S, int D, int K, const int32_t* __restrict__ l_bin, const int32_t* __restrict__ l_d,
                        const int32_t* __restrict__ l_nnz, const double* __restrict__ zb64,
@@ -990,6 +1013,10 @@ cwb_status setup_model(cwb_model* m, const void* X_in, int x_dtype, const void* 
                     m->zb, m->zb64, m->zcol};
         k_basis<<<K, kThreads, 0, s>>>(a);
         k_col_ranges<<<K, 64, 0, s>>>(S, D, m->l_nstar, m->l_d, nnz_d, m->zcol, m->crange);
+        CWB_TRY(dev_alloc((void**)&m->toff, sizeof(int32_t) * (size_t)K * D, s));
+        CWB_TRY(dev_alloc((void**)&m->ztab, sizeof(float) * (size_t)K * kMaxNnz * S, s));
+        CWB_CUDA_TRY(cudaMemsetAsync(m->ztab, 0, sizeof(float) * (size_t)K * kMaxNnz * S, s));
+        k_build_ztab<<<K, 64, 0, s>>>(S, D, m->l_d, m->zb, m->zcol, m->crange, m->toff, m->ztab);
     }
 
     // --- weighted bin counts per phase: phase 0 = fitting rows of the first phase, phase 1 = all rows
