@@ -176,7 +176,7 @@ __device__ __forceinline__ void store_df4(float* p, int64_t i4, const DF v[4])
 }
 
 template <int KIND, typename IndT>
-__global__ void __launch_bounds__(kRowThreads) k_rows(RowArgs a)
+__global__ void __launch_bounds__(kRowThreads, 4) k_rows(RowArgs a)
 {
     const DevState st = *a.state;
     const bool pend = (KIND != kRowsResid) && (st.m > st.m_applied);
@@ -758,8 +758,9 @@ __global__ void __launch_bounds__(256) k_reduce_partials(const DevState* __restr
                                                          const int32_t* __restrict__ slot_c0, int B, int F, int bin_ranges,
                                                          int nb_cta, int cmax, int S, int hybrid, float* __restrict__ u)
 {
-    __shared__ long long acc_i[4][64];
-    __shared__ float acc_f[4][64];
+    constexpr int kE = 16, kR = 16;                 // entries per block x cluster rows
+    __shared__ long long acc_i[kR][kE];
+    __shared__ float acc_f[kR][kE];
     const int mode = state->mode;
     const int C = (cmax == 2 && mode == kModeACWB) ? 2 : 1;
     const int ch = blockIdx.z;
@@ -768,43 +769,44 @@ __global__ void __launch_bounds__(256) k_reduce_partials(const DevState* __restr
     const int g = slot / bin_ranges, br = slot % bin_ranges;
     const int c0 = slot_c0[slot], c1 = slot_c0[slot + 1];
     const int nbf = nb_cta * F;
-    const int e = blockIdx.x * 64 + (threadIdx.x & 63);
-    const int part_row = threadIdx.x >> 6;          // 0..3
+    const int e = blockIdx.x * kE + (threadIdx.x % kE);
+    const int row = threadIdx.x / kE;
     if (INT_ACC) {
         const int* pi = reinterpret_cast<const int*>(part);
         long long acc = 0;
         if (e < nbf) {
-            int c = c0 + part_row;
-            for (; c + 12 < c1; c += 16) {
+            int c = c0 + row;
+            for (; c + kR < c1; c += 2 * kR) {
                 const int v0 = __ldcg(pi + ((int64_t)c * cmax + ch) * nbf + e);
-                const int v1 = __ldcg(pi + ((int64_t)(c + 4) * cmax + ch) * nbf + e);
-                const int v2 = __ldcg(pi + ((int64_t)(c + 8) * cmax + ch) * nbf + e);
-                const int v3 = __ldcg(pi + ((int64_t)(c + 12) * cmax + ch) * nbf + e);
-                acc += (long long)v0 + v1 + v2 + v3;
+                const int v1 = __ldcg(pi + ((int64_t)(c + kR) * cmax + ch) * nbf + e);
+                acc += (long long)v0 + v1;
             }
-            for (; c < c1; c += 4) acc += __ldcg(pi + ((int64_t)c * cmax + ch) * nbf + e);
+            for (; c < c1; c += kR) acc += __ldcg(pi + ((int64_t)c * cmax + ch) * nbf + e);
         }
-        acc_i[part_row][threadIdx.x & 63] = acc;
+        acc_i[row][threadIdx.x % kE] = acc;
     } else {
-        float s = 0.0f, comp = 0.0f;
+        float sum = 0.0f, comp = 0.0f;
         if (e < nbf)
-            for (int c = c0 + part_row; c < c1; c += 4) {
+            for (int c = c0 + row; c < c1; c += kR) {
                 const float y = __ldcg(part + ((int64_t)c * cmax + ch) * nbf + e) - comp;
-                const float t = s + y;
-                comp = (t - s) - y;
-                s = t;
+                const float t = sum + y;
+                comp = (t - sum) - y;
+                sum = t;
             }
-        acc_f[part_row][threadIdx.x & 63] = s;
+        acc_f[row][threadIdx.x % kE] = sum;
     }
     __syncthreads();
-    if (threadIdx.x < 64 && e < nbf) {
+    if (threadIdx.x < kE && e < nbf) {
         float val;
         if (INT_ACC) {
-            const long long tot = acc_i[0][threadIdx.x] + acc_i[1][threadIdx.x] + acc_i[2][threadIdx.x] + acc_i[3][threadIdx.x];
+            long long tot = 0;
+            for (int r = 0; r < kR; ++r) tot += acc_i[r][threadIdx.x];
             const int sc = fixed_scale(state->rmax_bits[ch], state->cnt_log2[(hybrid && mode == kModeACWB) ? 1 : 0]);
             val = (float)ldexp((double)tot, -sc);
         } else {
-            val = (acc_f[0][threadIdx.x] + acc_f[1][threadIdx.x]) + (acc_f[2][threadIdx.x] + acc_f[3][threadIdx.x]);
+            float tot = 0.0f;
+            for (int r = 0; r < kR; ++r) tot += acc_f[r][threadIdx.x];
+            val = tot;
         }
         const int lb = e / F, f = e % F;
         const int b = g * F + f;
@@ -888,23 +890,49 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(SolveArgs a)
     const float* zt = a.ztab + (int64_t)k * kMaxNnz * a.S;
     const float* u0 = a.u + (int64_t)b * a.S;
     const float* u1 = a.u + ((int64_t)a.B + b) * a.S;
-    for (int j = warp; j < d; j += blockDim.x / 32) {
-        const int lo = a.crange[((int64_t)k * D + j) * 2], hi = a.crange[((int64_t)k * D + j) * 2 + 1];
-        const float* zc = zt + a.toff[(int64_t)k * D + j] - lo;
-        float acc0 = 0.0f, acc1 = 0.0f;
-#pragma unroll 4
-        for (int l = lo + lane; l < hi; l += 32) {
-            const float z = __ldg(zc + l);
-            acc0 = fmaf(z, __ldcg(u0 + l), acc0);
-            if (C == 2) acc1 = fmaf(z, __ldcg(u1 + l), acc1);
+    {
+        // each warp sums up to kColsPerWarp columns at once (more loads in flight)
+        constexpr int kColsPerWarp = kMaxD / (kSolveThreads / 32);
+        const int nw = blockDim.x / 32;
+        int lo[kColsPerWarp], len[kColsPerWarp];
+        const float* zc[kColsPerWarp];
+        float acc0[kColsPerWarp], acc1[kColsPerWarp];
+        int maxlen = 0;
+#pragma unroll
+        for (int c = 0; c < kColsPerWarp; ++c) {
+            const int j = warp + c * nw;
+            lo[c] = 0;
+            len[c] = 0;
+            zc[c] = zt;
+            acc0[c] = acc1[c] = 0.0f;
+            if (j < d) {
+                lo[c] = a.crange[((int64_t)k * D + j) * 2];
+                len[c] = a.crange[((int64_t)k * D + j) * 2 + 1] - lo[c];
+                zc[c] = zt + a.toff[(int64_t)k * D + j];
+                maxlen = max(maxlen, len[c]);
+            }
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            acc0 += __shfl_xor_sync(0xffffffffu, acc0, o);
-            acc1 += __shfl_xor_sync(0xffffffffu, acc1, o);
+        for (int t = lane; t < maxlen; t += 32) {
+#pragma unroll
+            for (int c = 0; c < kColsPerWarp; ++c) {
+                if (t < len[c]) {
+                    const float z = __ldg(zc[c] + t);
+                    acc0[c] = fmaf(z, __ldcg(u0 + lo[c] + t), acc0[c]);
+                    if (C == 2) acc1[c] = fmaf(z, __ldcg(u1 + lo[c] + t), acc1[c]);
+                }
+            }
         }
-        if (lane == 0) {
-            s_s[0][j] = (double)acc0;
-            s_s[1][j] = (double)acc1;
+#pragma unroll
+        for (int c = 0; c < kColsPerWarp; ++c) {
+            for (int o = 16; o > 0; o >>= 1) {
+                acc0[c] += __shfl_xor_sync(0xffffffffu, acc0[c], o);
+                acc1[c] += __shfl_xor_sync(0xffffffffu, acc1[c], o);
+            }
+            const int j = warp + c * nw;
+            if (lane == 0 && j < d) {
+                s_s[0][j] = (double)acc0[c];
+                s_s[1][j] = (double)acc1[c];
+            }
         }
     }
     __syncthreads();
@@ -949,7 +977,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(SolveArgs a)
 
     // ---- last CTA: argmin per channel, update tables, trace, state
     __shared__ double cand_q[2 * kSolveThreads];
-    __shared__ int cand_k[2 * kSolveThreads];
+    __shared__ int cand_k[kSolveThreads];
     __shared__ int best_k[2];
     __shared__ float th32[2][kMaxD];
     __shared__ uint32_t bad;
@@ -958,36 +986,40 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(SolveArgs a)
     const int it = st.m;
     const bool trace_ok = it < a.trace_cap;
     for (int ch = 0; ch < C; ++ch) {
+        // per-thread best and second best, then a tree merge (ties go to the lowest index)
         double q1 = INFINITY, q2 = INFINITY;
-        int k1 = -1, k2 = -1;
+        int k1 = -1;
         for (int kk = tid; kk < a.K; kk += blockDim.x) {
             double q = __ldcg(a.q_it + (int64_t)ch * a.K + kk);
             if (!(q == q) || isinf(q)) {
                 atomicOr(&bad, 1u);
                 q = INFINITY;
             }
-            if (q < q1) { q2 = q1; k2 = k1; q1 = q; k1 = kk; }
-            else if (q < q2) { q2 = q; k2 = kk; }
+            if (k1 < 0 || q < q1) { q2 = q1; q1 = q; k1 = kk; }
+            else if (q < q2) { q2 = q; }
         }
-        cand_q[2 * tid] = q1; cand_k[2 * tid] = k1;
-        cand_q[2 * tid + 1] = q2; cand_k[2 * tid + 1] = k2;
+        cand_q[2 * tid] = q1;
+        cand_q[2 * tid + 1] = q2;
+        cand_k[tid] = k1;
         __syncthreads();
-        if (tid == 0) {
-            double b1 = INFINITY, b2 = INFINITY;
-            int i1 = -1;
-            for (int c = 0; c < 2 * (int)blockDim.x; ++c) {
-                double q = cand_q[c];
-                int kk = cand_k[c];
-                if (kk < 0) continue;
-                if (i1 < 0 || q < b1 || (q == b1 && kk < i1)) {
-                    if (i1 >= 0) b2 = fmin(b2, b1);
-                    b1 = q;
-                    i1 = kk;
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if (tid < w) {
+                const double a1 = cand_q[2 * tid], a2 = cand_q[2 * tid + 1];
+                const double b1 = cand_q[2 * (tid + w)], b2 = cand_q[2 * (tid + w) + 1];
+                const int ka = cand_k[tid], kb2 = cand_k[tid + w];
+                bool take_b = kb2 >= 0 && (ka < 0 || b1 < a1 || (b1 == a1 && kb2 < ka));
+                if (take_b) {
+                    cand_q[2 * tid] = b1;
+                    cand_q[2 * tid + 1] = fmin(fmin(a1, a2), b2);
+                    cand_k[tid] = kb2;
                 } else {
-                    b2 = fmin(b2, q);
+                    cand_q[2 * tid + 1] = fmin(a2, fmin(b1, b2));
                 }
             }
-            if (i1 < 0) i1 = 0;
+            __syncthreads();
+        }
+        if (tid == 0) {
+            int i1 = cand_k[0] < 0 ? 0 : cand_k[0];
             if (ch == 0 && trace_ok && a.forced) {
                 int fk = a.forced[it];
                 if (fk >= 0 && fk < a.K) i1 = fk;
@@ -996,8 +1028,8 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(SolveArgs a)
             if (trace_ok) {
                 a.tr_k[2 * it + ch] = i1;
                 if (ch == 0) {
-                    a.tr_q[2 * it] = b1;
-                    a.tr_q[2 * it + 1] = b2;
+                    a.tr_q[2 * it] = cand_q[0];
+                    a.tr_q[2 * it + 1] = cand_q[1];
                 }
             }
         }
@@ -1076,7 +1108,7 @@ int num_sms(int device)
 int rows_grid(const cwb_model* m)
 {
     int64_t g = (m->n_pad / 4 + kRowThreads - 1) / kRowThreads;
-    int64_t cap = (int64_t)num_sms(m->device) * 2;
+    int64_t cap = (int64_t)num_sms(m->device) * 4;
     return (int)std::max<int64_t>(1, std::min(g, cap));
 }
 
@@ -1193,7 +1225,7 @@ void launch_scatter(cwb_model* m, cudaStream_t s)
 void launch_reduce(cwb_model* m, cudaStream_t s)
 {
     const ScatterPlan& P = m->plan;
-    dim3 grid((P.nb_cta * P.f_lane + 63) / 64, P.slots, P.cmax);
+    dim3 grid((P.nb_cta * P.f_lane + 15) / 16, P.slots, P.cmax);
     if (P.int_acc)
         k_reduce_partials<true><<<grid, 256, 0, s>>>(m->state, m->part, m->slot_c0, m->B, P.f_lane, P.bin_ranges,
                                                      P.nb_cta, P.cmax, m->nstar_max, m->hybrid ? 1 : 0, m->u);
