@@ -63,6 +63,7 @@ _SIGS = {
     "cwb_force_selection": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
     "cwb_get_residuals": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     "cwb_get_scatter_plan": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
+    "cwb_predict_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int64, C.c_void_p]),
     "cwb_synchronize": (C.c_int, [C.c_void_p]),
     "cwb_profile": (C.c_int, [C.c_void_p, C.c_int32]),
     "cwb_get_profile": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
@@ -144,6 +145,10 @@ def cwb_fit(model, iterations: int):
 
 def cwb_predict(model, Xnew, x_dtype: int, n_new: int, out, device_ptrs: int):
     _check(load_library().cwb_predict(model, _ptr(Xnew), x_dtype, n_new, _ptr(out), device_ptrs), "cwb_predict")
+
+
+def cwb_predict_noalloc(model, Xnew: np.ndarray, x_dtype: int, n_new: int, out: np.ndarray):
+    _check(load_library().cwb_predict_noalloc(model, _ptr(Xnew), x_dtype, n_new, _ptr(out)), "cwb_predict_noalloc")
 
 
 def cwb_get_coefficients(model, k: int, which: int, theta: np.ndarray, offset: np.ndarray | None = None):

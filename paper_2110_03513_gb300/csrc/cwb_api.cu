@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <utility>
 #include <vector>
@@ -611,6 +612,62 @@ cwb_status cwb_get_scatter_plan(const cwb_model* m, int32_t* values, int32_t cap
                            (int32_t)P.smem, P.int_acc ? 1 : 0};
     for (int i = 0; i < cap && i < 11; ++i) values[i] = v[i];
     return CWB_OK;
+}
+
+// Fixed device scratch for cwb_predict_noalloc: staged Xnew followed by the predictions.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[CWB_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on `dev` (looked up once per device, with that device current).
+cwb_status noalloc_scratch(int dev, unsigned char** out)
+{
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (dev < 0 || dev >= kNoAllocMaxDevices) {
+        set_error("cwb_predict_noalloc supports device ordinals below 64");
+        return CWB_EINVAL;
+    }
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress(scratch)");
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = static_cast<unsigned char*>(g_noalloc_ptr[dev]);
+    return CWB_OK;
+}
+}  // namespace
+
+cwb_status cwb_predict_noalloc(const cwb_model* mc, const void* Xnew, int32_t x_dtype, int64_t n_new, float* out)
+{
+    set_error("");
+    cwb_model* m = const_cast<cwb_model*>(mc);
+    if (!m || !Xnew || !out) { set_error("NULL argument"); return CWB_EINVAL; }
+    if (n_new < 0) { set_error("n_new must be >= 0"); return CWB_EINVAL; }
+    if (x_dtype != CWB_F32 && x_dtype != CWB_F64) { set_error("x_dtype must be CWB_F32 or CWB_F64"); return CWB_EINVAL; }
+    if (n_new == 0) return CWB_OK;
+    const size_t xsz = (x_dtype == CWB_F64) ? 8 : 4;
+    const size_t x_bytes = xsz * (size_t)n_new * (size_t)m->p;
+    const size_t out_off = (x_bytes + 255) & ~(size_t)255;
+    const size_t need = out_off + sizeof(float) * (size_t)n_new;
+    if (need > (size_t)CWB_NOALLOC_SCRATCH_BYTES) {
+        set_error("cwb_predict_noalloc needs " + std::to_string(need) + " bytes of scratch for this request, the limit is " +
+                  std::to_string((size_t)CWB_NOALLOC_SCRATCH_BYTES) + " bytes; split the rows into several calls");
+        return CWB_EINVAL;
+    }
+    DeviceGuard guard(m->device);
+    unsigned char* base = nullptr;
+    CWB_TRY(noalloc_scratch(m->device, &base));
+    CWB_TRY(launch_aggregate(m));
+    CWB_CUDA_TRY(cudaMemcpyAsync(base, Xnew, x_bytes, cudaMemcpyHostToDevice, m->stream));
+    float* out_dev = reinterpret_cast<float*>(base + out_off);
+    CWB_TRY(launch_predict(m, base, x_dtype, n_new, out_dev));
+    CWB_CUDA_TRY(cudaMemcpyAsync(out, out_dev, sizeof(float) * (size_t)n_new, cudaMemcpyDeviceToHost, m->stream));
+    CWB_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    return read_device_error(m);
 }
 
 const char* cwb_last_error(void) { return g_last_error.c_str(); }
