@@ -137,9 +137,11 @@ cwb_status cwb_create(const cwb_config* cfg, const void* X, int32_t x_dtype, int
  * histogram (Algorithm 2), Z^T u, theta = P (Z^T u), the SSE criterion, argmin
  * over learners and the update f += nu Z_k theta_k (Algorithm 1; Algorithm 3 for
  * ACWB with two fits per iteration).  No host synchronisation happens between
- * iterations; the call returns once the work is queued on the model's stream.
- * A device-side wait that ran out is reported by the next call that
- * synchronises, as CWB_ETIMEOUT.
+ * iterations; the call returns once the work is queued on the model's stream
+ * (as CUDA graphs).  The update of the last iteration is folded into the next
+ * iteration's row pass; calls that read the fitted values, the trace or the
+ * coefficients apply it first.  A device-side wait that ran out is reported by
+ * the next call that synchronises, as CWB_ETIMEOUT.
  */
 cwb_status cwb_fit(cwb_model* m, int32_t iterations);
 
@@ -204,20 +206,26 @@ cwb_status cwb_get_bin_index(const cwb_model* m, int32_t k, int32_t* ind);
 cwb_status cwb_force_selection(cwb_model* m, const int32_t* k_forced, int32_t count);
 
 /*
- * cwb_profile -- enable (1) or disable (0) per-kernel timing: while enabled, every
- * kernel an iteration launches is bracketed by CUDA events recorded on the model's
- * stream (iterations are then launched one by one instead of from a CUDA graph).
- * Enabling also clears the accumulated figures.
+ * cwb_profile -- per-kernel timing.  `enable` = 0 switches it off, CWB_PROF_ALL
+ * brackets every kernel class, otherwise an OR of CWB_PROF_ROWS, CWB_PROF_SCATTER
+ * and CWB_PROF_SOLVE selects the classes.  While enabled, iterations are launched
+ * one by one from a one-iteration CUDA graph whose event-record nodes (CUDA events
+ * on the model's stream) bracket the selected kernels; unselected kernels run
+ * without events between them.  Changing the setting clears the accumulated figures.
  */
+#define CWB_PROF_ALL 1
+#define CWB_PROF_ROWS 0x10
+#define CWB_PROF_SCATTER 0x20
+#define CWB_PROF_SOLVE 0x40
 cwb_status cwb_profile(cwb_model* m, int32_t enable);
 
 /*
  * cwb_get_profile -- accumulated device time (ms) and launch counts per kernel
  * class since profiling was enabled: index 0 = row pass (update / pseudo
- * residuals), 1 = binMatVec scatter, 2 = solve / criterion / argmin, 3 = reduction
- * of the per-cluster partial histograms.  `ms` and
- * `launches` hold `cap` entries (host memory, either may be NULL).  Synchronises
- * the model's stream.
+ * residuals), 1 = binMatVec scatter, 2 = per-learner solve (sum of the cluster
+ * partial histograms, Z^T u, theta, criterion, update table, argmin), 3 = reserved
+ * (always 0).  `ms` and `launches` hold `cap` entries (host memory, either may be
+ * NULL).  Synchronises the model's stream.
  */
 cwb_status cwb_get_profile(cwb_model* m, double* ms, int64_t* launches, int32_t cap);
 

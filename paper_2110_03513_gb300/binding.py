@@ -19,6 +19,8 @@ OPT_CWB, OPT_ACWB, OPT_HCWB = 0, 1, 2
 BL_PSPLINE, BL_LINEAR = 0, 1
 F32, F64 = 0, 1
 BINS_EXACT, BINS_SQRT = 0, -1
+PROF_ALL = 1
+_PROF_BITS = {"rows": 0x10, "scatter": 0x20, "solve": 0x40}
 
 _STATUS = {0: "CWB_OK", 1: "CWB_EINVAL", 2: "CWB_ENOMEM", 3: "CWB_ECUDA", 4: "CWB_ENUMERIC", 5: "CWB_ETIMEOUT",
            6: "CWB_ESTATE"}
@@ -351,14 +353,23 @@ class Model:
         cwb_get_bin_index(self.handle, k, ind)
         return ind
 
-    def profile(self, enable: bool = True):
-        cwb_profile(self.handle, 1 if enable else 0)
+    def profile(self, enable: bool = True, classes=None):
+        """Per-kernel event timing; `classes` picks kernel classes ("rows", "scatter", "solve"), None = all."""
+        if not enable:
+            code = 0
+        elif classes is None:
+            code = PROF_ALL
+        else:
+            code = 0
+            for c in classes:
+                code |= _PROF_BITS[c]
+        cwb_profile(self.handle, code)
 
     def get_profile(self):
         ms = np.zeros(4)
         launches = np.zeros(4, dtype=np.int64)
         cwb_get_profile(self.handle, ms, launches)
-        return {name: (float(ms[i]), int(launches[i])) for i, name in enumerate(("rows", "scatter", "solve", "reduce"))}
+        return {name: (float(ms[i]), int(launches[i])) for i, name in enumerate(("rows", "scatter", "solve"))}
 
     def residuals(self, channel: int = 0) -> np.ndarray:
         out = np.zeros(self.n, dtype=np.float32)

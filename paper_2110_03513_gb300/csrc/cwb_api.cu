@@ -139,11 +139,13 @@ void free_model(cwb_model* m)
     if (m->stream) cudaStreamSynchronize(m->stream);
     void* bufs[] = {m->ind, m->y, m->y_lo, m->w, m->f, m->h, m->c, m->rw, m->perm, m->zb, m->zb64, m->zcol, m->crange, m->toff, m->ztab, m->G,
                     m->P, m->lambda, m->l_bin, m->l_d, m->l_nstar, m->l_type, m->l_xmin, m->l_xmax, m->l_degree,
-                    m->l_nknots, m->l_feat, m->part, m->u, m->cluster_slot, m->slot_c0, m->theta_it, m->q_it, m->v, m->state, m->risk_part, m->blk_max, m->tr_k,
+                    m->l_nknots, m->l_feat, m->part, m->cluster_slot, m->slot_c0, m->theta_it, m->q_it, m->v, m->state, m->risk_part, m->blk_max, m->tr_k,
                     m->tr_mode, m->tr_theta, m->tr_q, m->forced, m->coef};
     for (void* p : bufs) dev_free(p);
     profile_release(m);
-    if (m->graph_exec) cudaGraphExecDestroy(m->graph_exec);
+    release_graphs(m);
+    for (cudaEvent_t e : m->prof_ph)
+        if (e) cudaEventDestroy(e);
     if (m->capture_stream) cudaStreamDestroy(m->capture_stream);
     if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
     delete m;
@@ -260,8 +262,7 @@ cwb_status create_impl(const cwb_config* cfg, const void* X, int32_t x_dtype, in
         st = dev_alloc((void**)&m->part, sizeof(float) * std::max<size_t>(m->plan.part_floats, 1), m->stream);
         if (st == CWB_OK) st = dev_alloc((void**)&m->theta_it, sizeof(double) * 2 * K * D, m->stream);
         if (st == CWB_OK) st = dev_alloc((void**)&m->q_it, sizeof(double) * 2 * K, m->stream);
-        if (st == CWB_OK) st = dev_alloc((void**)&m->v, sizeof(float) * 2 * (size_t)S, m->stream);
-        if (st == CWB_OK) st = dev_alloc((void**)&m->u, sizeof(float) * 2 * (size_t)m->B * S, m->stream);
+        if (st == CWB_OK) st = dev_alloc((void**)&m->v, sizeof(float) * 2 * (size_t)K * S, m->stream);
         if (st == CWB_OK) st = dev_alloc((void**)&m->state, sizeof(DevState), m->stream);
         if (st == CWB_OK) st = dev_alloc((void**)&m->coef, sizeof(double) * 2 * K * D, m->stream);
         if (st == CWB_OK) st = dev_alloc((void**)&l_feat, sizeof(int32_t) * K, m->stream);
@@ -286,7 +287,7 @@ cwb_status create_impl(const cwb_config* cfg, const void* X, int32_t x_dtype, in
             s0.k_cor = -1;
             s0.pend_mode = kModeCWB;
             cudaError_t e = cudaMemcpyAsync(m->state, &s0, sizeof(s0), cudaMemcpyHostToDevice, m->stream);
-            if (e == cudaSuccess) e = cudaMemsetAsync(m->v, 0, sizeof(float) * 2 * S, m->stream);
+            if (e == cudaSuccess) e = cudaMemsetAsync(m->v, 0, sizeof(float) * 2 * (size_t)K * S, m->stream);
             if (e == cudaSuccess) e = cudaMemsetAsync(m->coef, 0, sizeof(double) * 2 * K * D, m->stream);
             if (e != cudaSuccess) st = cuda_status(e, "state init");
         }
@@ -352,8 +353,7 @@ cwb_status cwb_fit(cwb_model* m, int32_t iterations)
     int32_t it = iterations > 0 ? iterations : m->cfg.iterations;
     if (it <= 0) return CWB_OK;
     try {
-        CWB_TRY(launch_iterations(m, it));
-        CWB_TRY(launch_final_update(m));
+        CWB_TRY(launch_iterations(m, it));   // the last update is applied when f is next read
     } catch (const std::exception& e) {
         set_error(std::string("host exception: ") + e.what());
         return CWB_ENOMEM;
@@ -433,6 +433,7 @@ cwb_status cwb_get_trace(const cwb_model* mc, int32_t* k_sel, int32_t* k_cor, in
     cwb_model* m = const_cast<cwb_model*>(mc);
     if (!m) { set_error("model is NULL"); return CWB_EINVAL; }
     DeviceGuard guard(m->device);
+    CWB_TRY(materialize(m));
     const int32_t cnt = std::min(std::max(cap, 0), m->done);
     std::vector<int32_t> tk(2 * (size_t)std::max(cnt, 1));
     if (cnt > 0)
@@ -473,6 +474,7 @@ cwb_status cwb_get_fitted(const cwb_model* mc, float* f, int32_t device_ptrs)
     cwb_model* m = const_cast<cwb_model*>(mc);
     if (!m || !f) { set_error("NULL argument"); return CWB_EINVAL; }
     DeviceGuard guard(m->device);
+    CWB_TRY(materialize(m));
     float* od = f;
     if (!device_ptrs) CWB_TRY(dev_alloc((void**)&od, sizeof(float) * m->n, m->stream));
     k_unpermute<<<grid_1d(m->n, m->device), 256, 0, m->stream>>>(m->f, m->perm, m->n, od);
@@ -586,7 +588,16 @@ cwb_status cwb_profile(cwb_model* m, int32_t enable)
         m->prof_ms[i] = 0.0;
         m->prof_launches[i] = 0;
     }
-    m->prof_on = enable != 0;
+    const int mask = enable == CWB_PROF_ALL ? 0x7 : ((enable >> 4) & 0x7);
+    if (mask != m->prof_mask && m->prof_exec) {
+        cudaGraphExecDestroy(m->prof_exec);
+        if (m->prof_graph) cudaGraphDestroy(m->prof_graph);
+        m->prof_exec = nullptr;
+        m->prof_graph = nullptr;
+        m->prof_nodes.clear();
+    }
+    m->prof_mask = mask;
+    m->prof_on = mask != 0;
     return CWB_OK;
 }
 

@@ -85,6 +85,9 @@ struct ScatterPlan {
     int threads;
     size_t smem;      // dynamic shared memory bytes (incl. alignment slack)
     size_t part_floats;
+    int stage_cb;     // bins per chunk of the cluster epilogue's transposing stage
+    bool solve_stage_v;  // the solve stages each learner's design rows in shared memory
+    bool solve_stage_z;  // ... and its column-major design
     bool int_acc;     // exact fixed-point int32 histograms (false: FP32 atomics for heavily skewed bins)
 };
 
@@ -136,14 +139,13 @@ struct cwb_model {
     int32_t *l_bin = nullptr, *l_d = nullptr, *l_nstar = nullptr, *l_type = nullptr;
     double *l_xmin = nullptr, *l_xmax = nullptr;
     int32_t *l_degree = nullptr, *l_nknots = nullptr, *l_feat = nullptr;
-    float* part = nullptr;                // [clusters][cmax][nb_cta * f_lane]
-    float* u = nullptr;                   // [2][B][S] histograms per binning
+    float* part = nullptr;                // [clusters][cmax][f_lane][nb_cta] per-cluster histograms
     int32_t* cluster_slot = nullptr;      // [clusters]
     int32_t* slot_c0 = nullptr;           // [slots + 1]
     CUtensorMap tmap;                     // 2D map of the index matrix [B][n_pad]
     double* theta_it = nullptr;           // [2][K][D]
     double* q_it = nullptr;               // [2][K]
-    float* v = nullptr;                   // [2][S]
+    float* v = nullptr;                   // [2][K][S] fitted values Z^b theta of every learner per bin
     cwb::DevState* state = nullptr;
     double* risk_part = nullptr;
     float* blk_max = nullptr;             // [rows grid][2]
@@ -159,16 +161,24 @@ struct cwb_model {
     int32_t coef_valid_at = -1;
     int32_t done = 0;                     // iterations queued so far
     std::vector<int32_t> forced_host;     // pending host-side forced selections
-    // per-kernel timing (cwb_profile)
+    bool update_pending = false;          // the last iteration's update is not yet applied to f
+    // per-kernel timing (cwb_profile): bit c of prof_mask brackets kernel class c
     bool prof_on = false;
+    int prof_mask = 0;
+    cudaEvent_t prof_ph[8] = {};          // placeholder events of the profiling graph
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_pending;
     std::vector<cudaEvent_t> prof_pool;
     double prof_ms[4] = {0.0, 0.0, 0.0, 0.0};
     int64_t prof_launches[4] = {0, 0, 0, 0};
-    // CUDA graph of a fixed block of iterations
+    // CUDA graphs: a block of kGraphIters iterations and a single iteration; the
+    // profiling graph of one iteration carries event-record nodes around the
+    // profiled kernels (their events are swapped before every launch)
     cudaGraphExec_t graph_exec = nullptr;
+    cudaGraphExec_t graph1_exec = nullptr;
+    cudaGraphExec_t prof_exec = nullptr;
+    cudaGraph_t prof_graph = nullptr;     // kept alive: its event-record nodes address the exec's nodes
+    std::vector<std::pair<int, std::pair<cudaGraphNode_t, cudaGraphNode_t>>> prof_nodes;
     int graph_iters = 0;
-    int graph_cap = 0;                    // trace capacity the graph was captured with
 };
 
 namespace cwb {
@@ -202,6 +212,8 @@ cwb_status scatter_count_pass(cwb_model* m);
 cwb_status ensure_trace(cwb_model* m, int32_t cap);
 cwb_status launch_iterations(cwb_model* m, int32_t iters);
 cwb_status launch_final_update(cwb_model* m);
+cwb_status materialize(cwb_model* m);
+void release_graphs(cwb_model* m);
 cwb_status launch_initial_rows(cwb_model* m);
 cwb_status launch_aggregate(cwb_model* m);
 cwb_status read_device_error(cwb_model* m);

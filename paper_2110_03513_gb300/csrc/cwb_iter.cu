@@ -28,7 +28,7 @@ namespace cwb {
 namespace {
 
 constexpr int kRowThreads = 256;
-constexpr int kSolveThreads = 256;
+constexpr int kSolveThreads = 512;
 constexpr int kScatterThreads = 320;   // 8 consumer warps + 1 loader warp + 1 converter warp
 constexpr int kGraphIters = 32;
 
@@ -45,9 +45,12 @@ struct RowArgs {
     float* h;             // [n_pad][2] hi, lo (ACWB/HCWB)
     float* c;
     float* rw;
-    const float* v;       // [2][S]
+    const float* v;       // [2][K][S] fitted values Z^b theta of every learner per bin
     const int32_t* l_bin;
-    int S;
+    int S, K, D;
+    const double* theta_it;   // [2][K][D] coefficients of the last solve
+    double* tr_theta;         // [cap][2][D] trace of the selected coefficients
+    int trace_cap;
     int loss;
     double nu, gamma;
     int hybrid;
@@ -184,27 +187,48 @@ __global__ void __launch_bounds__(kRowThreads, 4) k_rows(RowArgs a)
     const IndT* ind = static_cast<const IndT*>(a.ind);
     const IndT* ind_sel = (st.k_sel >= 0) ? ind + (int64_t)a.l_bin[st.k_sel] * a.n_pad : nullptr;
     const IndT* ind_cor = (st.k_cor >= 0) ? ind + (int64_t)a.l_bin[st.k_cor] * a.n_pad : nullptr;
-    const float* v0 = a.v;
-    const float* v1 = a.v + a.S;
-    const DF nu = df_of(a.nu);
-
-    // pending update of iteration st.m (Algorithm 1 line "f = f + nu b"; Algorithm 3: f = g + nu b, h += eta b_cor)
-    DF om_p = {1.0f, 0.0f}, th_p = {0.0f, 0.0f}, eta_p = {0.0f, 0.0f};
-    if (pend && pm == kModeACWB) {
-        const double thm = 2.0 / ((double)st.m + 1.0);
-        om_p = df_of(1.0 - thm);
-        th_p = df_of(thm);
-        eta_p = df_of(a.gamma * a.nu / thm);
+    const float* v0 = a.v + (int64_t)max(st.k_sel, 0) * a.S;
+    const float* v1 = a.v + ((int64_t)a.K + max(st.k_cor, 0)) * a.S;
+    // the pending iteration's selected coefficients go to the trace (the next solve overwrites theta_it)
+    if (pend && blockIdx.x == 0 && st.m >= 1 && st.m - 1 < a.trace_cap) {
+        for (int e = threadIdx.x; e < 2 * a.D; e += blockDim.x) {
+            const int ch = e / a.D, i = e % a.D;
+            const int kk = ch ? st.k_cor : st.k_sel;
+            if (kk >= 0)
+                a.tr_theta[((int64_t)2 * (st.m - 1) + ch) * a.D + i] = a.theta_it[((int64_t)ch * a.K + kk) * a.D + i];
+        }
     }
-    // residuals of iteration st.m + 1
+
+    // Per-iteration scalars, one thread per block (FP64 is slow on this part and every value
+    // is uniform): pending update of iteration st.m (Algorithm 1: f = f + nu b; Algorithm 3:
+    // f = g + nu b, h += eta b_cor) and the momentum weights of iteration st.m + 1.
+    __shared__ DF sc_df[7];
     const int mode_n = st.mode;
     const int m_n = st.m + 1;
     const bool acwb_n = (mode_n == kModeACWB);
+    if (threadIdx.x == 0) {
+        DF om_p = {1.0f, 0.0f}, th_p = {0.0f, 0.0f}, eta_p = {0.0f, 0.0f};
+        if (pend && pm == kModeACWB) {
+            const double thm = 2.0 / ((double)st.m + 1.0);
+            om_p = df_of(1.0 - thm);
+            th_p = df_of(thm);
+            eta_p = df_of(a.gamma * a.nu / thm);
+        }
+        const double thn_d = 2.0 / ((double)m_n + 1.0);
+        sc_df[0] = om_p;
+        sc_df[1] = th_p;
+        sc_df[2] = eta_p;
+        sc_df[3] = df_of(1.0 - thn_d);
+        sc_df[4] = df_of(thn_d);
+        sc_df[5] = df_of((double)m_n / ((double)m_n + 1.0));
+        sc_df[6] = df_of(a.nu);
+    }
+    __syncthreads();
+    const DF om_p = sc_df[0], th_p = sc_df[1], eta_p = sc_df[2];
+    const DF om_n = sc_df[3], th_n = sc_df[4], cmul = sc_df[5];
     const int64_t n_act = (acwb_n && a.hybrid) ? a.n_tr : a.n;
-    const double thn_d = 2.0 / ((double)m_n + 1.0);
-    const DF om_n = df_of(1.0 - thn_d), th_n = df_of(thn_d);
-    const DF cmul = df_of((double)m_n / ((double)m_n + 1.0));
     const bool first_acwb = (m_n == 1);
+    const DF nu = sc_df[6];
     const bool need_bc = pend && pm == kModeACWB;
     const bool need_bc_resid = (KIND != kRowsUpdate) && acwb_n && !first_acwb;
     const bool eval_risk = (KIND == kRowsUpdate) && a.hybrid && (!st.risk_valid || (pend && pm == kModeACWB));
@@ -329,15 +353,19 @@ __global__ void __launch_bounds__(kRowThreads, 4) k_rows(RowArgs a)
             a.blk_max[2 * blockIdx.x + 1] = b1;
         }
     }
-    red[threadIdx.x] = risk_acc;
-    __syncthreads();
-    for (int s = kRowThreads / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    if (eval_risk) {
+        red[threadIdx.x] = risk_acc;
+        __syncthreads();
+        for (int s = kRowThreads / 2; s > 0; s >>= 1) {
+            if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+            __syncthreads();
+        }
+    } else {
         __syncthreads();
     }
     if (threadIdx.x == 0) {
         if (bad_blk) atomicOr(&a.state->err, kErrNonFinite);
-        if (a.risk_part) a.risk_part[blockIdx.x] = red[0];
+        if (eval_risk && a.risk_part) a.risk_part[blockIdx.x] = red[0];
         __threadfence();
         unsigned t = atomicAdd(&a.state->ticket_rows, 1u);
         is_last = (t == gridDim.x - 1);
@@ -427,7 +455,8 @@ struct ScatterArgs {
     const int32_t* slot_c0;        // [slots + 1]: first cluster of each slot
     int hybrid;
     uint32_t ind_off, r_off, q_off, hist_off, bar_off, stage_ind_bytes, stage_r_bytes;
-    float* part;                   // [clusters][cmax][nb_cta * F] (int32 fixed point or FP32)
+    float* part;                   // [clusters][cmax][F][nb_cta] (int32 fixed point or FP32)
+    int stage_cb;                  // bins per chunk of the epilogue's transposing stage
     uint32_t* err;
     int64_t count_rows;            // >= 0: counting pass over this many rows (every row adds 1)
 };
@@ -526,6 +555,9 @@ __device__ __forceinline__ int fixed_scale(uint32_t rmax_bits, int cnt_log2)
     return max(-120, min(100, 30 - cnt_log2 - e));
 }
 
+// 2^e as an FP32 value for -126 <= e <= 127 (fixed_scale keeps every exponent used here in range).
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }
+
 template <typename IndT, int CMAX, bool INT_ACC, bool RANGED>
 __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_constant__ CUtensorMap tmap, ScatterArgs a)
 {
@@ -611,8 +643,11 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
         float scale[2] = {1.0f, 1.0f};
         if (INT_ACC && !counting) {
             const int cidx = train_rows ? 1 : 0;
-            scale[0] = ldexpf(1.0f, fixed_scale(a.state->rmax_bits[0], a.state->cnt_log2[cidx]));
-            if (C == 2) scale[1] = ldexpf(1.0f, fixed_scale(a.state->rmax_bits[1], a.state->cnt_log2[cidx]));
+            scale[0] = pow2f(fixed_scale(a.state->rmax_bits[0], a.state->cnt_log2[cidx]));
+            if (C == 2) scale[1] = pow2f(fixed_scale(a.state->rmax_bits[1], a.state->cnt_log2[cidx]));
+        }
+        if (a.stage_rows % 128 != 0) {               // the vectorised conversion below needs it
+            if (lane == 0) atomicOr(a.err, kErrIndex);
         }
         for (int jt = 0; jt < ntiles; ++jt) {
             const int s = jt % a.stages;
@@ -626,12 +661,24 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
                 const float* rt = reinterpret_cast<const float*>(smem + a.r_off + (size_t)s * a.stage_r_bytes);
                 int* qt = reinterpret_cast<int*>(smem + a.q_off + (size_t)s * a.stage_r_bytes);
                 const int64_t row0 = (t_lo + jt) * a.stage_rows;
-                for (int i = lane; i < C * a.stage_rows; i += 32) {
-                    const int ch = i / a.stage_rows;
-                    int q;
-                    if (counting) q = (row0 + (i % a.stage_rows) < n_act) ? 1 : 0;
-                    else q = __float2int_rn(rt[i] * (ch ? scale[1] : scale[0]));
-                    qt[i] = q;
+                // 16-byte vectors, the loads of a lane issued together: the conversion sits on
+                // the pipeline's critical path and its shared-memory accesses queue behind the
+                // consumers' atomics, so it pays that queue once per batch, not once per value
+                const int total = C * a.stage_rows;          // multiple of 128
+#pragma unroll 4
+                for (int i0 = lane * 4; i0 < total; i0 += 128) {
+                    const int ch = i0 >= a.stage_rows ? 1 : 0;
+                    int4 q;
+                    if (counting) {
+                        const int64_t r = row0 + i0;
+                        q = make_int4(r < n_act, r + 1 < n_act, r + 2 < n_act, r + 3 < n_act);
+                    } else {
+                        const float sc = ch ? scale[1] : scale[0];
+                        const float4 x = *reinterpret_cast<const float4*>(rt + i0);
+                        q = make_int4(__float2int_rn(x.x * sc), __float2int_rn(x.y * sc), __float2int_rn(x.z * sc),
+                                      __float2int_rn(x.w * sc));
+                    }
+                    *reinterpret_cast<int4*>(qt + i0) = q;
                 }
             }
             __syncwarp();
@@ -704,115 +751,66 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
     }
     __syncthreads();
     cluster.sync();
-    // sum the cluster's histograms (fixed rank order), each CTA one slice of the bins, four
-    // 16-byte words per thread in flight; slices start on 16-byte boundaries
-    const int per = ((a.nb_cta * F + a.cs - 1) / a.cs + 3) & ~3;
-    const int e0 = min(a.nb_cta * F, rank * per), e1 = min(a.nb_cta * F, e0 + per);
+    // Sum the cluster's histograms (fixed rank order), each CTA one slice of the bins,
+    // and store them binning-major, part[cluster][ch][f][bin], so that a learner's
+    // partial histogram is one contiguous row.  The slice goes through the idle ring
+    // as [f][cb + 1] (odd row pitch): the 16-byte DSMEM reads in [bin][f] order and
+    // the transposed stores are both free of bank conflicts, the global stores coalesced.
+    const int nb = a.nb_cta;
+    const int bpr = ((nb + a.cs - 1) / a.cs + 3) & ~3;          // bins per rank, multiple of 4
+    const int bl0 = min(nb, rank * bpr), bl1 = min(nb, bl0 + bpr);
+    const int cb = a.stage_cb;                                  // bins per staged chunk, multiple of 4
+    const int fsh_e = __ffs(F) - 1;
+    Acc* stg = reinterpret_cast<Acc*>(smem);
     for (int ch = 0; ch < C; ++ch) {
-        Acc* dst = reinterpret_cast<Acc*>(a.part) + ((int64_t)cl * CMAX + ch) * (int64_t)a.nb_cta * F;
-        const int nvec = (e1 - e0) / 4;
-        for (int v0 = tid; v0 < nvec; v0 += 4 * blockDim.x) {
-            Acc acc[4][4];
+        Acc* dst = reinterpret_cast<Acc*>(a.part) + ((int64_t)cl * CMAX + ch) * (int64_t)F * nb;
+        for (int c0 = bl0; c0 < bl1; c0 += cb) {
+            const int c1 = min(bl1, c0 + cb);
+            const int nvec = ((c1 - c0) * F) >> 2;
+            for (int v0 = tid; v0 < nvec; v0 += 4 * blockDim.x) {
+                Acc acc[4][4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
+                for (int k = 0; k < 4; ++k)
 #pragma unroll
-                for (int t = 0; t < 4; ++t) acc[k][t] = Acc(0);
-            for (int r = 0; r < a.cs; ++r) {
-                const Acc* h = cluster.map_shared_rank(hist, r) + ch * a.ch_stride + e0;
+                    for (int t = 0; t < 4; ++t) acc[k][t] = Acc(0);
+                for (int r = 0; r < a.cs; ++r) {
+                    const Acc* h = cluster.map_shared_rank(hist, r) + ch * a.ch_stride + c0 * F;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int v = v0 + k * blockDim.x;
+                        if (v < nvec) {
+                            if (INT_ACC) {
+                                const int4 x = reinterpret_cast<const int4*>(h)[v];
+                                acc[k][0] += x.x; acc[k][1] += x.y; acc[k][2] += x.z; acc[k][3] += x.w;
+                            } else {
+                                const float4 x = reinterpret_cast<const float4*>(h)[v];
+                                acc[k][0] += x.x; acc[k][1] += x.y; acc[k][2] += x.z; acc[k][3] += x.w;
+                            }
+                        }
+                    }
+                }
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const int v = v0 + k * blockDim.x;
                     if (v < nvec) {
-                        if (INT_ACC) {
-                            const int4 x = reinterpret_cast<const int4*>(h)[v];
-                            acc[k][0] += x.x; acc[k][1] += x.y; acc[k][2] += x.z; acc[k][3] += x.w;
-                        } else {
-                            const float4 x = reinterpret_cast<const float4*>(h)[v];
-                            acc[k][0] += x.x; acc[k][1] += x.y; acc[k][2] += x.z; acc[k][3] += x.w;
+#pragma unroll
+                        for (int t = 0; t < 4; ++t) {
+                            const int e = 4 * v + t;
+                            stg[(e & (F - 1)) * (cb + 1) + (e >> fsh_e)] = acc[k][t];
                         }
                     }
                 }
             }
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int v = v0 + k * blockDim.x;
-                if (v < nvec)
-                    for (int t = 0; t < 4; ++t) dst[e0 + 4 * v + t] = acc[k][t];
+            __syncthreads();
+            const int nbc = c1 - c0;
+            for (int e = tid; e < F * nbc; e += blockDim.x) {
+                const int f = e / nbc, lb = e - f * nbc;
+                dst[(int64_t)f * nb + c0 + lb] = stg[f * (cb + 1) + lb];
             }
-        }
-        for (int e = e0 + 4 * nvec + tid; e < e1; e += blockDim.x) {
-            Acc x = Acc(0);
-            for (int r = 0; r < a.cs; ++r) x += cluster.map_shared_rank(hist, r)[ch * a.ch_stride + e];
-            dst[e] = x;
+            __syncthreads();
         }
     }
     cluster.sync();
-}
-
-// u[ch][b][l]: sum over the slot's clusters of the partial histograms (exact int64
-// sum of the fixed-point partials, or a compensated FP32 sum).  A block covers 64
-// consecutive [bin][binning] entries of one slot and channel; its four thread rows
-// split the clusters and meet in shared memory.
-template <bool INT_ACC>
-__global__ void __launch_bounds__(256) k_reduce_partials(const DevState* __restrict__ state, const float* __restrict__ part,
-                                                         const int32_t* __restrict__ slot_c0, int B, int F, int bin_ranges,
-                                                         int nb_cta, int cmax, int S, int hybrid, float* __restrict__ u)
-{
-    constexpr int kE = 16, kR = 16;                 // entries per block x cluster rows
-    __shared__ long long acc_i[kR][kE];
-    __shared__ float acc_f[kR][kE];
-    const int mode = state->mode;
-    const int C = (cmax == 2 && mode == kModeACWB) ? 2 : 1;
-    const int ch = blockIdx.z;
-    if (ch >= C) return;
-    const int slot = blockIdx.y;
-    const int g = slot / bin_ranges, br = slot % bin_ranges;
-    const int c0 = slot_c0[slot], c1 = slot_c0[slot + 1];
-    const int nbf = nb_cta * F;
-    const int e = blockIdx.x * kE + (threadIdx.x % kE);
-    const int row = threadIdx.x / kE;
-    if (INT_ACC) {
-        const int* pi = reinterpret_cast<const int*>(part);
-        long long acc = 0;
-        if (e < nbf) {
-            int c = c0 + row;
-            for (; c + kR < c1; c += 2 * kR) {
-                const int v0 = __ldcg(pi + ((int64_t)c * cmax + ch) * nbf + e);
-                const int v1 = __ldcg(pi + ((int64_t)(c + kR) * cmax + ch) * nbf + e);
-                acc += (long long)v0 + v1;
-            }
-            for (; c < c1; c += kR) acc += __ldcg(pi + ((int64_t)c * cmax + ch) * nbf + e);
-        }
-        acc_i[row][threadIdx.x % kE] = acc;
-    } else {
-        float sum = 0.0f, comp = 0.0f;
-        if (e < nbf)
-            for (int c = c0 + row; c < c1; c += kR) {
-                const float y = __ldcg(part + ((int64_t)c * cmax + ch) * nbf + e) - comp;
-                const float t = sum + y;
-                comp = (t - sum) - y;
-                sum = t;
-            }
-        acc_f[row][threadIdx.x % kE] = sum;
-    }
-    __syncthreads();
-    if (threadIdx.x < kE && e < nbf) {
-        float val;
-        if (INT_ACC) {
-            long long tot = 0;
-            for (int r = 0; r < kR; ++r) tot += acc_i[r][threadIdx.x];
-            const int sc = fixed_scale(state->rmax_bits[ch], state->cnt_log2[(hybrid && mode == kModeACWB) ? 1 : 0]);
-            val = (float)ldexp((double)tot, -sc);
-        } else {
-            float tot = 0.0f;
-            for (int r = 0; r < kR; ++r) tot += acc_f[r][threadIdx.x];
-            val = tot;
-        }
-        const int lb = e / F, f = e % F;
-        const int b = g * F + f;
-        const int l = br * nb_cta + lb;
-        if (b < B && l < S) u[((int64_t)ch * B + b) * S + l] = val;
-    }
 }
 
 // ceil(log2(largest bin count of any cluster)) from a counting pass of the scatter.
@@ -837,16 +835,31 @@ __global__ void k_count_max(const int* __restrict__ part, int clusters, int cmax
 
 // ---------------------------------------------------------------------------
 // Per-learner fit, criterion and argmin.
+//
+// One CTA per learner k on binning b: u_b[l] = sum over the clusters of b's slot
+// of the partial histograms (exact int64 sum of the fixed-point partials, or a
+// compensated FP32 sum), s = Z^b^T u (FP32, column-major design staged in shared
+// memory), theta = P s and Q = theta^T G theta - 2 theta^T s (FP64), and the
+// learner's update table v_k = Z^b theta (FP32).  The last CTA to finish takes
+// the argmin of Q per channel (ties: lowest k), writes the trace and advances the
+// iteration state.
+
+constexpr int kSolveChunk = 1024;      // bins of u held in shared memory per pass
+constexpr int kSolveBatch = 8;         // partial-histogram rows per thread and batch (per channel)
 
 struct SolveArgs {
     DevState* state;
-    int K, D, S, B;
-    const float* u;           // [2][B][S] histograms per binning
-    const float* zb;
-    const int32_t* zcol;
-    const int32_t* crange;
-    const int32_t* toff;
-    const float* ztab;
+    int K, D, S;
+    const float* part;        // [clusters][cmax][F][nb_cta]
+    const int32_t* slot_c0;   // [slots + 1]
+    int F, FE, cmax, nb_cta, bin_ranges, hybrid;   // binning b lives in lane b % FE of group b / FE
+    int stage_v;              // the learner's design rows (float4 + first column per bin) are staged
+    int stage_z;              // the learner's column-major design is staged
+    const float* zb;          // [K][S][4]
+    const int32_t* zcol;      // [K][S]
+    const int32_t* crange;    // [K][D][2]
+    const int32_t* toff;      // [K][D]
+    const float* ztab;        // [K][4 S]
     const int32_t* l_bin;
     const int32_t* l_d;
     const int32_t* l_nstar;
@@ -854,116 +867,295 @@ struct SolveArgs {
     const double* P;
     double* theta_it;         // [2][K][D]
     double* q_it;             // [2][K]
-    float* v;                 // [2][S]
+    float* v;                 // [2][K][S]
     int32_t* tr_k;            // [cap][2]
     int32_t* tr_mode;         // [cap]
-    double* tr_theta;         // [cap][2][D]
     double* tr_q;             // [cap][2]
     const int32_t* forced;    // [cap]
     int trace_cap;
 };
 
+// (best, index of best, second best) over a set of criteria; ties go to the lowest index.
+struct Best2 {
+    double q1, q2;
+    int k1;
+};
+
+__device__ __forceinline__ Best2 best2_merge(Best2 a, Best2 b)
+{
+    const bool take_b = b.k1 >= 0 && (a.k1 < 0 || b.q1 < a.q1 || (b.q1 == a.q1 && b.k1 < a.k1));
+    Best2 r;
+    if (take_b) {
+        r.q1 = b.q1;
+        r.k1 = b.k1;
+        r.q2 = fmin(a.q1, fmin(a.q2, b.q2));
+    } else {
+        r.q1 = a.q1;
+        r.k1 = a.k1;
+        r.q2 = fmin(a.q2, fmin(b.q1, b.q2));
+    }
+    return r;
+}
+
+__device__ __forceinline__ Best2 best2_shfl(Best2 x, int o)
+{
+    Best2 y;
+    y.q1 = __shfl_xor_sync(0xffffffffu, x.q1, o);
+    y.q2 = __shfl_xor_sync(0xffffffffu, x.q2, o);
+    y.k1 = __shfl_xor_sync(0xffffffffu, x.k1, o);
+    return y;
+}
+
+__device__ __forceinline__ void cp_async4(void* dst, const void* src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+template <bool INT_ACC>
 __global__ void __launch_bounds__(kSolveThreads) k_solve(SolveArgs a)
 {
+    constexpr int NW = kSolveThreads / 32;
+    constexpr int kColsPerWarp = (kMaxD + NW - 1) / NW;
     const int k = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const DevState st = *a.state;
     const int mode = st.mode;
     const int C = (mode == kModeACWB) ? 2 : 1;
     const int ph = (mode == kModeACWB) ? 0 : st.phase;
-    const int b = a.l_bin[k], d = a.l_d[k];
-    const int D = a.D;
-    extern __shared__ double dsm[];                     // P and G of this learner (d x d each)
+    const int b = a.l_bin[k], d = a.l_d[k], nst = a.l_nstar[k];
+    const int D = a.D, S = a.S;
+    // dynamic shared memory: P, G (D x D, FP64), the learner's design rows (float4 + first
+    // column per bin), u for one chunk of bins, the second cluster half's partial sums and,
+    // when it fits, the column-major design
+    extern __shared__ __align__(16) double dsm[];
     double* Ps = dsm;
-    double* Gs = dsm + (size_t)D * D;
+    double* Gs = Ps + (size_t)D * D;
+    float* u_s = reinterpret_cast<float*>(Gs + (size_t)D * D);                    // [2][kSolveChunk]
+    long long* pb = reinterpret_cast<long long*>(u_s + 2 * kSolveChunk);          // [2][kSolveChunk]
+    float4* zb_s = reinterpret_cast<float4*>(pb + 2 * kSolveChunk);              // [nst] when staged
+    int* zc_s = reinterpret_cast<int*>(zb_s + (a.stage_v ? S : 0));
+    float* zt_s = reinterpret_cast<float*>(zc_s + (a.stage_v ? ((S + 3) & ~3) : 0));   // [4 nst] when staged
     __shared__ double s_s[2][kMaxD], th_s[2][kMaxD], term[2][kMaxD];
     __shared__ bool is_last;
-    // stage P and G (independent of the histograms: their loads overlap the s sums below)
-    const double* Pk = a.P + ((int64_t)ph * a.K + k) * D * D;
-    const double* Gk = a.G + ((int64_t)ph * a.K + k) * D * D;
-    for (int e = tid; e < d * d; e += blockDim.x) {
-        const int i = e / d, j = e % d;
-        Ps[e] = __ldg(Pk + i * D + j);
-        Gs[e] = __ldg(Gk + i * D + j);
-    }
-    // s = Z^b^T u for every channel: warp per column, lanes over the column's contiguous bin range
-    const float* zt = a.ztab + (int64_t)k * kMaxNnz * a.S;
-    const float* u0 = a.u + (int64_t)b * a.S;
-    const float* u1 = a.u + ((int64_t)a.B + b) * a.S;
+
+    // ---- static per-learner data (independent of this iteration): asynchronous copies, one round trip
     {
-        // each warp sums up to kColsPerWarp columns at once (more loads in flight)
-        constexpr int kColsPerWarp = kMaxD / (kSolveThreads / 32);
-        const int nw = blockDim.x / 32;
-        int lo[kColsPerWarp], len[kColsPerWarp];
-        const float* zc[kColsPerWarp];
-        float acc0[kColsPerWarp], acc1[kColsPerWarp];
-        int maxlen = 0;
-#pragma unroll
-        for (int c = 0; c < kColsPerWarp; ++c) {
-            const int j = warp + c * nw;
-            lo[c] = 0;
-            len[c] = 0;
-            zc[c] = zt;
-            acc0[c] = acc1[c] = 0.0f;
-            if (j < d) {
-                lo[c] = a.crange[((int64_t)k * D + j) * 2];
-                len[c] = a.crange[((int64_t)k * D + j) * 2 + 1] - lo[c];
-                zc[c] = zt + a.toff[(int64_t)k * D + j];
-                maxlen = max(maxlen, len[c]);
+        const double* Pk = a.P + ((int64_t)ph * a.K + k) * D * D;
+        const double* Gk = a.G + ((int64_t)ph * a.K + k) * D * D;
+        for (int e = tid; e < D * D; e += blockDim.x) {
+            cp_async8(Ps + e, Pk + e);
+            cp_async8(Gs + e, Gk + e);
+        }
+        if (a.stage_v) {
+            const float4* zb_g = reinterpret_cast<const float4*>(a.zb) + (int64_t)k * S;
+            const int* zc_g = a.zcol + (int64_t)k * S;
+            for (int e = tid; e < nst; e += blockDim.x) {
+                cp_async16(zb_s + e, zb_g + e);
+                cp_async4(zc_s + e, zc_g + e);
             }
         }
-        for (int t = lane; t < maxlen; t += 32) {
+        if (a.stage_z) {
+            const float4* zt4 = reinterpret_cast<const float4*>(a.ztab + (int64_t)k * kMaxNnz * S);
+            for (int e = tid; e < nst; e += blockDim.x) cp_async16(reinterpret_cast<float4*>(zt_s) + e, zt4 + e);
+        }
+    }
+    const float* zt = a.stage_z ? zt_s : a.ztab + (int64_t)k * kMaxNnz * S;
+    const float4* zbp = a.stage_v ? zb_s : reinterpret_cast<const float4*>(a.zb) + (int64_t)k * S;
+    const int* zcp = a.stage_v ? zc_s : a.zcol + (int64_t)k * S;
+    int c_lo[kColsPerWarp], c_len[kColsPerWarp], c_off[kColsPerWarp];
 #pragma unroll
-            for (int c = 0; c < kColsPerWarp; ++c) {
-                if (t < len[c]) {
-                    const float z = __ldg(zc[c] + t);
-                    acc0[c] = fmaf(z, __ldcg(u0 + lo[c] + t), acc0[c]);
-                    if (C == 2) acc1[c] = fmaf(z, __ldcg(u1 + lo[c] + t), acc1[c]);
+    for (int c = 0; c < kColsPerWarp; ++c) {
+        const int j = warp + c * NW;
+        c_lo[c] = 0;
+        c_len[c] = 0;
+        c_off[c] = 0;
+        if (j < d) {
+            c_lo[c] = __ldg(a.crange + ((int64_t)k * D + j) * 2);
+            c_len[c] = __ldg(a.crange + ((int64_t)k * D + j) * 2 + 1) - c_lo[c];
+            c_off[c] = __ldg(a.toff + (int64_t)k * D + j);
+        }
+    }
+    if (tid < 2 * kMaxD) {
+        th_s[tid / kMaxD][tid % kMaxD] = 0.0;
+        s_s[tid / kMaxD][tid % kMaxD] = 0.0;
+    }
+
+    // ---- u = sum of the slot's partial histograms, then s = Z^b^T u, in chunks of bins.
+    // Thread (i, half): bins 4i..4i+3 of the chunk, clusters of parity `half`.
+    const int g = b / a.FE, f = b - g * a.FE;
+    const int64_t cl_stride = (int64_t)a.cmax * a.F * a.nb_cta;
+    const int cidx = (a.hybrid && mode == kModeACWB) ? 1 : 0;
+    float scl0 = 1.0f, scl1 = 1.0f;
+    if (INT_ACC) {
+        scl0 = pow2f(-fixed_scale(st.rmax_bits[0], st.cnt_log2[cidx]));
+        scl1 = pow2f(-fixed_scale(st.rmax_bits[1], st.cnt_log2[cidx]));
+    }
+    const int gi = tid & (kSolveThreads / 2 - 1), half = tid / (kSolveThreads / 2);
+    float acc0[kColsPerWarp], acc1[kColsPerWarp];
+#pragma unroll
+    for (int c = 0; c < kColsPerWarp; ++c) acc0[c] = acc1[c] = 0.0f;
+    for (int L0 = 0; L0 < nst; L0 += kSolveChunk) {
+        const int L1 = min(nst, L0 + kSolveChunk);
+        const bool mine = 4 * gi < L1 - L0;
+        int c0 = 0, c1 = 0, lb = 0;
+        if (mine) {
+            const int l0 = L0 + 4 * gi;
+            const int br = l0 / a.nb_cta;
+            lb = l0 - br * a.nb_cta;
+            const int slot = g * a.bin_ranges + br;
+            c0 = __ldg(a.slot_c0 + slot);
+            c1 = __ldg(a.slot_c0 + slot + 1);
+        }
+        long long it0[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+        float ft[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+        float fc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+        for (int cc = c0 + half; cc < c1; cc += 2 * kSolveBatch) {
+#pragma unroll
+            for (int ch = 0; ch < 2; ++ch) {
+                if (ch >= C) break;
+                const float* base = a.part + ((int64_t)ch * a.F + f) * a.nb_cta + lb;
+                int4 x[kSolveBatch];
+#pragma unroll
+                for (int q = 0; q < kSolveBatch; ++q) {
+                    const int c = cc + 2 * q;
+                    x[q] = c < c1 ? __ldcg(reinterpret_cast<const int4*>(base + c * cl_stride)) : make_int4(0, 0, 0, 0);
+                }
+#pragma unroll
+                for (int q = 0; q < kSolveBatch; ++q) {
+                    if (INT_ACC) {
+                        it0[ch][0] += x[q].x; it0[ch][1] += x[q].y; it0[ch][2] += x[q].z; it0[ch][3] += x[q].w;
+                    } else {
+                        const float xv[4] = {__int_as_float(x[q].x), __int_as_float(x[q].y), __int_as_float(x[q].z),
+                                             __int_as_float(x[q].w)};
+#pragma unroll
+                        for (int t = 0; t < 4; ++t) {       // compensated sum
+                            const float y = xv[t] - fc[ch][t];
+                            const float tt = ft[ch][t] + y;
+                            fc[ch][t] = (tt - ft[ch][t]) - y;
+                            ft[ch][t] = tt;
+                        }
+                    }
                 }
             }
         }
+        // the odd-cluster half hands its sums to the even half
+        if (half == 1 && mine) {
+#pragma unroll
+            for (int ch = 0; ch < 2; ++ch)
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    if (ch >= C) break;
+                    if (INT_ACC) pb[ch * kSolveChunk + 4 * gi + t] = it0[ch][t];
+                    else reinterpret_cast<float*>(pb)[ch * kSolveChunk + 4 * gi + t] = ft[ch][t] - fc[ch][t];
+                }
+        }
+        __syncthreads();
+        if (half == 0 && mine) {
+#pragma unroll
+            for (int ch = 0; ch < 2; ++ch) {
+                if (ch >= C) break;
+                float o[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    if (INT_ACC) {
+                        const long long tot = it0[ch][t] + pb[ch * kSolveChunk + 4 * gi + t];
+                        o[t] = (float)tot * (ch ? scl1 : scl0);     // exact sum, one rounding, power-of-two scale
+                    } else {
+                        o[t] = (ft[ch][t] - fc[ch][t]) + reinterpret_cast<float*>(pb)[ch * kSolveChunk + 4 * gi + t];
+                    }
+                }
+                *reinterpret_cast<float4*>(u_s + ch * kSolveChunk + 4 * gi) = make_float4(o[0], o[1], o[2], o[3]);
+            }
+        }
+        if (L0 == 0) cp_async_wait_all();              // the design must be in shared memory before s
+        __syncthreads();
 #pragma unroll
         for (int c = 0; c < kColsPerWarp; ++c) {
-            for (int o = 16; o > 0; o >>= 1) {
-                acc0[c] += __shfl_xor_sync(0xffffffffu, acc0[c], o);
-                acc1[c] += __shfl_xor_sync(0xffffffffu, acc1[c], o);
-            }
-            const int j = warp + c * nw;
-            if (lane == 0 && j < d) {
-                s_s[0][j] = (double)acc0[c];
-                s_s[1][j] = (double)acc1[c];
+            const int from = max(c_lo[c], L0), to = min(c_lo[c] + c_len[c], L1);
+            const float* zc = zt + c_off[c] - c_lo[c];
+            for (int t = from + lane; t < to; t += 32) {
+                const float z = zc[t];
+                acc0[c] = fmaf(z, u_s[t - L0], acc0[c]);
+                if (C == 2) acc1[c] = fmaf(z, u_s[kSolveChunk + t - L0], acc1[c]);
             }
         }
+        __syncthreads();
     }
-    __syncthreads();
-    // theta = P s (FP64); thread (ch, i)
-    if (tid < C * kMaxD) {
-        const int ch = tid / kMaxD, i = tid % kMaxD;
-        if (i < d) {
-            double t = 0.0;
-            for (int jj = 0; jj < d; ++jj) t += Ps[i * d + jj] * s_s[ch][jj];
-            th_s[ch][i] = t;
+#pragma unroll
+    for (int c = 0; c < kColsPerWarp; ++c) {
+        for (int o = 16; o > 0; o >>= 1) {
+            acc0[c] += __shfl_xor_sync(0xffffffffu, acc0[c], o);
+            acc1[c] += __shfl_xor_sync(0xffffffffu, acc1[c], o);
+        }
+        const int j = warp + c * NW;
+        if (lane == 0 && j < d) {
+            s_s[0][j] = (double)acc0[c];
+            s_s[1][j] = (double)acc1[c];
         }
     }
     __syncthreads();
-    // Q = theta^T G theta - 2 theta^T s (FP64)
-    if (tid < C * kMaxD) {
-        const int ch = tid / kMaxD, i = tid % kMaxD;
-        if (i < d) {
-            double gt = 0.0;
-            for (int jj = 0; jj < d; ++jj) gt += Gs[i * d + jj] * th_s[ch][jj];
-            term[ch][i] = th_s[ch][i] * (gt - 2.0 * s_s[ch][i]);
-        }
+
+    // ---- theta = P s and the criterion terms (FP64): four lanes per row, partial sums over j = q mod 4
+    const int rows4 = C * d * 4;
+    for (int base = 0; base < rows4; base += blockDim.x) {
+        const int e = base + tid;
+        const bool valid = e < rows4;
+        const int ch = valid ? e / (4 * d) : 0;
+        const int rem = e - ch * 4 * d;
+        const int i = rem >> 2, q = rem & 3;
+        double p = 0.0;
+        if (valid)
+            for (int j = q; j < d; j += 4) p = fma(Ps[i * D + j], s_s[ch][j], p);
+        p += __shfl_xor_sync(0xffffffffu, p, 1);
+        p += __shfl_xor_sync(0xffffffffu, p, 2);
+        if (valid && q == 0) th_s[ch][i] = p;
     }
     __syncthreads();
-    if (tid < C * D) {
-        const int ch = tid / D, i = tid % D;
-        a.theta_it[((int64_t)ch * a.K + k) * D + i] = i < d ? th_s[ch][i] : 0.0;
+    for (int base = 0; base < rows4; base += blockDim.x) {
+        const int e = base + tid;
+        const bool valid = e < rows4;
+        const int ch = valid ? e / (4 * d) : 0;
+        const int rem = e - ch * 4 * d;
+        const int i = rem >> 2, q = rem & 3;
+        double p = 0.0;
+        if (valid)
+            for (int j = q; j < d; j += 4) p = fma(Gs[i * D + j], th_s[ch][j], p);
+        p += __shfl_xor_sync(0xffffffffu, p, 1);
+        p += __shfl_xor_sync(0xffffffffu, p, 2);
+        if (valid && q == 0) term[ch][i] = th_s[ch][i] * (p - 2.0 * s_s[ch][i]);
     }
-    if (tid < C) {
-        double q = 0.0;
-        for (int jj = 0; jj < d; ++jj) q += term[tid][jj];
-        a.q_it[(int64_t)tid * a.K + k] = q;
+    __syncthreads();
+    if (warp < C) {
+        // Q = sum_i term_i: fixed-order tree over the warp
+        double x = 0.0;
+        for (int i = lane; i < d; i += 32) x += term[warp][i];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) a.q_it[(int64_t)warp * a.K + k] = x;
+    }
+    for (int e = tid; e < C * D; e += blockDim.x) {
+        const int ch = e / D, i = e - (e / D) * D;
+        a.theta_it[((int64_t)ch * a.K + k) * D + i] = th_s[ch][i];
+    }
+    // ---- update table of this learner, v_k = Z^b theta (FP32)
+    for (int e = tid; e < C * nst; e += blockDim.x) {
+        const int ch = e >= nst ? 1 : 0, l = e - ch * nst;
+        const int c0 = zcp[l];
+        const float4 z = zbp[l];
+        float acc = 0.0f;
+        if (c0 < D) acc = fmaf(z.x, (float)th_s[ch][c0], acc);
+        if (c0 + 1 < D) acc = fmaf(z.y, (float)th_s[ch][c0 + 1], acc);
+        if (c0 + 2 < D) acc = fmaf(z.z, (float)th_s[ch][c0 + 2], acc);
+        if (c0 + 3 < D) acc = fmaf(z.w, (float)th_s[ch][c0 + 3], acc);
+        a.v[((int64_t)ch * a.K + k) * S + l] = acc;
     }
     __syncthreads();
     if (tid == 0) {
@@ -974,104 +1166,59 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(SolveArgs a)
     __syncthreads();
     if (!is_last) return;
     __threadfence();
-
-    // ---- last CTA: argmin per channel, update tables, trace, state
-    __shared__ double cand_q[2 * kSolveThreads];
-    __shared__ int cand_k[kSolveThreads];
-    __shared__ int best_k[2];
-    __shared__ float th32[2][kMaxD];
+    // ---- last CTA: argmin per channel, trace, state
+    __shared__ Best2 cand[2][NW];
     __shared__ uint32_t bad;
     if (tid == 0) bad = 0;
     __syncthreads();
-    const int it = st.m;
-    const bool trace_ok = it < a.trace_cap;
     for (int ch = 0; ch < C; ++ch) {
-        // per-thread best and second best, then a tree merge (ties go to the lowest index)
-        double q1 = INFINITY, q2 = INFINITY;
-        int k1 = -1;
+        Best2 x = {INFINITY, INFINITY, -1};
         for (int kk = tid; kk < a.K; kk += blockDim.x) {
             double q = __ldcg(a.q_it + (int64_t)ch * a.K + kk);
             if (!(q == q) || isinf(q)) {
                 atomicOr(&bad, 1u);
                 q = INFINITY;
             }
-            if (k1 < 0 || q < q1) { q2 = q1; q1 = q; k1 = kk; }
-            else if (q < q2) { q2 = q; }
+            x = best2_merge(x, Best2{q, INFINITY, kk});
         }
-        cand_q[2 * tid] = q1;
-        cand_q[2 * tid + 1] = q2;
-        cand_k[tid] = k1;
-        __syncthreads();
-        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-            if (tid < w) {
-                const double a1 = cand_q[2 * tid], a2 = cand_q[2 * tid + 1];
-                const double b1 = cand_q[2 * (tid + w)], b2 = cand_q[2 * (tid + w) + 1];
-                const int ka = cand_k[tid], kb2 = cand_k[tid + w];
-                bool take_b = kb2 >= 0 && (ka < 0 || b1 < a1 || (b1 == a1 && kb2 < ka));
-                if (take_b) {
-                    cand_q[2 * tid] = b1;
-                    cand_q[2 * tid + 1] = fmin(fmin(a1, a2), b2);
-                    cand_k[tid] = kb2;
-                } else {
-                    cand_q[2 * tid + 1] = fmin(a2, fmin(b1, b2));
-                }
-            }
-            __syncthreads();
-        }
-        if (tid == 0) {
-            int i1 = cand_k[0] < 0 ? 0 : cand_k[0];
+        for (int o = 16; o > 0; o >>= 1) x = best2_merge(x, best2_shfl(x, o));
+        if (lane == 0) cand[ch][warp] = x;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const int it = st.m;
+        const bool trace_ok = it < a.trace_cap;
+        DevState* S_ = a.state;
+        int best_k[2] = {-1, -1};
+        for (int ch = 0; ch < C; ++ch) {
+            Best2 x = cand[ch][0];
+            for (int w = 1; w < NW; ++w) x = best2_merge(x, cand[ch][w]);
+            int i1 = x.k1 < 0 ? 0 : x.k1;
             if (ch == 0 && trace_ok && a.forced) {
-                int fk = a.forced[it];
+                const int fk = a.forced[it];
                 if (fk >= 0 && fk < a.K) i1 = fk;
             }
             best_k[ch] = i1;
             if (trace_ok) {
                 a.tr_k[2 * it + ch] = i1;
                 if (ch == 0) {
-                    a.tr_q[2 * it] = cand_q[0];
-                    a.tr_q[2 * it + 1] = cand_q[1];
+                    a.tr_q[2 * it] = x.q1;
+                    a.tr_q[2 * it + 1] = x.q2;
                 }
             }
         }
-        __syncthreads();
-    }
-    // update tables v[ch] = Z^b theta of the winners (FP32)
-    for (int e = tid; e < C * D; e += blockDim.x) {
-        const int ch = e / D, i = e % D;
-        const double tv = __ldcg(a.theta_it + ((int64_t)ch * a.K + best_k[ch]) * D + i);
-        th32[ch][i] = (float)tv;
-        if (trace_ok) a.tr_theta[((int64_t)2 * it + ch) * D + i] = tv;
-    }
-    __syncthreads();
-    for (int ch = 0; ch < C; ++ch) {
-        const int kb = best_k[ch];
-        const int nstb = a.l_nstar[kb];
-        for (int l = tid; l < nstb; l += blockDim.x) {
-            const int c0 = a.zcol[(int64_t)kb * a.S + l];
-            const float4 z = reinterpret_cast<const float4*>(a.zb)[(int64_t)kb * a.S + l];
-            float acc = 0.0f;
-            if (c0 < D) acc = fmaf(z.x, th32[ch][c0], acc);
-            if (c0 + 1 < D) acc = fmaf(z.y, th32[ch][c0 + 1], acc);
-            if (c0 + 2 < D) acc = fmaf(z.z, th32[ch][c0 + 2], acc);
-            if (c0 + 3 < D) acc = fmaf(z.w, th32[ch][c0 + 3], acc);
-            a.v[(int64_t)ch * a.S + l] = acc;
-        }
-    }
-    __syncthreads();
-    if (tid == 0) {
-        DevState* S = a.state;
         if (trace_ok) {
             a.tr_mode[it] = mode;
             if (C == 1) a.tr_k[2 * it + 1] = -1;
         } else {
-            atomicOr(&S->err, kErrIndex);
+            atomicOr(&S_->err, kErrIndex);
         }
-        if (bad) atomicOr(&S->err, kErrNonFinite);
-        S->k_sel = best_k[0];
-        S->k_cor = (C == 2) ? best_k[1] : -1;
-        S->pend_mode = mode;
-        S->m = st.m + 1;
-        S->ticket_solve = 0;
+        if (bad) atomicOr(&S_->err, kErrNonFinite);
+        S_->k_sel = best_k[0];
+        S_->k_cor = (C == 2) ? best_k[1] : -1;
+        S_->pend_mode = mode;
+        S_->m = st.m + 1;
+        S_->ticket_solve = 0;
     }
 }
 
@@ -1130,6 +1277,11 @@ RowArgs row_args(cwb_model* m)
     a.v = m->v;
     a.l_bin = m->l_bin;
     a.S = m->nstar_max;
+    a.K = m->K;
+    a.D = m->d_max;
+    a.theta_it = m->theta_it;
+    a.tr_theta = m->tr_theta;
+    a.trace_cap = m->trace_cap;
     a.loss = m->cfg.loss;
     a.nu = m->cfg.nu;
     a.gamma = m->cfg.gamma;
@@ -1201,6 +1353,7 @@ ScatterArgs scatter_args(cwb_model* m)
     a.stage_ind_bytes = P.stage_ind_bytes;
     a.stage_r_bytes = P.stage_r_bytes;
     a.part = m->part;
+    a.stage_cb = P.stage_cb;
     a.err = &m->state->err;
     a.count_rows = -1;
     return a;
@@ -1222,29 +1375,34 @@ void launch_scatter(cwb_model* m, cudaStream_t s)
     launch_scatter_args(m, s, scatter_args(m), m->plan.int_acc);
 }
 
-void launch_reduce(cwb_model* m, cudaStream_t s)
+size_t solve_smem(const cwb_model* m, bool stage_v, bool stage_z)
 {
-    const ScatterPlan& P = m->plan;
-    dim3 grid((P.nb_cta * P.f_lane + 15) / 16, P.slots, P.cmax);
-    if (P.int_acc)
-        k_reduce_partials<true><<<grid, 256, 0, s>>>(m->state, m->part, m->slot_c0, m->B, P.f_lane, P.bin_ranges,
-                                                     P.nb_cta, P.cmax, m->nstar_max, m->hybrid ? 1 : 0, m->u);
-    else
-        k_reduce_partials<false><<<grid, 256, 0, s>>>(m->state, m->part, m->slot_c0, m->B, P.f_lane, P.bin_ranges,
-                                                      P.nb_cta, P.cmax, m->nstar_max, m->hybrid ? 1 : 0, m->u);
+    const size_t S = m->nstar_max;
+    size_t b = sizeof(double) * 2 * (size_t)m->d_max * m->d_max;        // P, G
+    b += sizeof(float) * 2 * kSolveChunk + sizeof(long long) * 2 * kSolveChunk;   // u chunk, half sums
+    if (stage_v) b += 16 * S + 4 * ((S + 3) & ~size_t(3));              // design rows, first columns
+    if (stage_z) b += sizeof(float) * kMaxNnz * S;                       // column-major design
+    return b;
 }
-
-size_t solve_smem(const cwb_model* m) { return sizeof(double) * 2 * (size_t)m->d_max * m->d_max; }
 
 void launch_solve(cwb_model* m, cudaStream_t s)
 {
+    const ScatterPlan& P = m->plan;
     SolveArgs a;
     a.state = m->state;
     a.K = m->K;
     a.D = m->d_max;
     a.S = m->nstar_max;
-    a.B = m->B;
-    a.u = m->u;
+    a.part = m->part;
+    a.slot_c0 = m->slot_c0;
+    a.F = P.f_lane;
+    a.FE = P.fe;
+    a.cmax = P.cmax;
+    a.nb_cta = P.nb_cta;
+    a.bin_ranges = P.bin_ranges;
+    a.hybrid = m->hybrid ? 1 : 0;
+    a.stage_v = P.solve_stage_v ? 1 : 0;
+    a.stage_z = P.solve_stage_z ? 1 : 0;
     a.zb = m->zb;
     a.zcol = m->zcol;
     a.crange = m->crange;
@@ -1260,70 +1418,37 @@ void launch_solve(cwb_model* m, cudaStream_t s)
     a.v = m->v;
     a.tr_k = m->tr_k;
     a.tr_mode = m->tr_mode;
-    a.tr_theta = m->tr_theta;
     a.tr_q = m->tr_q;
     a.forced = m->forced;
     a.trace_cap = m->trace_cap;
-    k_solve<<<m->K, kSolveThreads, solve_smem(m), s>>>(a);
+    const size_t smem = solve_smem(m, P.solve_stage_v, P.solve_stage_z);
+    if (P.int_acc) k_solve<true><<<m->K, kSolveThreads, smem, s>>>(a);
+    else k_solve<false><<<m->K, kSolveThreads, smem, s>>>(a);
 }
 
-// Event pair around one launch when profiling (never while capturing a graph).
-struct ProfScope {
-    cwb_model* m;
-    cudaStream_t s;
-    int cls;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    static cudaEvent_t take(cwb_model* m)
-    {
-        if (!m->prof_pool.empty()) {
-            cudaEvent_t e = m->prof_pool.back();
-            m->prof_pool.pop_back();
-            return e;
-        }
-        cudaEvent_t e = nullptr;
-        cudaEventCreate(&e);
-        return e;
-    }
-    ProfScope(cwb_model* mm, cudaStream_t ss, int c) : m(mm), s(ss), cls(c)
-    {
-        if (m->prof_on && s == m->stream) {
-            e0 = take(m);
-            e1 = take(m);
-            if (e0) cudaEventRecord(e0, s);
-        }
-    }
-    ~ProfScope()
-    {
-        if (e0 && e1) {
-            cudaEventRecord(e1, s);
-            m->prof_pending.push_back({cls, {e0, e1}});
-        }
-    }
-};
-
-void enqueue_iteration(cwb_model* m, cudaStream_t s)
+// One iteration's launches.  With a profiling mask (only while capturing the
+// profiling graph) the kernels of the selected classes are bracketed by external
+// event-record nodes on placeholder events; the placeholders are replaced by fresh
+// events before every launch of that graph.
+void enqueue_iteration(cwb_model* m, cudaStream_t s, int mask)
 {
-    {
-        ProfScope p(m, s, 0);
-        if (m->hybrid) {
-            launch_rows<kRowsUpdate>(m, s);
-            launch_rows<kRowsResid>(m, s);
-        } else {
-            launch_rows<kRowsFused>(m, s);
-        }
+    auto mark = [&](int cls, int edge) {
+        if (mask & (1 << cls)) cudaEventRecordWithFlags(m->prof_ph[2 * cls + edge], s, cudaEventRecordExternal);
+    };
+    mark(0, 0);
+    if (m->hybrid) {
+        launch_rows<kRowsUpdate>(m, s);
+        launch_rows<kRowsResid>(m, s);
+    } else {
+        launch_rows<kRowsFused>(m, s);
     }
-    {
-        ProfScope p(m, s, 1);
-        launch_scatter(m, s);
-    }
-    {
-        ProfScope p(m, s, 3);
-        launch_reduce(m, s);
-    }
-    {
-        ProfScope p(m, s, 2);
-        launch_solve(m, s);
-    }
+    mark(0, 1);
+    mark(1, 0);
+    launch_scatter(m, s);
+    mark(1, 1);
+    mark(2, 0);
+    launch_solve(m, s);
+    mark(2, 1);
 }
 
 template <typename IndT, int CMAX>
@@ -1387,13 +1512,12 @@ EncodeTiledFn encode_tiled_fn()
 
 cwb_status plan_scatter(cwb_model* m)
 {
-    CWB_CUDA_TRY(cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)solve_smem(m)));
     int optin = 0, sms = num_sms(m->device);
     CWB_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, m->device));
     const int budget = optin - 1024 - 512;          // alignment slack and mbarriers
     const int cmax = m->accel ? 2 : 1;
     const int elem = m->ind_bytes;
-    const int nbins = m->nstar_max;
+    const int nbins = (m->nstar_max + 3) & ~3;     // bins per binning rounded to 16-byte rows
     const int B = m->B;
     int pow2B = 1;
     while (pow2B < B) pow2B <<= 1;
@@ -1424,7 +1548,7 @@ cwb_status plan_scatter(cwb_model* m)
     const int F = P.f_lane;
     P.groups = (B + F - 1) / F;
     P.fe = (B + P.groups - 1) / P.groups;          // binnings per group, balanced across groups
-    P.nb_cta = (nbins + P.bin_ranges - 1) / P.bin_ranges;
+    P.nb_cta = (((nbins + P.bin_ranges - 1) / P.bin_ranges) + 3) & ~3;
     P.nbins_pad = P.nb_cta * P.bin_ranges;
     P.ch_stride = ch_stride_for(P.nb_cta, F);
     P.box_bytes = ((P.fe * P.stage_rows * elem + 127) / 128) * 128;
@@ -1469,6 +1593,29 @@ cwb_status plan_scatter(cwb_model* m)
     }
     P.clusters = (int)cl_slot.size();
     P.part_floats = (size_t)P.clusters * cmax * P.nb_cta * F;
+    {
+        // the cluster epilogue stages [F][cb + 1] values in the ring, which precedes the histograms
+        const int bpr = ((P.nb_cta + P.cs - 1) / P.cs + 3) & ~3;
+        const int fit = (((int)P.hist_off / (4 * F)) - 1) & ~3;
+        P.stage_cb = std::min(bpr, fit);
+        if (P.stage_cb < 4) {
+            set_error("scatter plan: no room for the epilogue stage");
+            return CWB_ECUDA;
+        }
+    }
+    // the solve stages the learner's column-major design when it fits
+    {
+        const int solve_static = 8 * 1024;
+        P.solve_stage_v = (int)solve_smem(m, true, false) + solve_static <= optin;
+        P.solve_stage_z = P.solve_stage_v && (int)solve_smem(m, true, true) + solve_static <= optin;
+        const int need = (int)solve_smem(m, P.solve_stage_v, P.solve_stage_z);
+        if (need + solve_static > optin) {
+            set_error("solve kernel: basis dimension too large for shared memory");
+            return CWB_EINVAL;
+        }
+        CWB_CUDA_TRY(cudaFuncSetAttribute(k_solve<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, need));
+        CWB_CUDA_TRY(cudaFuncSetAttribute(k_solve<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, need));
+    }
     m->plan = P;
     CWB_TRY(dev_alloc((void**)&m->cluster_slot, sizeof(int32_t) * cl_slot.size(), m->stream));
     CWB_TRY(dev_alloc((void**)&m->slot_c0, sizeof(int32_t) * slot_c0.size(), m->stream));
@@ -1559,26 +1706,72 @@ cwb_status ensure_trace(cwb_model* m, int32_t need)
     m->tr_theta = tt;
     m->tr_q = tq;
     m->trace_cap = cap;
-    if (m->graph_exec) {                 // pointers baked into the graph changed
-        cudaGraphExecDestroy(m->graph_exec);
-        m->graph_exec = nullptr;
-    }
+    release_graphs(m);                   // pointers baked into the graphs changed
     return CWB_OK;
 }
 
-static cwb_status build_graph(cwb_model* m)
+void release_graphs(cwb_model* m)
+{
+    if (m->graph_exec) cudaGraphExecDestroy(m->graph_exec);
+    if (m->graph1_exec) cudaGraphExecDestroy(m->graph1_exec);
+    if (m->prof_exec) cudaGraphExecDestroy(m->prof_exec);
+    if (m->prof_graph) cudaGraphDestroy(m->prof_graph);
+    m->graph_exec = m->graph1_exec = m->prof_exec = nullptr;
+    m->prof_graph = nullptr;
+    m->prof_nodes.clear();
+}
+
+// Captures `iters` iterations into an executable graph (profiling mask: see enqueue_iteration).
+static cwb_status capture_graph(cwb_model* m, int iters, int mask, cudaGraphExec_t* out)
 {
     if (!m->capture_stream) CWB_CUDA_TRY(cudaStreamCreateWithFlags(&m->capture_stream, cudaStreamNonBlocking));
+    if (mask && !m->prof_ph[0])
+        for (auto& e : m->prof_ph) CWB_CUDA_TRY(cudaEventCreate(&e));
     cudaGraph_t graph = nullptr;
     CWB_CUDA_TRY(cudaStreamBeginCapture(m->capture_stream, cudaStreamCaptureModeThreadLocal));
-    for (int i = 0; i < kGraphIters; ++i) enqueue_iteration(m, m->capture_stream);
+    for (int i = 0; i < iters; ++i) enqueue_iteration(m, m->capture_stream, mask);
     cudaError_t e = cudaStreamEndCapture(m->capture_stream, &graph);
     if (e != cudaSuccess) return cuda_status(e, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&m->graph_exec, graph, 0);
-    cudaGraphDestroy(graph);
+    if (mask) {
+        // find the event-record nodes of each profiled class
+        size_t nn = 0;
+        cudaGraphGetNodes(graph, nullptr, &nn);
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if (nn) cudaGraphGetNodes(graph, nodes.data(), &nn);
+        cudaGraphNode_t found[8] = {};
+        for (cudaGraphNode_t nd : nodes) {
+            cudaGraphNodeType ty;
+            if (cudaGraphNodeGetType(nd, &ty) != cudaSuccess || ty != cudaGraphNodeTypeEventRecord) continue;
+            cudaEvent_t ev = nullptr;
+            if (cudaGraphEventRecordNodeGetEvent(nd, &ev) != cudaSuccess) continue;
+            for (int i = 0; i < 8; ++i)
+                if (ev == m->prof_ph[i]) found[i] = nd;
+        }
+        m->prof_nodes.clear();
+        for (int c = 0; c < 4; ++c)
+            if ((mask & (1 << c)) && found[2 * c] && found[2 * c + 1]) m->prof_nodes.push_back({c, {found[2 * c], found[2 * c + 1]}});
+    }
+    e = cudaGraphInstantiate(out, graph, 0);
+    if (mask) {
+        if (m->prof_graph) cudaGraphDestroy(m->prof_graph);
+        m->prof_graph = graph;
+    } else {
+        cudaGraphDestroy(graph);
+    }
     if (e != cudaSuccess) return cuda_status(e, "cudaGraphInstantiate");
-    m->graph_iters = kGraphIters;
     return CWB_OK;
+}
+
+static cudaEvent_t take_event(cwb_model* m)
+{
+    if (!m->prof_pool.empty()) {
+        cudaEvent_t e = m->prof_pool.back();
+        m->prof_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
 }
 
 cwb_status launch_iterations(cwb_model* m, int32_t iters)
@@ -1592,26 +1785,50 @@ cwb_status launch_iterations(cwb_model* m, int32_t iters)
         CWB_CUDA_TRY(cudaStreamSynchronize(m->stream));
         m->forced_host.clear();
     }
-    int32_t left = iters;
-    if (left >= kGraphIters && !m->prof_on) {
-        if (!m->graph_exec) CWB_TRY(build_graph(m));
-        while (left >= kGraphIters) {
-            CWB_CUDA_TRY(cudaGraphLaunch(m->graph_exec, m->stream));
-            left -= kGraphIters;
+    if (m->prof_on) {
+        if (!m->prof_exec) CWB_TRY(capture_graph(m, 1, m->prof_mask, &m->prof_exec));
+        for (int32_t i = 0; i < iters; ++i) {
+            for (auto& pn : m->prof_nodes) {
+                cudaEvent_t e0 = take_event(m), e1 = take_event(m);
+                CWB_CUDA_TRY(cudaGraphExecEventRecordNodeSetEvent(m->prof_exec, pn.second.first, e0));
+                CWB_CUDA_TRY(cudaGraphExecEventRecordNodeSetEvent(m->prof_exec, pn.second.second, e1));
+                m->prof_pending.push_back({pn.first, {e0, e1}});
+            }
+            CWB_CUDA_TRY(cudaGraphLaunch(m->prof_exec, m->stream));
         }
+    } else {
+        int32_t left = iters;
+        if (left >= kGraphIters) {
+            if (!m->graph_exec) CWB_TRY(capture_graph(m, kGraphIters, 0, &m->graph_exec));
+            while (left >= kGraphIters) {
+                CWB_CUDA_TRY(cudaGraphLaunch(m->graph_exec, m->stream));
+                left -= kGraphIters;
+            }
+        }
+        if (left > 0 && !m->graph1_exec) CWB_TRY(capture_graph(m, 1, 0, &m->graph1_exec));
+        for (int32_t i = 0; i < left; ++i) CWB_CUDA_TRY(cudaGraphLaunch(m->graph1_exec, m->stream));
     }
-    for (int32_t i = 0; i < left; ++i) enqueue_iteration(m, m->stream);
     CWB_CUDA_TRY(cudaGetLastError());
     m->done += iters;
     m->coef_valid_at = -1;
+    m->update_pending = true;
     return CWB_OK;
 }
 
 cwb_status launch_final_update(cwb_model* m)
 {
-    ProfScope p(m, m->stream, 0);
     launch_rows<kRowsUpdate>(m, m->stream);
     CWB_CUDA_TRY(cudaGetLastError());
+    return CWB_OK;
+}
+
+// Applies the last iteration's update to the fitted values (and, for HCWB, takes
+// its validation risk) unless the next iteration's row pass has done so already.
+cwb_status materialize(cwb_model* m)
+{
+    if (!m->update_pending) return CWB_OK;
+    CWB_TRY(launch_final_update(m));
+    m->update_pending = false;
     return CWB_OK;
 }
 
@@ -1624,6 +1841,7 @@ cwb_status launch_initial_rows(cwb_model* m)
 
 cwb_status launch_aggregate(cwb_model* m)
 {
+    CWB_TRY(materialize(m));           // the trace holds the last selected coefficients once applied
     if (m->coef_valid_at == m->done) return CWB_OK;
     const int threads = ((m->d_max + 31) / 32) * 32;
     k_aggregate<<<m->K, threads, 0, m->stream>>>(m->K, m->d_max, m->done, m->l_d, m->tr_k, m->tr_mode, m->tr_theta,

@@ -152,6 +152,26 @@ def test_cwb_l2_binned_uint16_many_tiles(cwb):
     run_pair(cwb, data.X, data.y, specs, M=150)
 
 
+def test_cwb_signal_in_the_second_binning_group(cwb):
+    """p = 40 splits into two scatter groups of 20 binnings; the informative features are the
+    last ten columns, so every selection comes from the second group's histograms."""
+    data = S.additive_regression(60_013, 40, 10, seed=27, dtype=np.float32)
+    X = np.ascontiguousarray(data.X[::-1])
+    specs = [dict(feature=j, n_bins=-1) for j in range(40)]
+    model, ref = run_pair(cwb, X, data.y, specs, M=80)
+    assert model.scatter_plan()["groups"] >= 2
+    assert np.mean(np.asarray(ref.k_sel) >= 20) > 0.9
+
+
+def test_cwb_bins_split_over_ranges(cwb):
+    """n* = 60,000 does not fit one CTA's shared memory: the scatter splits the bins over
+    ranges (slots) and the solve gathers each learner's histogram from both."""
+    data = S.additive_regression(150_001, 3, 3, seed=28, dtype=np.float32)
+    specs = [dict(feature=0, n_bins=60_000), dict(feature=1, n_bins=-1), dict(feature=2, n_bins=5000)]
+    model, ref = run_pair(cwb, data.X, data.y, specs, M=60)
+    assert model.scatter_plan()["bin_ranges"] >= 2
+
+
 def test_cwb_exact_binning_small_config(cwb):
     """n = 10,000, p = 10 FP64, exact binning (n* = number of unique values), M = 500."""
     data = S.sim_small_exact(seed=0)
