@@ -237,7 +237,10 @@ def run_ours(args):
         Xd = torch.from_numpy(data.X).to(dev)
         yd = torch.from_numpy(data.y).to(dev)
         stream.synchronize()
+        t_setup = time.perf_counter()
         model = cwb.Model(Xd, yd, learners, nu=NU, iterations=M_FIT, stream=stream, device=local)
+        stream.synchronize()
+        t_setup = time.perf_counter() - t_setup
         del Xd, yd
         flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
         sink = torch.empty(1, dtype=torch.float32, device=dev)
@@ -312,7 +315,8 @@ def run_ours(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "kernel": "k_scatter",
                          "peak_source": f"{peak_kind} hbm_gbs"},
-            "gpu_launches": launches, "clocks": clocks, "scatter_plan": plan}
+            "gpu_launches": launches, "clocks": clocks, "scatter_plan": plan,
+            "setup_ms": t_setup * 1e3}
 
     if not args.skip_e2e:
         line["e2e"] = run_e2e(cwb, data, stream, dev, local)

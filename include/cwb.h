@@ -242,7 +242,11 @@ cwb_status cwb_get_residuals(const cwb_model* m, int32_t channel, float* out);
  * tuning and reports.  values (host int32, `cap` entries) receive in order:
  * binnings per warp (lane-private columns), binnings per group, groups, bin ranges,
  * bins per CTA, cluster size, clusters, pipeline stages, threads per CTA,
- * dynamic shared memory bytes, 1 if histograms use exact int32 fixed point.
+ * dynamic shared memory bytes, 1 if histograms use exact int32 fixed point,
+ * then the scatter CTAs that can be resident at cluster sizes 1, 2, 4 and 8.
+ * The cluster size is the largest that keeps nearly every SM busy; the
+ * environment variable CWB_CLUSTER_SIZE (1, 2, 4, 8 or 16), read when a model is
+ * created, overrides it when that size can be resident.
  */
 cwb_status cwb_get_scatter_plan(const cwb_model* m, int32_t* values, int32_t cap);
 

@@ -139,7 +139,7 @@ void free_model(cwb_model* m)
     if (m->stream) cudaStreamSynchronize(m->stream);
     void* bufs[] = {m->ind, m->y, m->y_lo, m->w, m->f, m->h, m->c, m->rw, m->perm, m->zb, m->zb64, m->zcol, m->crange, m->toff, m->ztab, m->G,
                     m->P, m->lambda, m->l_bin, m->l_d, m->l_nstar, m->l_type, m->l_xmin, m->l_xmax, m->l_degree,
-                    m->l_nknots, m->l_feat, m->part, m->cluster_slot, m->slot_c0, m->theta_it, m->q_it, m->v, m->state, m->risk_part, m->blk_max, m->tr_k,
+                    m->l_nknots, m->l_feat, m->part, m->cluster_slot, m->slot_c0, m->theta_it, m->q_it, m->v, m->state, m->risk_part, m->tr_k,
                     m->tr_mode, m->tr_theta, m->tr_q, m->forced, m->coef};
     for (void* p : bufs) dev_free(p);
     profile_release(m);
@@ -271,7 +271,6 @@ cwb_status create_impl(const cwb_config* cfg, const void* X, int32_t x_dtype, in
             int sms = 0;
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
             st = dev_alloc((void**)&m->risk_part, sizeof(double) * (size_t)std::max(sms, 1) * 8, m->stream);
-            if (st == CWB_OK) st = dev_alloc((void**)&m->blk_max, sizeof(float) * 2 * (size_t)std::max(sms, 1) * 8, m->stream);
         }
         if (st == CWB_OK) {
             cudaError_t e = cudaMemcpyAsync(l_feat, feat.data(), sizeof(int32_t) * K, cudaMemcpyHostToDevice, m->stream);
@@ -619,9 +618,10 @@ cwb_status cwb_get_scatter_plan(const cwb_model* m, int32_t* values, int32_t cap
     set_error("");
     if (!m || (cap > 0 && !values)) { set_error("bad argument"); return CWB_EINVAL; }
     const ScatterPlan& P = m->plan;
-    const int32_t v[11] = {P.f_lane, P.fe, P.groups, P.bin_ranges, P.nb_cta, P.cs, P.clusters, P.stages, P.threads,
-                           (int32_t)P.smem, P.int_acc ? 1 : 0};
-    for (int i = 0; i < cap && i < 11; ++i) values[i] = v[i];
+    const int32_t v[15] = {P.f_lane, P.fe, P.groups, P.bin_ranges, P.nb_cta, P.cs, P.clusters, P.stages, P.threads,
+                           (int32_t)P.smem, P.int_acc ? 1 : 0, P.active_ctas[0], P.active_ctas[1], P.active_ctas[2],
+                           P.active_ctas[3]};
+    for (int i = 0; i < cap && i < 15; ++i) values[i] = v[i];
     return CWB_OK;
 }
 

@@ -63,8 +63,10 @@ struct DevState {
     uint32_t ticket_solve;
     uint32_t pad0;
     double risk_prev;
-    uint32_t rmax_bits[2];  // max |w r| and max |w c| of the current iteration (FP32 bits), reset by k_solve
+    uint32_t rmax_bits[2];  // max |w r| and max |w c| of the current iteration (FP32 bits): atomicMax by the
+                            // row pass, reset to 0 by the solve's last block
     int32_t cnt_log2[2];    // ceil(log2(largest per-cluster bin count)): [0] all rows, [1] HCWB training rows
+    int32_t cnt_max[2];     // largest per-cluster bin count of the counting passes
 };
 
 // Static description of the scatter decomposition (see k_scatter).
@@ -86,6 +88,7 @@ struct ScatterPlan {
     size_t smem;      // dynamic shared memory bytes (incl. alignment slack)
     size_t part_floats;
     int stage_cb;     // bins per chunk of the cluster epilogue's transposing stage
+    int active_ctas[4];  // resident scatter CTAs for cluster sizes 1, 2, 4, 8
     bool solve_stage_v;  // the solve stages each learner's design rows in shared memory
     bool solve_stage_z;  // ... and its column-major design
     bool int_acc;     // exact fixed-point int32 histograms (false: FP32 atomics for heavily skewed bins)
@@ -148,7 +151,6 @@ struct cwb_model {
     float* v = nullptr;                   // [2][K][S] fitted values Z^b theta of every learner per bin
     cwb::DevState* state = nullptr;
     double* risk_part = nullptr;
-    float* blk_max = nullptr;             // [rows grid][2]
     int risk_blocks = 0;
     // trace
     int32_t trace_cap = 0;

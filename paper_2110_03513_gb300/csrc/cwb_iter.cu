@@ -15,6 +15,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <string>
 #include <type_traits>
 
@@ -29,7 +30,7 @@ namespace {
 
 constexpr int kRowThreads = 256;
 constexpr int kSolveThreads = 512;
-constexpr int kScatterThreads = 320;   // 8 consumer warps + 1 loader warp + 1 converter warp
+constexpr int kScatterThreads = 576;   // 16 consumer warps + 1 loader warp + 1 converter warp
 constexpr int kGraphIters = 32;
 
 enum { kRowsFused = 0, kRowsUpdate = 1, kRowsResid = 2 };
@@ -56,7 +57,6 @@ struct RowArgs {
     int hybrid;
     int patience;
     double* risk_part;
-    float* blk_max;       // [grid][2] per-block max |scatter input|
 };
 
 template <typename IndT>
@@ -337,21 +337,29 @@ __global__ void __launch_bounds__(kRowThreads, 4) k_rows(RowArgs a)
             rmax1 = fmaxf(rmax1, __shfl_xor_sync(0xffffffffu, rmax1, o));
         }
         const bool anybad = __any_sync(0xffffffffu, nonfinite);
+        __shared__ bool wbad[kRowThreads / 32];
         if ((threadIdx.x & 31) == 0) {
             wmax[0][threadIdx.x >> 5] = rmax0;
             wmax[1][threadIdx.x >> 5] = rmax1;
+            wbad[threadIdx.x >> 5] = anybad;
         }
         __syncthreads();
-        if (anybad && (threadIdx.x & 31) == 0) bad_blk = true;
         if (threadIdx.x == 0) {
             float b0 = 0.0f, b1 = 0.0f;
             for (int w = 0; w < kRowThreads / 32; ++w) {
                 b0 = fmaxf(b0, wmax[0][w]);
                 b1 = fmaxf(b1, wmax[1][w]);
+                if (wbad[w]) bad_blk = true;
             }
-            a.blk_max[2 * blockIdx.x] = b0;
-            a.blk_max[2 * blockIdx.x + 1] = b1;
+            // non-negative FP32 values order like their bit patterns; the solve of the
+            // previous iteration reset both maxima to 0
+            atomicMax(&a.state->rmax_bits[0], __float_as_uint(b0));
+            if (acwb_n) atomicMax(&a.state->rmax_bits[1], __float_as_uint(b1));
+            if (bad_blk) atomicOr(&a.state->err, kErrNonFinite);
         }
+        // the residual passes end here: the next iteration's row pass sees m > m_applied for
+        // the pending update, and only the update pass records what it applied
+        if (KIND != kRowsUpdate) return;
     }
     if (eval_risk) {
         red[threadIdx.x] = risk_acc;
@@ -373,29 +381,16 @@ __global__ void __launch_bounds__(kRowThreads, 4) k_rows(RowArgs a)
     __syncthreads();
     if (!is_last) return;
     __threadfence();
-    // last block: block-parallel, fixed-order reductions of the per-block partials
-    __shared__ float mx[2][kRowThreads];
+    // last block (update pass): block-parallel, fixed-order reduction of the validation risk partials
     {
-        float b0 = 0.0f, b1 = 0.0f;
         double rs = 0.0;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += kRowThreads) {
-            if (KIND != kRowsUpdate) {
-                b0 = fmaxf(b0, __ldcg(a.blk_max + 2 * b));
-                b1 = fmaxf(b1, __ldcg(a.blk_max + 2 * b + 1));
-            }
-            if (eval_risk) rs += __ldcg(a.risk_part + b);
-        }
-        mx[0][threadIdx.x] = b0;
-        mx[1][threadIdx.x] = b1;
+        if (eval_risk)
+            for (int b = threadIdx.x; b < (int)gridDim.x; b += kRowThreads) rs += __ldcg(a.risk_part + b);
         red[threadIdx.x] = rs;
     }
     __syncthreads();
     for (int s = kRowThreads / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) {
-            mx[0][threadIdx.x] = fmaxf(mx[0][threadIdx.x], mx[0][threadIdx.x + s]);
-            mx[1][threadIdx.x] = fmaxf(mx[1][threadIdx.x], mx[1][threadIdx.x + s]);
-            red[threadIdx.x] += red[threadIdx.x + s];
-        }
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
         __syncthreads();
     }
     if (threadIdx.x == 0) {
@@ -409,10 +404,6 @@ __global__ void __launch_bounds__(kRowThreads, 4) k_rows(RowArgs a)
                 S->counter = (risk > S->risk_prev) ? S->counter + 1 : 0;
                 S->risk_prev = risk;
             }
-        }
-        if (KIND != kRowsUpdate) {
-            S->rmax_bits[0] = __float_as_uint(mx[0][0]);
-            S->rmax_bits[1] = acwb_n ? __float_as_uint(mx[1][0]) : 0u;
         }
         if (KIND == kRowsUpdate && a.hybrid && S->mode == kModeACWB && S->counter >= a.patience) {
             S->mode = kModeCWB;
@@ -429,18 +420,19 @@ __global__ void __launch_bounds__(kRowThreads, 4) k_rows(RowArgs a)
 //
 // A thread-block cluster of `cs` CTAs owns one slot (F binnings x one bin range)
 // and a contiguous run of 256-row tiles.  Inside a CTA one producer warp streams
-// tiles with TMA: a 2D tiled copy of the uint8/uint16 index matrix (box = the
-// tile's 256 rows x F binnings, one contiguous row per binning) and a 1D bulk
-// copy of the matching residual rows, into a ring of `stages` shared-memory
-// buffers guarded by mbarriers; it then converts the residual tile to fixed
-// point (see fixed_scale).  Consumer warps give every lane its own binning
-// (lane % F), channel and row subset; lanes start at different 16-byte units
-// of their rows so a warp's reads cover all banks, and they add into
-// hist[channel][bin][lane's binning] with int32 shared-memory atomics: lanes of
-// a warp never share an address and, for F = 32 (or F = 16 with two channels),
-// never share a bank.  At the end the cluster's histograms are summed through
-// distributed shared memory, each CTA reducing a slice of the bins, and written
-// once per cluster.
+// tiles with TMA: a 3D tiled copy of the uint8/uint16 index matrix (box = the
+// tile's 256 rows x FE binnings, landing as 128-byte rows [chunk][binning] with
+// the 128-byte swizzle) and a 1D bulk copy of the matching residual rows, into a
+// ring of `stages` shared-memory buffers guarded by mbarriers; a converter warp
+// turns the residual tile into fixed point (see fixed_scale).  Consumer warps give
+// every lane its own binning (lane % F), channel and row subset; the lanes of a
+// row subset read the same 16-byte unit of rows of their binnings, so the residual
+// read is a broadcast and the swizzle spreads the index reads over all banks.
+// Lanes add into hist[channel][bin][lane's binning] with int32 shared-memory
+// atomics: lanes of a warp never share an address and, for F = 32 (or F = 16
+// with two channels), never share a bank.  At the end the cluster's histograms
+// are summed through distributed shared memory, each CTA reducing a slice of the
+// bins, and written once per cluster.
 
 namespace cg = cooperative_groups;
 
@@ -500,11 +492,11 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long l
     return true;
 }
 
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar)
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar)
 {
     asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-        ::"r"(smem_addr(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_addr(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
         : "memory");
 }
 
@@ -558,11 +550,12 @@ __device__ __forceinline__ int fixed_scale(uint32_t rmax_bits, int cnt_log2)
 // 2^e as an FP32 value for -126 <= e <= 127 (fixed_scale keeps every exponent used here in range).
 __device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }
 
-template <typename IndT, int CMAX, bool INT_ACC, bool RANGED>
+// FL2 >= 0: the lanes per channel F = 2^FL2 is a compile-time constant (the common plans), -1: read at run time.
+template <typename IndT, int CMAX, bool INT_ACC, bool RANGED, int FL2>
 __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_constant__ CUtensorMap tmap, ScatterArgs a)
 {
     constexpr int U = 16 / sizeof(IndT);                   // rows per 16-byte unit
-    constexpr int UN = sizeof(IndT) == 2 ? 4 : 2;          // units in flight per lane
+    constexpr int UN = sizeof(IndT) == 2 ? 2 : 1;          // units in flight per lane (16 consumer warps)
     using Acc = typename std::conditional<INT_ACC, int, float>::type;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte alignment of the ring; offsetting the shared array itself keeps every
@@ -586,7 +579,7 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
     const int64_t t_lo = tiles * piece / pieces, t_hi = tiles * (piece + 1) / pieces;
     const int ntiles = (int)(t_hi - t_lo);
 
-    const int F = a.F;                  // lanes per channel and row set (power of two)
+    const int F = FL2 >= 0 ? (1 << FL2) : a.F;   // lanes per channel and row set (power of two)
     const int FE = a.FE;                // binnings of this group held in the ring (<= F)
     const int b_lo = br * a.nb_cta;
     const int row_bytes = a.stage_rows * (int)sizeof(IndT);
@@ -612,7 +605,7 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
     if (warp == W) {
         // loader: one 2D TMA box (the tile's rows x FE binnings) and C residual rows per tile
         if (lane == 0) {
-            const uint32_t bytes = (uint32_t)(FE * row_bytes + C * a.stage_rows * 4);
+            const uint32_t bytes = (uint32_t)(FE * row_bytes + C * a.stage_rows * 4);   // box bytes + residual rows
             int issued = 0;
             bool ok = true;
             for (int it = 0; it < ntiles; ++it) {
@@ -623,7 +616,8 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
                 }
                 const int64_t row0 = (t_lo + it) * a.stage_rows;
                 mbar_arrive_expect_tx(&full[s], bytes);
-                tma_load_2d(smem + a.ind_off + (size_t)s * a.stage_ind_bytes, &tmap, (int)row0, g * FE, &full[s]);
+                tma_load_3d(smem + a.ind_off + (size_t)s * a.stage_ind_bytes, &tmap, 0, g * FE,
+                            (int)(row0 / (128 / (int)sizeof(IndT))), &full[s]);
                 float* r_dst = reinterpret_cast<float*>(smem + a.r_off + (size_t)s * a.stage_r_bytes);
                 for (int ch = 0; ch < C; ++ch)
                     bulk_load(r_dst + ch * a.stage_rows, a.rw + ch * a.n_pad + row0, (uint32_t)a.stage_rows * 4,
@@ -691,7 +685,7 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
         const int RS = 32 / (F * C);
         const bool active = f < FE && g * FE + f < a.B;
         Acc* hf = hist + ch * a.ch_stride + f;
-        const int fsh = __ffs(F) - 1;                     // F is a power of two
+        const int fsh = FL2 >= 0 ? FL2 : __ffs(F) - 1;    // F is a power of two
         const int nunits = row_bytes / 16;
         const int step = UN * RS;
         for (int it = 0; it < ntiles; ++it) {
@@ -700,7 +694,7 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
                 if (lane == 0) atomicOr(a.err, kErrTimeout);
                 break;
             }
-            const unsigned char* ind_row = smem + a.ind_off + (size_t)s * a.stage_ind_bytes + (size_t)f * row_bytes;
+            const unsigned char* ind_st = smem + a.ind_off + (size_t)s * a.stage_ind_bytes;
             const Acc* r_st =
                 reinterpret_cast<const Acc*>(smem + (INT_ACC ? a.q_off : a.r_off) + (size_t)s * a.stage_r_bytes) +
                 ch * a.stage_rows;
@@ -712,11 +706,14 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
                     bool live[UN];
 #pragma unroll
                     for (int k = 0; k < UN; ++k) {
-                        // lanes start at different 16-byte units of their rows (rotation by the
-                        // lane's binning) so the reads of a warp spread over all banks
-                        live[k] = u0 + k * RS + rs < nunits;
-                        const int pos = (u0 + k * RS + rs + f) & (nunits - 1);
-                        raw[k] = *reinterpret_cast<const uint4*>(ind_row + (pos << 4));
+                        // the lanes of a row set read the same logical 16-byte unit (8 or 16 rows) of
+                        // their binnings: the residuals are one broadcast, and the 128-byte swizzle
+                        // of the TMA box spreads the index reads over all banks.  Unit u of binning
+                        // f sits in 128-byte row R = (u / 8) FE + f at 16-byte slot (u % 8) ^ (R % 8).
+                        const int pos = u0 + k * RS + rs;
+                        live[k] = pos < nunits;
+                        const int R = (pos >> 3) * FE + f;
+                        raw[k] = *reinterpret_cast<const uint4*>(ind_st + R * 128 + (((pos & 7) ^ (R & 7)) << 4));
 #pragma unroll
                         for (int t4 = 0; t4 < U / 4; ++t4) {
                             if (INT_ACC) {
@@ -816,21 +813,29 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
 // ceil(log2(largest bin count of any cluster)) from a counting pass of the scatter.
 __global__ void k_count_max(const int* __restrict__ part, int clusters, int cmax, int nbf, DevState* state, int idx)
 {
-    __shared__ int red[1024];
+    __shared__ int red[256];
+    const int64_t total = (int64_t)clusters * nbf;
     int mx = 0;
-    for (int64_t c = 0; c < clusters; ++c)
-        for (int e = threadIdx.x; e < nbf; e += blockDim.x) mx = max(mx, part[(c * cmax) * (int64_t)nbf + e]);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = e / nbf, i = e - c * nbf;
+        mx = max(mx, part[(c * cmax) * (int64_t)nbf + i]);
+    }
     red[threadIdx.x] = mx;
     __syncthreads();
     for (int s = blockDim.x / 2; s > 0; s >>= 1) {
         if (threadIdx.x < s) red[threadIdx.x] = max(red[threadIdx.x], red[threadIdx.x + s]);
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        int l = 0;
-        while ((1 << l) < red[0] && l < 30) ++l;
-        state->cnt_log2[idx] = l;
-    }
+    if (threadIdx.x == 0) atomicMax(&state->cnt_max[idx], red[0]);
+}
+
+__global__ void k_count_log2(DevState* state, int idx)
+{
+    if (threadIdx.x != 0) return;
+    const int c = state->cnt_max[idx];
+    int l = 0;
+    while ((1 << l) < c && l < 30) ++l;
+    state->cnt_log2[idx] = l;
 }
 
 // ---------------------------------------------------------------------------
@@ -875,9 +880,19 @@ struct SolveArgs {
     int trace_cap;
 };
 
-// (best, index of best, second best) over a set of criteria; ties go to the lowest index.
+// Criteria are compared as integers: an FP64 value maps to a signed 64-bit key with the
+// same order (negative values have their magnitude bits flipped); the map is its own
+// inverse.  Integer compares keep the argmin off the (slow) FP64 pipe.
+__device__ __forceinline__ long long order_key(double q)
+{
+    const long long b = __double_as_longlong(q);
+    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double key_value(long long k) { return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffLL)); }
+
+// (best key, index of best, second best key); ties go to the lowest index.
 struct Best2 {
-    double q1, q2;
+    long long q1, q2;
     int k1;
 };
 
@@ -888,11 +903,11 @@ __device__ __forceinline__ Best2 best2_merge(Best2 a, Best2 b)
     if (take_b) {
         r.q1 = b.q1;
         r.k1 = b.k1;
-        r.q2 = fmin(a.q1, fmin(a.q2, b.q2));
+        r.q2 = min(a.q1, min(a.q2, b.q2));
     } else {
         r.q1 = a.q1;
         r.k1 = a.k1;
-        r.q2 = fmin(a.q2, fmin(b.q1, b.q2));
+        r.q2 = min(a.q2, min(b.q1, b.q2));
     }
     return r;
 }
@@ -1092,12 +1107,12 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(SolveArgs a)
     }
 #pragma unroll
     for (int c = 0; c < kColsPerWarp; ++c) {
-        for (int o = 16; o > 0; o >>= 1) {
-            acc0[c] += __shfl_xor_sync(0xffffffffu, acc0[c], o);
-            acc1[c] += __shfl_xor_sync(0xffffffffu, acc1[c], o);
-        }
         const int j = warp + c * NW;
-        if (lane == 0 && j < d) {
+        if (j >= d) break;                    // warp-uniform
+        for (int o = 16; o > 0; o >>= 1) acc0[c] += __shfl_xor_sync(0xffffffffu, acc0[c], o);
+        if (C == 2)
+            for (int o = 16; o > 0; o >>= 1) acc1[c] += __shfl_xor_sync(0xffffffffu, acc1[c], o);
+        if (lane == 0) {
             s_s[0][j] = (double)acc0[c];
             s_s[1][j] = (double)acc1[c];
         }
@@ -1171,15 +1186,17 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(SolveArgs a)
     __shared__ uint32_t bad;
     if (tid == 0) bad = 0;
     __syncthreads();
+    const long long kInf = order_key(INFINITY);
     for (int ch = 0; ch < C; ++ch) {
-        Best2 x = {INFINITY, INFINITY, -1};
+        Best2 x = {kInf, kInf, -1};
         for (int kk = tid; kk < a.K; kk += blockDim.x) {
-            double q = __ldcg(a.q_it + (int64_t)ch * a.K + kk);
-            if (!(q == q) || isinf(q)) {
+            const double q = __ldcg(a.q_it + (int64_t)ch * a.K + kk);
+            long long key = q == 0.0 ? 0LL : order_key(q);                                 // -0 ties with +0
+            if ((__double_as_longlong(q) & 0x7ff0000000000000LL) == 0x7ff0000000000000LL) {   // inf or NaN
                 atomicOr(&bad, 1u);
-                q = INFINITY;
+                key = kInf;
             }
-            x = best2_merge(x, Best2{q, INFINITY, kk});
+            x = best2_merge(x, Best2{key, kInf, kk});
         }
         for (int o = 16; o > 0; o >>= 1) x = best2_merge(x, best2_shfl(x, o));
         if (lane == 0) cand[ch][warp] = x;
@@ -1202,8 +1219,8 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(SolveArgs a)
             if (trace_ok) {
                 a.tr_k[2 * it + ch] = i1;
                 if (ch == 0) {
-                    a.tr_q[2 * it] = x.q1;
-                    a.tr_q[2 * it + 1] = x.q2;
+                    a.tr_q[2 * it] = key_value(x.q1);
+                    a.tr_q[2 * it + 1] = key_value(x.q2);
                 }
             }
         }
@@ -1218,6 +1235,8 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(SolveArgs a)
         S_->k_cor = (C == 2) ? best_k[1] : -1;
         S_->pend_mode = mode;
         S_->m = st.m + 1;
+        S_->rmax_bits[0] = 0u;           // the next row pass takes its maxima with atomicMax
+        S_->rmax_bits[1] = 0u;
         S_->ticket_solve = 0;
     }
 }
@@ -1288,7 +1307,6 @@ RowArgs row_args(cwb_model* m)
     a.hybrid = m->hybrid ? 1 : 0;
     a.patience = m->cfg.patience;
     a.risk_part = m->risk_part;
-    a.blk_max = m->blk_max;
     return a;
 }
 
@@ -1317,8 +1335,10 @@ cudaError_t launch_scatter_t(cwb_model* m, cudaStream_t s, const ScatterArgs& a)
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (P.bin_ranges > 1) return cudaLaunchKernelEx(&cfg, k_scatter<IndT, CMAX, INT_ACC, true>, m->tmap, a);
-    return cudaLaunchKernelEx(&cfg, k_scatter<IndT, CMAX, INT_ACC, false>, m->tmap, a);
+    if (P.bin_ranges > 1) return cudaLaunchKernelEx(&cfg, k_scatter<IndT, CMAX, INT_ACC, true, -1>, m->tmap, a);
+    if (P.f_lane == 32) return cudaLaunchKernelEx(&cfg, k_scatter<IndT, CMAX, INT_ACC, false, 5>, m->tmap, a);
+    if (P.f_lane == 16) return cudaLaunchKernelEx(&cfg, k_scatter<IndT, CMAX, INT_ACC, false, 4>, m->tmap, a);
+    return cudaLaunchKernelEx(&cfg, k_scatter<IndT, CMAX, INT_ACC, false, -1>, m->tmap, a);
 }
 
 ScatterArgs scatter_args(cwb_model* m)
@@ -1455,10 +1475,16 @@ template <typename IndT, int CMAX>
 cwb_status prepare_scatter_kernel(cwb_model* m, int cs, int* active_clusters)
 {
     const ScatterPlan& P = m->plan;
-    CWB_CUDA_TRY(cudaFuncSetAttribute(k_scatter<IndT, CMAX, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem));
-    CWB_CUDA_TRY(cudaFuncSetAttribute(k_scatter<IndT, CMAX, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem));
-    CWB_CUDA_TRY(cudaFuncSetAttribute(k_scatter<IndT, CMAX, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem));
-    CWB_CUDA_TRY(cudaFuncSetAttribute(k_scatter<IndT, CMAX, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem));
+    // every instantiation a launch may pick
+    const void* kernels[] = {
+        (const void*)k_scatter<IndT, CMAX, true, true, -1>,  (const void*)k_scatter<IndT, CMAX, false, true, -1>,
+        (const void*)k_scatter<IndT, CMAX, true, false, 5>,  (const void*)k_scatter<IndT, CMAX, false, false, 5>,
+        (const void*)k_scatter<IndT, CMAX, true, false, 4>,  (const void*)k_scatter<IndT, CMAX, false, false, 4>,
+        (const void*)k_scatter<IndT, CMAX, true, false, -1>, (const void*)k_scatter<IndT, CMAX, false, false, -1>};
+    for (const void* kf : kernels) {
+        CWB_CUDA_TRY(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem));
+        if (cs > 8) CWB_CUDA_TRY(cudaFuncSetAttribute(kf, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cs * 64, 1, 1);
     cfg.blockDim = dim3(P.threads, 1, 1);
@@ -1471,7 +1497,7 @@ cwb_status prepare_scatter_kernel(cwb_model* m, int cs, int* active_clusters)
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int n = 0;
-    cudaError_t e = cudaOccupancyMaxActiveClusters(&n, k_scatter<IndT, CMAX, true, false>, &cfg);
+    cudaError_t e = cudaOccupancyMaxActiveClusters(&n, k_scatter<IndT, CMAX, true, false, -1>, &cfg);
     if (e != cudaSuccess) {
         cudaGetLastError();
         n = 0;
@@ -1532,7 +1558,8 @@ cwb_status plan_scatter(cwb_model* m)
         return base + pad;
     };
     auto hist_bytes = [&](int nb, int F) { return ((cmax * ch_stride_for(nb, F) * 4 + 1023) / 1024) * 1024; };
-    auto stage_bytes = [&](int F) { return ((F * P.stage_rows * elem + 127) / 128) * 128 + 2 * cmax * P.stage_rows * 4; };
+    // a stage's index box starts on a 1024-byte boundary (the 128-byte swizzle pattern repeats every 1 KB)
+    auto stage_bytes = [&](int F) { return ((F * P.stage_rows * elem + 1023) / 1024) * 1024 + 2 * cmax * P.stage_rows * 4; };
     P.f_lane = 0;
     for (int F = 32; F >= 1; F >>= 1) {
         if (F * cmax > 32 || F > pow2B) continue;
@@ -1551,8 +1578,8 @@ cwb_status plan_scatter(cwb_model* m)
     P.nb_cta = (((nbins + P.bin_ranges - 1) / P.bin_ranges) + 3) & ~3;
     P.nbins_pad = P.nb_cta * P.bin_ranges;
     P.ch_stride = ch_stride_for(P.nb_cta, F);
-    P.box_bytes = ((P.fe * P.stage_rows * elem + 127) / 128) * 128;
-    P.stage_ind_bytes = (uint32_t)P.box_bytes;
+    P.box_bytes = P.fe * P.stage_rows * elem;
+    P.stage_ind_bytes = (uint32_t)(((P.box_bytes + 1023) / 1024) * 1024);
     P.stage_r_bytes = (uint32_t)(cmax * P.stage_rows * 4);
     const int hb = hist_bytes(P.nb_cta, F);
     P.stages = std::min(8, (budget - hb) / stage_bytes(P.fe));
@@ -1566,15 +1593,28 @@ cwb_status plan_scatter(cwb_model* m)
     P.threads = kScatterThreads;
     m->plan = P;
 
-    // cluster size: the largest that keeps (nearly) every SM busy
+    // cluster size: the largest that keeps (nearly) every SM busy; CWB_CLUSTER_SIZE
+    // (1, 2, 4, 8 or 16) overrides the choice when that size can be resident
     int best_cs = 1, best_used = 0;
     for (int cs : {8, 4, 2, 1}) {
         int act = 0;
         CWB_TRY(active_clusters_for(m, cs, &act));
         int used = act * cs;
+        P.active_ctas[cs == 8 ? 3 : cs == 4 ? 2 : cs == 2 ? 1 : 0] = used;
         if (used > best_used + sms / 50) {
             best_used = used;
             best_cs = cs;
+        }
+    }
+    if (const char* env = std::getenv("CWB_CLUSTER_SIZE")) {
+        const int want = std::atoi(env);
+        if (want == 1 || want == 2 || want == 4 || want == 8 || want == 16) {
+            int act = 0;
+            CWB_TRY(active_clusters_for(m, want, &act));
+            if (act > 0) {
+                best_cs = want;
+                best_used = act * want;
+            }
         }
     }
     if (best_used == 0) {
@@ -1625,18 +1665,21 @@ cwb_status plan_scatter(cwb_model* m)
                                  m->stream));
     CWB_CUDA_TRY(cudaStreamSynchronize(m->stream));
 
-    // tensor map of the index matrix: [B][n_pad] elements, boxes of one tile's rows x F binnings
+    // tensor map of the index matrix [B][n_pad] viewed as {E rows, B binnings, n_pad / E chunks} with
+    // E = 128 bytes of rows: one box is a tile's 256 rows of FE binnings, landing as 128-byte rows
+    // [chunk][binning] with the 128-byte swizzle
     EncodeTiledFn enc = encode_tiled_fn();
     if (!enc) {
         set_error("cuTensorMapEncodeTiled is not available from the driver");
         return CWB_ECUDA;
     }
-    cuuint64_t dims[2] = {(cuuint64_t)m->n_pad, (cuuint64_t)B};
-    cuuint64_t strides[1] = {(cuuint64_t)m->n_pad * elem};
-    cuuint32_t box[2] = {(cuuint32_t)P.stage_rows, (cuuint32_t)P.fe};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult r = enc(&m->tmap, elem == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, m->ind,
-                     dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+    const int E = 128 / elem;
+    cuuint64_t dims[3] = {(cuuint64_t)E, (cuuint64_t)B, (cuuint64_t)(m->n_pad / E)};
+    cuuint64_t strides[2] = {(cuuint64_t)m->n_pad * elem, 128};
+    cuuint32_t box[3] = {(cuuint32_t)E, (cuuint32_t)P.fe, (cuuint32_t)(P.stage_rows / E)};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(&m->tmap, elem == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, m->ind,
+                     dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         set_error("cuTensorMapEncodeTiled failed with code " + std::to_string((int)r));
@@ -1656,8 +1699,11 @@ cwb_status scatter_count_pass(cwb_model* m)
         ScatterArgs a = scatter_args(m);
         a.count_rows = idx == 1 ? m->n_tr : m->n;
         CWB_CUDA_TRY(launch_scatter_args(m, m->stream, a, true));
-        k_count_max<<<1, 1024, 0, m->stream>>>(reinterpret_cast<const int*>(m->part), P.clusters, P.cmax,
-                                               P.nb_cta * P.f_lane, m->state, idx);
+        const int64_t total = (int64_t)P.clusters * P.nb_cta * P.f_lane;
+        const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(4 * num_sms(m->device), (total + 255) / 256));
+        k_count_max<<<blocks, 256, 0, m->stream>>>(reinterpret_cast<const int*>(m->part), P.clusters, P.cmax,
+                                                   P.nb_cta * P.f_lane, m->state, idx);
+        k_count_log2<<<1, 32, 0, m->stream>>>(m->state, idx);
         CWB_CUDA_TRY(cudaGetLastError());
     }
     DevState st;

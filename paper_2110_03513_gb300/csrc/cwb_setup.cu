@@ -89,16 +89,19 @@ __global__ void k_minmax_partial(const T* __restrict__ X, const int32_t* __restr
 {
     const int b = blockIdx.y;
     const T* x = X + (int64_t)feat[b] * n;
-    double lo = INFINITY, hi = -INFINITY;
+    // compared in the input type (exact; FP64 arithmetic is slow on this part)
+    T lo = T(INFINITY), hi = T(-INFINITY);
+    bool bad = false;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double v = (double)x[i];
-        if (!isfinite(v)) { atomicOr(nonfinite, 1u); continue; }
-        lo = fmin(lo, v);
-        hi = fmax(hi, v);
+        const T v = x[i];
+        if (!isfinite(v)) { bad = true; continue; }
+        lo = v < lo ? v : lo;
+        hi = v > hi ? v : hi;
     }
+    if (bad) atomicOr(nonfinite, 1u);
     __shared__ double slo[kThreads], shi[kThreads];
-    slo[threadIdx.x] = lo;
-    shi[threadIdx.x] = hi;
+    slo[threadIdx.x] = (double)lo;
+    shi[threadIdx.x] = (double)hi;
     __syncthreads();
     for (int s = blockDim.x / 2; s > 0; s >>= 1) {
         if (threadIdx.x < s) {
@@ -414,94 +417,22 @@ __global__ void k_gram(int S, int D, int K, const int32_t* __restrict__ l_bin, c
 }
 
 // ---------------------------------------------------------------------------
-// Dense FP64 kernels for one learner (single thread, d <= 64, row-major in shared memory).
+// lambda from df and P = (G + lambda K)^-1 (App. A.2), one CTA of kLamThreads
+// threads per learner and phase, everything in shared memory (d <= 64).
+//
+// With A = G + lambda K = L L^T and K = Dp^T Dp (Dp: the difference matrix),
+//   df1(lambda) = tr(A^-1 G) = d - lambda tr(A^-1 K) = d - lambda ||Y||_F^2,
+//   d df1 / d ln(lambda) = -lambda tr(A^-1 K) + lambda^2 tr((A^-1 K)^2)
+//                        = -lambda ||Y||_F^2 + lambda^2 ||Y^T Y||_F^2,
+// where Y = L^-1 Dp^T.  The root of df1 = df is bracketed in log10(lambda) within
+// twelve decades of tr(G) / tr(K), as in the reference computation, and found by
+// Newton steps in log(lambda) that fall back to bisection whenever a step leaves
+// the bracket or does not halve the residual.  Every evaluation is a fresh
+// factorisation of A on the definition (no eigen-decomposition).
 
-__device__ bool dev_cholesky(const double* A, int d, int ld, double* L)
-{
-    for (int i = 0; i < d * ld; ++i) L[i] = 0.0;
-    for (int j = 0; j < d; ++j) {
-        double s = A[j * ld + j];
-        for (int k = 0; k < j; ++k) s -= L[j * ld + k] * L[j * ld + k];
-        if (!(s > 0.0)) return false;
-        double ljj = sqrt(s);
-        L[j * ld + j] = ljj;
-        for (int i = j + 1; i < d; ++i) {
-            double t = A[i * ld + j];
-            for (int k = 0; k < j; ++k) t -= L[i * ld + k] * L[j * ld + k];
-            L[i * ld + j] = t / ljj;
-        }
-    }
-    return true;
-}
+constexpr int kLamThreads = 64;
 
-// Solve L L^T x = b in place.
-__device__ void dev_chol_solve(const double* L, int d, int ld, double* b)
-{
-    for (int i = 0; i < d; ++i) {
-        double t = b[i];
-        for (int k = 0; k < i; ++k) t -= L[i * ld + k] * b[k];
-        b[i] = t / L[i * ld + i];
-    }
-    for (int i = d - 1; i >= 0; --i) {
-        double t = b[i];
-        for (int k = i + 1; k < d; ++k) t -= L[k * ld + i] * b[k];
-        b[i] = t / L[i * ld + i];
-    }
-}
-
-// Eigenvalues of a symmetric matrix by cyclic Jacobi rotations (A is overwritten).
-__device__ void dev_jacobi_eigenvalues(double* A, int d, int ld, double* ev)
-{
-    for (int sweep = 0; sweep < 100; ++sweep) {
-        double off = 0.0, tot = 0.0;
-        for (int i = 0; i < d; ++i)
-            for (int j = 0; j < d; ++j) {
-                double v = A[i * ld + j] * A[i * ld + j];
-                tot += v;
-                if (i != j) off += v;
-            }
-        if (off <= 1e-30 * tot || off == 0.0) break;
-        for (int p = 0; p < d - 1; ++p)
-            for (int q = p + 1; q < d; ++q) {
-                double apq = A[p * ld + q];
-                if (fabs(apq) <= 1e-300) continue;
-                double app = A[p * ld + p], aqq = A[q * ld + q];
-                double theta = (aqq - app) / (2.0 * apq);
-                double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-                double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
-                for (int k = 0; k < d; ++k) {        // A <- A J (columns p, q)
-                    double akp = A[k * ld + p], akq = A[k * ld + q];
-                    A[k * ld + p] = c * akp - s * akq;
-                    A[k * ld + q] = s * akp + c * akq;
-                }
-                for (int k = 0; k < d; ++k) {        // A <- J^T A (rows p, q)
-                    double apk = A[p * ld + k], aqk = A[q * ld + k];
-                    A[p * ld + k] = c * apk - s * aqk;
-                    A[q * ld + k] = s * apk + c * aqk;
-                }
-            }
-    }
-    for (int i = 0; i < d; ++i) ev[i] = A[i * ld + i];
-}
-
-// df1(lambda) = tr((G + lambda K)^-1 G) by its definition (used when G is singular).
-__device__ bool dev_df_direct(const double* G, const double* Kp, int d, int ld, double lambda, double* A, double* L,
-                              double* col, double* out)
-{
-    for (int i = 0; i < d; ++i)
-        for (int j = 0; j < d; ++j) A[i * ld + j] = G[i * ld + j] + lambda * Kp[i * ld + j];
-    if (!dev_cholesky(A, d, ld, L)) return false;
-    double tr = 0.0;
-    for (int j = 0; j < d; ++j) {
-        for (int i = 0; i < d; ++i) col[i] = G[i * ld + j];
-        dev_chol_solve(L, d, ld, col);
-        tr += col[j];
-    }
-    *out = tr;
-    return true;
-}
-
-struct DroArgs {
+struct LamArgs {
     int K, D;
     const int32_t* l_type;
     const int32_t* l_d;
@@ -511,161 +442,243 @@ struct DroArgs {
     const double* G;        // [2][K][D][D]
     double* P;              // [2][K][D][D]
     double* lambda;         // [2][K]
-    int32_t* status;        // [2][K]: 0 ok, 1 singular, 2 df unreachable
+    int32_t* status;        // [2][K]: 0 ok, 1 not positive definite, 2 df unreachable
     int phases;
 };
 
-// Per learner and phase: penalty K = D^T D, then lambda with df1(lambda) = df
-// (App. A.2) by a Demmler-Reinsch orthogonalisation set up on the well
-// conditioned matrix C = G + c K (c = tr G / tr K): with C = L L^T the
-// eigenvalues t_i of L^-1 G L^-T lie in [0, 1] and the generalised eigenvalues
-// of (K, G) are s_i = (1 - t_i) / (c t_i), so
-//   df1(lambda) = sum_i 1 / (1 + lambda s_i) = sum_i c t_i / (c t_i + lambda (1 - t_i)).
-// (Factorising G itself loses the small s_i when tail bins are nearly empty.)
-// The root found on that curve is then polished on the definition
-// tr((G + lambda K)^-1 G) with fresh factorisations.  Finally P = (G + lambda K)^-1.
-__device__ double dev_df_dro(const double* t, int d, double c, double lambda)
+// In-place Cholesky of the lower triangle of A (d x d, leading dimension d), right-looking:
+// column j is scaled by 1 / L_jj, then the trailing lower triangle takes the rank-1 update.
+// rinv[j] = 1 / L_jj.  Returns false (uniformly) if a pivot is not positive.
+__device__ bool blk_cholesky(double* A, int d, double* rinv, int* fail)
 {
-    double s = 0.0;
-    for (int i = 0; i < d; ++i) {
-        const double ct = c * t[i];
-        const double den = ct + lambda * (1.0 - t[i]);
-        s += den > 0.0 ? ct / den : 0.0;
+    const int tid = threadIdx.x;
+    if (tid == 0) *fail = 0;
+    __syncthreads();
+    for (int j = 0; j < d; ++j) {
+        if (tid == 0) {
+            const double p = A[j * d + j];
+            if (!(p > 0.0)) {
+                *fail = 1;
+            } else {
+                const double l = sqrt(p);
+                A[j * d + j] = l;
+                rinv[j] = 1.0 / l;
+            }
+        }
+        __syncthreads();
+        if (*fail) return false;
+        for (int i = j + 1 + tid; i < d; i += blockDim.x) A[i * d + j] *= rinv[j];
+        __syncthreads();
+        const int m = d - j - 1;                 // trailing size; its lower triangle is updated
+        for (int e = tid; e < m * m; e += blockDim.x) {
+            const int p = e / m, q = e - (e / m) * m;
+            if (q > p) continue;
+            const int r = j + 1 + p, c = j + 1 + q;
+            A[r * d + c] -= A[r * d + j] * A[c * d + j];
+        }
+        __syncthreads();
     }
-    return s;
+    return true;
 }
 
-__global__ void k_dro(DroArgs a)
+// Block sum of one value per thread (fixed order: warp shuffles, then warps in order).
+__device__ double blk_sum(double v, double* red)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int nw = blockDim.x >> 5;
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t += red[w];
+    __syncthreads();
+    return t;
+}
+
+__global__ void __launch_bounds__(kLamThreads) k_lambda(LamArgs a)
 {
     const int k = blockIdx.x, ph = blockIdx.y;
-    if (ph >= a.phases || threadIdx.x != 0) return;
-    const int d = a.l_d[k], ld = d;
+    if (ph >= a.phases) return;
+    const int tid = threadIdx.x;
+    const int d = a.l_d[k];
     extern __shared__ double sm[];
-    double* G = sm;
-    double* Kp = G + d * d;
-    double* L = Kp + d * d;
-    double* M = L + d * d;
-    double* A = M + d * d;
-    double* col = A + d * d;
-    double* ev = col + d;
+    double* G = sm;                 // d x d
+    double* A = G + d * d;          // d x d: G + lambda K, then its Cholesky factor
+    double* Dp = A + d * d;         // nr x d difference matrix
+    double* Y = Dp + d * d;         // d x nr: L^-1 Dp^T
+    double* rinv = Y + d * d;       // d
+    __shared__ double red[kLamThreads / 32];
+    __shared__ int fail;
+    __shared__ double sh_x;
+    __shared__ int sh_done, sh_status;
     const double* Gs = a.G + ((int64_t)ph * a.K + k) * a.D * a.D;
-    for (int i = 0; i < d; ++i)
-        for (int j = 0; j < d; ++j) G[i * ld + j] = Gs[i * a.D + j];
-    for (int i = 0; i < d * d; ++i) Kp[i] = 0.0;
+    for (int e = tid; e < d * d; e += blockDim.x) G[e] = Gs[(e / d) * a.D + e % d];
     const bool pspline = a.l_type[k] == CWB_BL_PSPLINE;
+    const int ord = pspline ? a.l_diff[k] : 0;
+    const int nr = d - ord;
+    if (pspline) {
+        // row r of the order-`ord` difference matrix: (-1)^(ord - t) binom(ord, t) at column r + t
+        for (int e = tid; e < nr * d; e += blockDim.x) {
+            const int r = e / d, c = e % d, t = c - r;
+            double v = 0.0;
+            if (t >= 0 && t <= ord) {
+                double bin = 1.0;
+                for (int u = 1; u <= t; ++u) bin = bin * (ord - u + 1) / u;
+                v = ((ord - t) & 1) ? -bin : bin;
+            }
+            Dp[e] = v;
+        }
+    }
+    __syncthreads();
+    // A = G + lam K, K = Dp^T Dp
+    auto form = [&](double lam) {
+        for (int e = tid; e < d * d; e += blockDim.x) {
+            const int i = e / d, j = e % d;
+            double kv = 0.0;
+            if (pspline)
+                for (int r = max(0, max(i, j) - ord); r <= min(nr - 1, min(i, j)); ++r) kv += Dp[r * d + i] * Dp[r * d + j];
+            A[e] = G[e] + lam * kv;
+        }
+        __syncthreads();
+    };
+    // df1(lam) and its derivative in ln(lam) from the factor in A; false if A is not PD
+    auto evaluate = [&](double lam, double* v, double* dv) -> bool {
+        form(lam);
+        if (!blk_cholesky(A, d, rinv, &fail)) return false;
+        // Y = L^-1 Dp^T: one column (difference row) per thread, forward substitution
+        for (int r = tid; r < nr; r += blockDim.x) {
+            for (int i = 0; i < d; ++i) {
+                double t = Dp[r * d + i];
+                for (int q = 0; q < i; ++q) t -= A[i * d + q] * Y[q * nr + r];
+                Y[i * nr + r] = t * rinv[i];
+            }
+        }
+        __syncthreads();
+        double t1 = 0.0, t2 = 0.0;
+        for (int e = tid; e < d * nr; e += blockDim.x) t1 += Y[e] * Y[e];
+        for (int e = tid; e < nr * nr; e += blockDim.x) {
+            const int r = e / nr, c = e % nr;
+            double g = 0.0;
+            for (int i = 0; i < d; ++i) g += Y[i * nr + r] * Y[i * nr + c];
+            t2 += g * g;
+        }
+        t1 = blk_sum(t1, red);
+        t2 = blk_sum(t2, red);
+        *v = (double)d - lam * t1;
+        *dv = -lam * t1 + lam * lam * t2;
+        return true;
+    };
+
     int status = 0;
     double lam = 0.0;
     if (pspline) {
-        // difference matrix of the requested order (in M), K = D^T D
-        const int ord = a.l_diff[k];
-        for (int i = 0; i < d * d; ++i) M[i] = 0.0;
-        for (int i = 0; i < d; ++i) M[i * ld + i] = 1.0;
-        int rows = d;
-        for (int o = 0; o < ord; ++o) {
-            for (int i = 0; i < rows - 1; ++i)
-                for (int j = 0; j < d; ++j) M[i * ld + j] = M[(i + 1) * ld + j] - M[i * ld + j];
-            rows -= 1;
-        }
-        for (int p = 0; p < d; ++p)
-            for (int q = 0; q < d; ++q) {
-                double s = 0.0;
-                for (int i = 0; i < rows; ++i) s += M[i * ld + p] * M[i * ld + q];
-                Kp[p * ld + q] = s;
-            }
         const double df = a.l_df[k];
-        double trg = 0.0, trk = 0.0;
-        for (int i = 0; i < d; ++i) { trg += G[i * ld + i]; trk += Kp[i * ld + i]; }
-        const double c = trg / trk;
         if (!(df > 0.0)) {
             lam = a.l_lambda[k];
         } else {
-            for (int i = 0; i < d * d; ++i) A[i] = G[i] + c * Kp[i];
-            if (!dev_cholesky(A, d, ld, L)) {
-                status = 1;
+            // unpenalised fit: df1(0) = d when G is positive definite
+            form(0.0);
+            const bool g_pd = blk_cholesky(A, d, rinv, &fail);
+            if (g_pd && df >= (double)d) {
+                lam = 0.0;
             } else {
-                // M = L^-1 G L^-T: solve L X = G column by column (X in A), then L M = X^T
-                for (int j = 0; j < d; ++j)
-                    for (int i = 0; i < d; ++i) {
-                        double t = G[i * ld + j];
-                        for (int q = 0; q < i; ++q) t -= L[i * ld + q] * A[q * ld + j];
-                        A[i * ld + j] = t / L[i * ld + i];
+                double trg = 0.0, trk = 0.0;
+                for (int i = 0; i < d; ++i) {
+                    trg += G[i * d + i];
+                    for (int r = max(0, i - ord); r <= min(nr - 1, i); ++r) trk += Dp[r * d + i] * Dp[r * d + i];
+                }
+                const double c = log10(trg / trk);
+                double lo = c - 12.0, hi = c + 12.0, v = 0.0, dv = 0.0;
+                if (!(trg > 0.0) || !(trk > 0.0)) status = 1;
+                else if (!evaluate(pow(10.0, lo), &v, &dv)) status = 1;
+                else if (v < df) lam = pow(10.0, lo);
+                else if (!evaluate(pow(10.0, hi), &v, &dv)) status = 1;
+                else if (v > df) status = 2;
+                else {
+                    if (tid == 0) {
+                        sh_x = c;
+                        sh_done = 0;
+                        sh_status = 0;
                     }
-                for (int j = 0; j < d; ++j)
-                    for (int i = 0; i < d; ++i) {
-                        double t = A[j * ld + i];
-                        for (int q = 0; q < i; ++q) t -= L[i * ld + q] * M[q * ld + j];
-                        M[i * ld + j] = t / L[i * ld + i];
-                    }
-                for (int i = 0; i < d; ++i)
-                    for (int j = i + 1; j < d; ++j) {
-                        double s = 0.5 * (M[i * ld + j] + M[j * ld + i]);
-                        M[i * ld + j] = s;
-                        M[j * ld + i] = s;
-                    }
-                dev_jacobi_eigenvalues(M, d, ld, ev);
-                for (int i = 0; i < d; ++i) ev[i] = fmin(fmax(ev[i], 0.0), 1.0);
-                const double full = dev_df_dro(ev, d, c, 0.0);
-                if (df >= full) {
-                    lam = 0.0;
-                } else {
-                    const double center = log10(c);
-                    double lo = center - 20.0, hi = center + 20.0;
-                    if (dev_df_dro(ev, d, c, pow(10.0, hi)) > df) {
-                        status = 2;
-                    } else {
-                        for (int it = 0; it < 400 && hi - lo >= 1e-15; ++it) {
-                            double mid = 0.5 * (lo + hi);
-                            if (dev_df_dro(ev, d, c, pow(10.0, mid)) > df) lo = mid; else hi = mid;
+                    __syncthreads();
+                    double prev_res = INFINITY;
+                    for (int it = 0; it < 200; ++it) {
+                        const double x = sh_x;
+                        if (!evaluate(pow(10.0, x), &v, &dv)) {
+                            if (tid == 0) sh_status = 1;
+                            __syncthreads();
+                            break;
                         }
-                        // polish on the definition in a narrow bracket around the root
-                        double x0 = 0.5 * (lo + hi), v;
-                        double blo = x0 - 1e-3, bhi = x0 + 1e-3;
-                        bool ok_lo = dev_df_direct(G, Kp, d, ld, pow(10.0, blo), A, L, col, &v) && v > df;
-                        bool ok_hi = dev_df_direct(G, Kp, d, ld, pow(10.0, bhi), A, L, col, &v) && v < df;
-                        if (ok_lo && ok_hi) {
-                            for (int it = 0; it < 80 && bhi - blo >= 1e-15; ++it) {
-                                double mid = 0.5 * (blo + bhi);
-                                if (!dev_df_direct(G, Kp, d, ld, pow(10.0, mid), A, L, col, &v)) break;
-                                if (v > df) blo = mid; else bhi = mid;
+                        if (tid == 0) {
+                            const double res = v - df;
+                            if (res > 0.0) lo = x; else hi = x;
+                            const double slope = dv * 2.302585092994046;     // d df1 / d log10(lambda)
+                            const double xt = slope < 0.0 ? x - res / slope : x;
+                            const bool in = xt > lo && xt < hi;
+                            double xn;
+                            if (fabs(res) <= 1e-13 * df) {            // converged: one last Newton step
+                                xn = in ? xt : x;
+                                sh_done = 1;
+                            } else {
+                                xn = (in && fabs(res) <= 0.5 * prev_res) ? xt : 0.5 * (lo + hi);
+                                if (hi - lo < 1e-15 || xn == x) sh_done = 1;
                             }
-                            x0 = 0.5 * (blo + bhi);
+                            prev_res = fabs(res);
+                            sh_x = xn;
                         }
-                        lam = pow(10.0, x0);
+                        __syncthreads();
+                        if (sh_done) break;
                     }
+                    status = sh_status;
+                    lam = pow(10.0, sh_x);
                 }
             }
         }
     }
+    // P = (G + lam K)^-1, zero outside d x d
     double* Pout = a.P + ((int64_t)ph * a.K + k) * a.D * a.D;
-    for (int i = 0; i < a.D * a.D; ++i) Pout[i] = 0.0;
+    for (int e = tid; e < a.D * a.D; e += blockDim.x) Pout[e] = 0.0;
+    __syncthreads();
     if (status == 0) {
-        for (int i = 0; i < d; ++i)
-            for (int j = 0; j < d; ++j) A[i * ld + j] = G[i * ld + j] + lam * Kp[i * ld + j];
-        if (!dev_cholesky(A, d, ld, L)) {
+        form(lam);
+        if (!blk_cholesky(A, d, rinv, &fail)) {
             status = 1;
         } else {
-            for (int j = 0; j < d; ++j) {
-                for (int i = 0; i < d; ++i) col[i] = (i == j) ? 1.0 : 0.0;
-                dev_chol_solve(L, d, ld, col);
+            // column j of A^-1: forward then backward substitution, one column per thread
+            for (int j = tid; j < d; j += blockDim.x) {
+                double* col = Y + j * d;          // Y is free now: d columns of length d
+                for (int i = 0; i < d; ++i) {
+                    double t = (i == j) ? 1.0 : 0.0;
+                    for (int q = 0; q < i; ++q) t -= A[i * d + q] * col[q];
+                    col[i] = t * rinv[i];
+                }
+                for (int i = d - 1; i >= 0; --i) {
+                    double t = col[i];
+                    for (int q = i + 1; q < d; ++q) t -= A[q * d + i] * col[q];
+                    col[i] = t * rinv[i];
+                }
                 for (int i = 0; i < d; ++i) Pout[i * a.D + j] = col[i];
             }
         }
     }
-    a.lambda[(int64_t)ph * a.K + k] = lam;
-    a.status[(int64_t)ph * a.K + k] = status;
+    if (tid == 0) {
+        a.lambda[(int64_t)ph * a.K + k] = lam;
+        a.status[(int64_t)ph * a.K + k] = status;
+    }
 }
 
 // ---------------------------------------------------------------------------
 // Offset: loss-optimal constant over the fitting rows (L2: weighted mean,
 // binomial: logit of the weighted mean).
 
-__global__ void k_offset(const double* __restrict__ y, const double* __restrict__ w, int64_t n_fit, int loss,
-                         double* __restrict__ out /* [0] offset, [1] mean */)
+constexpr int kOffsetBlocks = 256;
+
+__global__ void k_offset_partial(const double* __restrict__ y, const double* __restrict__ w, int64_t n_fit,
+                                 double* __restrict__ part /* [2][kOffsetBlocks] */)
 {
-    __shared__ double s1[1024], s2[1024];
+    __shared__ double s1[kThreads], s2[kThreads];
     double a = 0.0, b = 0.0;
-    for (int64_t i = threadIdx.x; i < n_fit; i += blockDim.x) {
-        double wi = w ? w[i] : 1.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_fit; i += (int64_t)gridDim.x * blockDim.x) {
+        const double wi = w ? w[i] : 1.0;
         a += wi * y[i];
         b += wi;
     }
@@ -680,10 +693,22 @@ __global__ void k_offset(const double* __restrict__ y, const double* __restrict_
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        double mean = s1[0] / s2[0];
-        out[1] = mean;
-        out[0] = (loss == CWB_LOSS_L2) ? mean : log(mean / (1.0 - mean));
+        part[blockIdx.x] = s1[0];
+        part[gridDim.x + blockIdx.x] = s2[0];
     }
+}
+
+__global__ void k_offset(const double* __restrict__ part, int nblk, int loss, double* __restrict__ out /* [0] offset, [1] mean */)
+{
+    if (threadIdx.x != 0) return;
+    double a = 0.0, b = 0.0;
+    for (int i = 0; i < nblk; ++i) {
+        a += part[i];
+        b += part[nblk + i];
+    }
+    const double mean = a / b;
+    out[1] = mean;
+    out[0] = (loss == CWB_LOSS_L2) ? mean : log(mean / (1.0 - mean));
 }
 
 __global__ void k_init_rows(int64_t n_pad, float off_hi, float off_lo, float* f, float* h, float* c, float* rw)
@@ -834,7 +859,7 @@ cwb_status setup_model(cwb_model* m, const void* X_in, int x_dtype, const void* 
     int32_t* feat_d = nullptr;
     CWB_TRY(tmp.get(&feat_d, (size_t)B, s));
     CWB_CUDA_TRY(cudaMemcpyAsync(feat_d, feat_h.data(), sizeof(int32_t) * B, cudaMemcpyHostToDevice, s));
-    const int nblk = std::min<int>(64, (int)ceil_div(n, kThreads));
+    const int nblk = std::max(1, std::min<int>(std::max(1, 2048 / std::max(B, 1)), (int)ceil_div(n, kThreads)));
     double *pmin = nullptr, *pmax = nullptr, *xmin_d = nullptr, *xmax_d = nullptr;
     CWB_TRY(tmp.get(&pmin, (size_t)B * nblk, s));
     CWB_TRY(tmp.get(&pmax, (size_t)B * nblk, s));
@@ -1044,10 +1069,15 @@ cwb_status setup_model(cwb_model* m, const void* X_in, int x_dtype, const void* 
     CWB_TRY(tmp.get(&lstat, (size_t)2 * K, s));
     k_gram<<<dim3(K, 2), kThreads, 0, s>>>(S, D, K, m->l_bin, m->l_d, nnz_d, m->zb64, m->zcol, m->crange, cnt, B, m->G);
     {
-        DroArgs a{K, D, m->l_type, m->l_d, ldiff_d, ldf_d, llam_d, m->G, m->P, m->lambda, lstat, 2};
-        size_t smem = sizeof(double) * (5 * dd + 2 * D);
-        CWB_CUDA_TRY(cudaFuncSetAttribute(k_dro, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_dro<<<dim3(K, 2), 32, smem, s>>>(a);
+        LamArgs a{K, D, m->l_type, m->l_d, ldiff_d, ldf_d, llam_d, m->G, m->P, m->lambda, lstat, phases};
+        size_t smem = sizeof(double) * (4 * dd + D);
+        CWB_CUDA_TRY(cudaFuncSetAttribute(k_lambda, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_lambda<<<dim3(K, phases), kLamThreads, smem, s>>>(a);
+        if (phases == 1) {           // one cache serves both phases
+            CWB_CUDA_TRY(cudaMemcpyAsync(m->P + (size_t)K * dd, m->P, sizeof(double) * K * dd, cudaMemcpyDeviceToDevice, s));
+            CWB_CUDA_TRY(cudaMemcpyAsync(m->lambda + K, m->lambda, sizeof(double) * K, cudaMemcpyDeviceToDevice, s));
+            CWB_CUDA_TRY(cudaMemsetAsync(lstat + K, 0, sizeof(int32_t) * K, s));
+        }
     }
     CWB_CUDA_TRY(cudaGetLastError());
     std::vector<int32_t> lstat_h(2 * K);
@@ -1069,9 +1099,11 @@ cwb_status setup_model(cwb_model* m, const void* X_in, int x_dtype, const void* 
         }
 
     // --- offset and initial models
-    double* off_d = nullptr;
+    double *off_d = nullptr, *off_part = nullptr;
     CWB_TRY(tmp.get(&off_d, 2, s));
-    k_offset<<<1, 1024, 0, s>>>(y64, w64, m->n_tr, m->cfg.loss, off_d);
+    CWB_TRY(tmp.get(&off_part, 2 * kOffsetBlocks, s));
+    k_offset_partial<<<kOffsetBlocks, kThreads, 0, s>>>(y64, w64, m->n_tr, off_part);
+    k_offset<<<1, 32, 0, s>>>(off_part, kOffsetBlocks, m->cfg.loss, off_d);
     double off_h[2] = {0.0, 0.0};
     CWB_CUDA_TRY(cudaMemcpyAsync(off_h, off_d, sizeof(off_h), cudaMemcpyDeviceToHost, s));
     CWB_CUDA_TRY(cudaStreamSynchronize(s));
