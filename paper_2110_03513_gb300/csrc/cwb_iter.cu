@@ -30,10 +30,19 @@ namespace {
 
 constexpr int kRowThreads = 256;
 constexpr int kSolveThreads = 512;
-constexpr int kScatterThreads = 576;   // 16 consumer warps + 1 loader warp + 1 converter warp
+constexpr int kScatterWarps = 16;      // consumer warps of a scatter CTA
+constexpr int kScatterThreads = (kScatterWarps + 2) * 32;   // + 1 loader warp + 1 converter warp
+constexpr int kStageRows = 256;        // rows per pipeline stage (tile)
 constexpr int kGraphIters = 32;
 
 enum { kRowsFused = 0, kRowsUpdate = 1, kRowsResid = 2 };
+
+// Programmatic dependent launch: the iteration's kernels are launched so that each may start
+// while its predecessor drains.  grid_dep_wait() blocks until the predecessor grid has completed
+// and its memory is visible (a no-op without a programmatic dependency); grid_dep_launch() lets
+// the successor grid be scheduled.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 struct RowArgs {
     DevState* state;
@@ -181,6 +190,8 @@ __device__ __forceinline__ void store_df4(float* p, int64_t i4, const DF v[4])
 template <int KIND, typename IndT>
 __global__ void __launch_bounds__(kRowThreads, 4) k_rows(RowArgs a)
 {
+    grid_dep_wait();
+    grid_dep_launch();
     const DevState st = *a.state;
     const bool pend = (KIND != kRowsResid) && (st.m > st.m_applied);
     const int pm = st.pend_mode;
@@ -443,7 +454,7 @@ struct ScatterArgs {
     int B, F, FE, bin_ranges, nb_cta, ch_stride;
     int stage_rows, stages, nb_box, box_bytes, unit_rows;
     int cs;
-    const int32_t* cluster_slot;   // [clusters]
+    const int32_t* cluster_slot;   // [2][clusters]: slot of each cluster, then its index within the slot
     const int32_t* slot_c0;        // [slots + 1]: first cluster of each slot
     int hybrid;
     uint32_t ind_off, r_off, q_off, hist_off, bar_off, stage_ind_bytes, stage_r_bytes;
@@ -565,30 +576,22 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
     const int rank = (int)cluster.block_rank();
     const int cl = blockIdx.x / a.cs;
     const int slot = a.cluster_slot[cl];
+    const int cin = a.cluster_slot[gridDim.x / a.cs + cl];
     const int g = slot / a.bin_ranges, br = slot % a.bin_ranges;
     const int ncl = a.slot_c0[slot + 1] - a.slot_c0[slot];
-    const int cin = cl - a.slot_c0[slot];
+    const int pcl = a.slot_c0[slot] + cin;        // this cluster's row of partial histograms
 
     const bool counting = a.count_rows >= 0;
-    const int mode = a.state->mode;
-    const int C = (!counting && CMAX == 2 && mode == kModeACWB) ? 2 : 1;
-    const bool train_rows = a.hybrid && mode == kModeACWB;
-    const int64_t n_act = counting ? a.count_rows : (train_rows ? a.n_tr : a.n);
-    const int64_t tiles = (n_act + a.stage_rows - 1) / a.stage_rows;
-    const int64_t pieces = (int64_t)ncl * a.cs, piece = (int64_t)cin * a.cs + rank;
-    const int64_t t_lo = tiles * piece / pieces, t_hi = tiles * (piece + 1) / pieces;
-    const int ntiles = (int)(t_hi - t_lo);
-
     const int F = FL2 >= 0 ? (1 << FL2) : a.F;   // lanes per channel and row set (power of two)
     const int FE = a.FE;                // binnings of this group held in the ring (<= F)
     const int b_lo = br * a.nb_cta;
-    const int row_bytes = a.stage_rows * (int)sizeof(IndT);
+    constexpr int row_bytes = kStageRows * (int)sizeof(IndT);
     Acc* hist = reinterpret_cast<Acc*>(smem + a.hist_off);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + a.bar_off);
     uint64_t* ready = full + a.stages;
     uint64_t* empty = ready + a.stages;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int W = (int)(blockDim.x >> 5) - 2;               // consumer warps; warp W loads, warp W+1 converts
+    constexpr int W = kScatterWarps;                          // consumer warps; warp W loads, warp W+1 converts
 
     for (int i = tid; i < CMAX * a.ch_stride; i += blockDim.x) hist[i] = Acc(0);
     if (tid == 0) {
@@ -600,27 +603,43 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
+    // everything below reads what the row pass wrote (iteration state, residuals)
+    grid_dep_wait();
+    const int mode = a.state->mode;
+    const int C = (!counting && CMAX == 2 && mode == kModeACWB) ? 2 : 1;
+    const bool train_rows = a.hybrid && mode == kModeACWB;
+    const int64_t n_act = counting ? a.count_rows : (train_rows ? a.n_tr : a.n);
+    const int64_t tiles = (n_act + kStageRows - 1) / kStageRows;
+    const int64_t pieces = (int64_t)ncl * a.cs, piece = (int64_t)cin * a.cs + rank;
+    const int64_t t_lo = tiles * piece / pieces, t_hi = tiles * (piece + 1) / pieces;
+    const int ntiles = (int)(t_hi - t_lo);
     const long long deadline = clock64() + kWaitCycles;
 
     if (warp == W) {
-        // loader: one 2D TMA box (the tile's rows x FE binnings) and C residual rows per tile
+        // loader: one 3D TMA box (the tile's rows x FE binnings) and C residual rows per tile
         if (lane == 0) {
-            const uint32_t bytes = (uint32_t)(FE * row_bytes + C * a.stage_rows * 4);   // box bytes + residual rows
+            const uint32_t bytes = (uint32_t)(FE * row_bytes + C * kStageRows * 4);   // box bytes + residual rows
             int issued = 0;
             bool ok = true;
-            for (int it = 0; it < ntiles; ++it) {
-                const int s = it % a.stages;
-                if (it >= a.stages && !mbar_wait(&empty[s], ((it / a.stages) - 1) & 1, deadline)) {
+            // ring position kept incrementally (no division by the run-time stage count per tile)
+            int s = 0;
+            uint32_t ph = 0;
+            for (int it = 0; it < ntiles; ++it, ++s) {
+                if (s == a.stages) {
+                    s = 0;
+                    ph ^= 1u;
+                }
+                if (it >= a.stages && !mbar_wait(&empty[s], ph ^ 1u, deadline)) {
                     ok = false;
                     break;
                 }
-                const int64_t row0 = (t_lo + it) * a.stage_rows;
+                const int64_t row0 = (t_lo + it) * kStageRows;
                 mbar_arrive_expect_tx(&full[s], bytes);
                 tma_load_3d(smem + a.ind_off + (size_t)s * a.stage_ind_bytes, &tmap, 0, g * FE,
                             (int)(row0 / (128 / (int)sizeof(IndT))), &full[s]);
                 float* r_dst = reinterpret_cast<float*>(smem + a.r_off + (size_t)s * a.stage_r_bytes);
                 for (int ch = 0; ch < C; ++ch)
-                    bulk_load(r_dst + ch * a.stage_rows, a.rw + ch * a.n_pad + row0, (uint32_t)a.stage_rows * 4,
+                    bulk_load(r_dst + ch * kStageRows, a.rw + ch * a.n_pad + row0, (uint32_t)kStageRows * 4,
                               &full[s]);
                 ++issued;
             }
@@ -640,12 +659,14 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
             scale[0] = pow2f(fixed_scale(a.state->rmax_bits[0], a.state->cnt_log2[cidx]));
             if (C == 2) scale[1] = pow2f(fixed_scale(a.state->rmax_bits[1], a.state->cnt_log2[cidx]));
         }
-        if (a.stage_rows % 128 != 0) {               // the vectorised conversion below needs it
-            if (lane == 0) atomicOr(a.err, kErrIndex);
-        }
-        for (int jt = 0; jt < ntiles; ++jt) {
-            const int s = jt % a.stages;
-            if (!__all_sync(0xffffffffu, mbar_wait(&full[s], (jt / a.stages) & 1, deadline))) {
+        int s = 0;
+        uint32_t ph = 0;
+        for (int jt = 0; jt < ntiles; ++jt, ++s) {
+            if (s == a.stages) {
+                s = 0;
+                ph ^= 1u;
+            }
+            if (!__all_sync(0xffffffffu, mbar_wait(&full[s], ph, deadline))) {
                 if (lane == 0) atomicOr(a.err, kErrTimeout);
                 break;
             }
@@ -654,14 +675,14 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
                 // async-proxy writes and generic reads
                 const float* rt = reinterpret_cast<const float*>(smem + a.r_off + (size_t)s * a.stage_r_bytes);
                 int* qt = reinterpret_cast<int*>(smem + a.q_off + (size_t)s * a.stage_r_bytes);
-                const int64_t row0 = (t_lo + jt) * a.stage_rows;
+                const int64_t row0 = (t_lo + jt) * kStageRows;
                 // 16-byte vectors, the loads of a lane issued together: the conversion sits on
                 // the pipeline's critical path and its shared-memory accesses queue behind the
                 // consumers' atomics, so it pays that queue once per batch, not once per value
-                const int total = C * a.stage_rows;          // multiple of 128
+                const int total = C * kStageRows;          // multiple of 128
 #pragma unroll 4
                 for (int i0 = lane * 4; i0 < total; i0 += 128) {
-                    const int ch = i0 >= a.stage_rows ? 1 : 0;
+                    const int ch = i0 >= kStageRows ? 1 : 0;
                     int4 q;
                     if (counting) {
                         const int64_t r = row0 + i0;
@@ -682,22 +703,27 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
         const int q = lane / F;
         const int f = lane % F;
         const int ch = q % C, rs = q / C;
-        const int RS = 32 / (F * C);
+        const int RS = 32 / (F * C);                      // compile-time for the common plans
         const bool active = f < FE && g * FE + f < a.B;
         Acc* hf = hist + ch * a.ch_stride + f;
         const int fsh = FL2 >= 0 ? FL2 : __ffs(F) - 1;    // F is a power of two
-        const int nunits = row_bytes / 16;
+        constexpr int nunits = row_bytes / 16;
         const int step = UN * RS;
-        for (int it = 0; it < ntiles; ++it) {
-            const int s = it % a.stages;
-            if (!__all_sync(0xffffffffu, mbar_wait(&ready[s], (it / a.stages) & 1, deadline))) {
+        int s = 0;
+        uint32_t ph = 0;
+        for (int it = 0; it < ntiles; ++it, ++s) {
+            if (s == a.stages) {
+                s = 0;
+                ph ^= 1u;
+            }
+            if (!__all_sync(0xffffffffu, mbar_wait(&ready[s], ph, deadline))) {
                 if (lane == 0) atomicOr(a.err, kErrTimeout);
                 break;
             }
             const unsigned char* ind_st = smem + a.ind_off + (size_t)s * a.stage_ind_bytes;
             const Acc* r_st =
                 reinterpret_cast<const Acc*>(smem + (INT_ACC ? a.q_off : a.r_off) + (size_t)s * a.stage_r_bytes) +
-                ch * a.stage_rows;
+                ch * kStageRows;
             if (active) {
 #pragma unroll 1
                 for (int u0 = warp * step; u0 < nunits; u0 += W * step) {
@@ -746,6 +772,7 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
             if (lane == 0) mbar_arrive(&empty[s]);
         }
     }
+    grid_dep_launch();                 // the solve may be scheduled as SMs free up
     __syncthreads();
     cluster.sync();
     // Sum the cluster's histograms (fixed rank order), each CTA one slice of the bins,
@@ -760,7 +787,7 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
     const int fsh_e = __ffs(F) - 1;
     Acc* stg = reinterpret_cast<Acc*>(smem);
     for (int ch = 0; ch < C; ++ch) {
-        Acc* dst = reinterpret_cast<Acc*>(a.part) + ((int64_t)cl * CMAX + ch) * (int64_t)F * nb;
+        Acc* dst = reinterpret_cast<Acc*>(a.part) + ((int64_t)pcl * CMAX + ch) * (int64_t)F * nb;
         for (int c0 = bl0; c0 < bl1; c0 += cb) {
             const int c1 = min(bl1, c0 + cb);
             const int nvec = ((c1 - c0) * F) >> 2;
@@ -800,10 +827,8 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
             }
             __syncthreads();
             const int nbc = c1 - c0;
-            for (int e = tid; e < F * nbc; e += blockDim.x) {
-                const int f = e / nbc, lb = e - f * nbc;
-                dst[(int64_t)f * nb + c0 + lb] = stg[f * (cb + 1) + lb];
-            }
+            for (int f = warp; f < F; f += (int)(blockDim.x >> 5))          // a warp per binning row
+                for (int lb = lane; lb < nbc; lb += 32) dst[(int64_t)f * nb + c0 + lb] = stg[f * (cb + 1) + lb];
             __syncthreads();
         }
     }
@@ -942,10 +967,6 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(SolveArgs a)
     constexpr int kColsPerWarp = (kMaxD + NW - 1) / NW;
     const int k = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const DevState st = *a.state;
-    const int mode = st.mode;
-    const int C = (mode == kModeACWB) ? 2 : 1;
-    const int ph = (mode == kModeACWB) ? 0 : st.phase;
     const int b = a.l_bin[k], d = a.l_d[k], nst = a.l_nstar[k];
     const int D = a.D, S = a.S;
     // dynamic shared memory: P, G (D x D, FP64), the learner's design rows (float4 + first
@@ -962,14 +983,9 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(SolveArgs a)
     __shared__ double s_s[2][kMaxD], th_s[2][kMaxD], term[2][kMaxD];
     __shared__ bool is_last;
 
-    // ---- static per-learner data (independent of this iteration): asynchronous copies, one round trip
+    // ---- static per-learner data (independent of this iteration): asynchronous copies issued
+    // before waiting for the scatter, so they overlap its tail
     {
-        const double* Pk = a.P + ((int64_t)ph * a.K + k) * D * D;
-        const double* Gk = a.G + ((int64_t)ph * a.K + k) * D * D;
-        for (int e = tid; e < D * D; e += blockDim.x) {
-            cp_async8(Ps + e, Pk + e);
-            cp_async8(Gs + e, Gk + e);
-        }
         if (a.stage_v) {
             const float4* zb_g = reinterpret_cast<const float4*>(a.zb) + (int64_t)k * S;
             const int* zc_g = a.zcol + (int64_t)k * S;
@@ -981,6 +997,20 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(SolveArgs a)
         if (a.stage_z) {
             const float4* zt4 = reinterpret_cast<const float4*>(a.ztab + (int64_t)k * kMaxNnz * S);
             for (int e = tid; e < nst; e += blockDim.x) cp_async16(reinterpret_cast<float4*>(zt_s) + e, zt4 + e);
+        }
+    }
+    grid_dep_wait();                   // histograms and iteration state from here on
+    grid_dep_launch();                 // the next row pass may be scheduled on idle SMs
+    const DevState st = *a.state;
+    const int mode = st.mode;
+    const int C = (mode == kModeACWB) ? 2 : 1;
+    const int ph = (mode == kModeACWB) ? 0 : st.phase;    // P and G of the cache this iteration uses
+    {
+        const double* Pk = a.P + ((int64_t)ph * a.K + k) * D * D;
+        const double* Gk = a.G + ((int64_t)ph * a.K + k) * D * D;
+        for (int e = tid; e < D * D; e += blockDim.x) {
+            cp_async8(Ps + e, Pk + e);
+            cp_async8(Gs + e, Gk + e);
         }
     }
     const float* zt = a.stage_z ? zt_s : a.ztab + (int64_t)k * kMaxNnz * S;
@@ -1314,9 +1344,17 @@ template <int KIND>
 void launch_rows(cwb_model* m, cudaStream_t s)
 {
     RowArgs a = row_args(m);
-    const int g = rows_grid(m);
-    if (m->ind_bytes == 1) k_rows<KIND, uint8_t><<<g, kRowThreads, 0, s>>>(a);
-    else k_rows<KIND, uint16_t><<<g, kRowThreads, 0, s>>>(a);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(rows_grid(m), 1, 1);
+    cfg.blockDim = dim3(kRowThreads, 1, 1);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (m->ind_bytes == 1) cudaLaunchKernelEx(&cfg, k_rows<KIND, uint8_t>, a);
+    else cudaLaunchKernelEx(&cfg, k_rows<KIND, uint16_t>, a);
 }
 
 template <typename IndT, int CMAX, bool INT_ACC>
@@ -1328,13 +1366,15 @@ cudaError_t launch_scatter_t(cwb_model* m, cudaStream_t s, const ScatterArgs& a)
     cfg.blockDim = dim3(P.threads, 1, 1);
     cfg.dynamicSmemBytes = P.smem;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = P.cs;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     if (P.bin_ranges > 1) return cudaLaunchKernelEx(&cfg, k_scatter<IndT, CMAX, INT_ACC, true, -1>, m->tmap, a);
     if (P.f_lane == 32) return cudaLaunchKernelEx(&cfg, k_scatter<IndT, CMAX, INT_ACC, false, 5>, m->tmap, a);
     if (P.f_lane == 16) return cudaLaunchKernelEx(&cfg, k_scatter<IndT, CMAX, INT_ACC, false, 4>, m->tmap, a);
@@ -1441,9 +1481,18 @@ void launch_solve(cwb_model* m, cudaStream_t s)
     a.tr_q = m->tr_q;
     a.forced = m->forced;
     a.trace_cap = m->trace_cap;
-    const size_t smem = solve_smem(m, P.solve_stage_v, P.solve_stage_z);
-    if (P.int_acc) k_solve<true><<<m->K, kSolveThreads, smem, s>>>(a);
-    else k_solve<false><<<m->K, kSolveThreads, smem, s>>>(a);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(m->K, 1, 1);
+    cfg.blockDim = dim3(kSolveThreads, 1, 1);
+    cfg.dynamicSmemBytes = solve_smem(m, P.solve_stage_v, P.solve_stage_z);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (P.int_acc) cudaLaunchKernelEx(&cfg, k_solve<true>, a);
+    else cudaLaunchKernelEx(&cfg, k_solve<false>, a);
 }
 
 // One iteration's launches.  With a profiling mask (only while capturing the
@@ -1549,7 +1598,7 @@ cwb_status plan_scatter(cwb_model* m)
     while (pow2B < B) pow2B <<= 1;
     ScatterPlan P{};
     P.cmax = cmax;
-    P.stage_rows = 256;
+    P.stage_rows = kStageRows;
     P.nb_box = 1;
     P.bin_ranges = 1;
     auto ch_stride_for = [&](int nb, int F) {
@@ -1626,12 +1675,22 @@ cwb_status plan_scatter(cwb_model* m)
     int total = std::max(best_used / best_cs, P.slots);
     std::vector<int> per(P.slots, total / P.slots);
     for (int sl = 0; sl < total % P.slots; ++sl) per[sl] += 1;
-    std::vector<int32_t> slot_c0(P.slots + 1, 0), cl_slot;
+    // clusters are dealt to the slots in turn, so neighbouring CTAs stream the same rows of
+    // different binning groups; partial histograms stay grouped by slot (slot_c0)
+    std::vector<int32_t> slot_c0(P.slots + 1, 0), cl_slot, cl_in;
+    int per_max = 0;
     for (int sl = 0; sl < P.slots; ++sl) {
         slot_c0[sl + 1] = slot_c0[sl] + per[sl];
-        for (int c = 0; c < per[sl]; ++c) cl_slot.push_back(sl);
+        per_max = std::max(per_max, per[sl]);
     }
+    for (int r = 0; r < per_max; ++r)
+        for (int sl = 0; sl < P.slots; ++sl)
+            if (r < per[sl]) {
+                cl_slot.push_back(sl);
+                cl_in.push_back(r);
+            }
     P.clusters = (int)cl_slot.size();
+    cl_slot.insert(cl_slot.end(), cl_in.begin(), cl_in.end());
     P.part_floats = (size_t)P.clusters * cmax * P.nb_cta * F;
     {
         // the cluster epilogue stages [F][cb + 1] values in the ring, which precedes the histograms
