@@ -51,7 +51,7 @@ WORKLOAD = ("binned CWB, L2 loss, n=1,000,000, p=50 U[0,1] FP32 features (10 inf
 
 # DRAM traffic of one scatter launch from the committed ncu capture, valid for the
 # scatter kernel source with this SHA-256 prefix (null once the kernel changes).
-SCATTER_TRAFFIC = {"sha256": None, "bytes": None}
+SCATTER_TRAFFIC = {"sha256": "c37d25dd55bfeaee", "bytes": 104049664 + 3606016}   # one ncu capture of this kernel
 
 
 def scatter_source_hash() -> str:
@@ -212,6 +212,21 @@ def run_reference(args):
 
 # ---------------------------------------------------------------------------- GPU arm
 
+def replica_throughput(local_ms: float, steps: int, world: int, dist=None, device=None):
+    """Whole-job iterations/s of `world` independent replicas that each timed `steps` steps.
+
+    The job's time is the slowest rank's (max over ranks, one all-reduce of a scalar; the data
+    path has no collective).  Returns (iterations/s over all ranks, ms per step of the slowest rank).
+    """
+    import torch
+    total_ms = float(local_ms)
+    if dist is not None and world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return world * steps / (total_ms / 1e3), total_ms / steps
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -292,13 +307,7 @@ def run_ours(args):
         breakdown = model.get_profile()
         model.profile(False)
         plan = model.scatter_plan()
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * K / (total_ms / 1e3)
-    ms_per_step = total_ms / K
+    value, ms_per_step = replica_throughput(sum(step_ms), K, world, dist, dev)
     launches = K * 3              # rows, scatter and solve per CWB iteration
 
     # roofline of the dominant kernel (the scatter), from its own events on the model's stream
