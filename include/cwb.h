@@ -281,6 +281,67 @@ cwb_status cwb_get_scatter_plan(const cwb_model* m, int32_t* values, int32_t cap
 #define CWB_NOALLOC_SCRATCH_BYTES (16u << 20)
 cwb_status cwb_predict_noalloc(const cwb_model* m, const void* Xnew, int32_t x_dtype, int64_t n_new, float* out);
 
+/*
+ * cwb_autotune -- pick the scatter decomposition (grid size and cluster size) for this model by
+ * timing `trials` scatter launches of each candidate on the model's own data.  objective 0: the
+ * fastest scatter (the model has the GPU to itself); 1: the least SM-time, CTAs x time (models that
+ * share the GPU, e.g. in a batch or a server).  Changes no fitting state; graphs captured earlier are
+ * rebuilt on the next fit.  best_us (nullable) receives the chosen plan's time per scatter launch.
+ * Synchronises the model's stream.
+ */
+cwb_status cwb_autotune(cwb_model* m, int32_t objective, int32_t trials, double* best_us);
+
+/*
+ * Batched fits -- many independent models advanced together (for example CV folds x a
+ * hyperparameter grid).  cwb_batch_fit queues `iterations` iterations of every model: each model's
+ * next `iters_per_launch` iterations are one branch of a single CUDA graph, so one graph launch runs
+ * them for all models at once and independent branches share the GPU.  Afterwards every model is in
+ * the state cwb_fit(model, iterations) would leave (same kernels, same plan), and work later queued
+ * on a model's own stream waits for the batch.  Models must live on one device and stay alive while
+ * the batch exists; a model must not be fitted through cwb_fit while a batch launch on it is queued.
+ * cwb_batch_fit returns once the work is queued; cwb_batch_synchronize waits and reports device
+ * errors of every model.
+ */
+typedef struct cwb_batch cwb_batch;
+cwb_status cwb_batch_create(cwb_model* const* models, int32_t count, int32_t iters_per_launch, cwb_batch** out);
+cwb_status cwb_batch_fit(cwb_batch* b, int32_t iterations);
+cwb_status cwb_batch_synchronize(cwb_batch* b);
+void cwb_batch_free(cwb_batch* b);
+
+/*
+ * Fit server -- continuous batching of fit requests on one GPU.  Submitted requests queue on the
+ * host and are admitted in arrival order while the sum of the admitted fits' estimated device
+ * footprints stays within hbm_budget_bytes (and at most max_active fits run).  Each admitted fit
+ * is created on a stream of its own and advanced in slices of slice_iterations iterations (up to two
+ * slices queued per fit), so the iterations of different fits interleave on the GPU; when a fit has
+ * run cfg.iterations iterations it is retired and its slot and memory go to the next request.
+ *   cwb_server_submit  host buffers X, y, w and the learners follow cwb_create; X, y and w must stay
+ *                      valid until the request completes (val_mask and the learners are copied).
+ *                      Returns the request id.  A request larger than the whole budget: CWB_EINVAL.
+ *   cwb_server_poll    one scheduling round (admit, queue slices, retire); with wait != 0 it repeats
+ *                      until at least one request completes or nothing is left.  Completed ids go to
+ *                      done_ids (cap entries), their number to n_done.
+ *   cwb_server_take    hands over a completed request's model (the caller frees it with cwb_free);
+ *                      a request that failed reports CWB_ESTATE and its message.
+ *   cwb_server_stats   pending, active, admitted, completed, bytes in use, budget (host int64).
+ *   cwb_server_free    frees the server, its running fits and completed fits not taken.
+ * The server is not thread-safe.
+ */
+typedef struct cwb_server cwb_server;
+typedef struct {
+    int32_t device;
+    uint64_t hbm_budget_bytes;
+    int32_t max_active;          /* <= 0: 64 */
+    int32_t slice_iterations;    /* <= 0: 32 */
+} cwb_server_config;
+cwb_status cwb_server_create(const cwb_server_config* cfg, cwb_server** out);
+cwb_status cwb_server_submit(cwb_server* s, const cwb_config* cfg, const void* X, int32_t x_dtype, int64_t n,
+                             int32_t p, const void* y, const double* w, const cwb_learner* bl, int32_t K, int64_t* id);
+cwb_status cwb_server_poll(cwb_server* s, int32_t wait, int64_t* done_ids, int32_t cap, int32_t* n_done);
+cwb_status cwb_server_take(cwb_server* s, int64_t id, cwb_model** out);
+cwb_status cwb_server_stats(const cwb_server* s, int64_t* values, int32_t cap);
+void cwb_server_free(cwb_server* s);
+
 /* cwb_synchronize -- wait for the model's queued work; reports device-side errors. */
 cwb_status cwb_synchronize(cwb_model* m);
 

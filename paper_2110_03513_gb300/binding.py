@@ -43,6 +43,11 @@ class cwb_config(C.Structure):
                 ("stream", C.c_void_p), ("device", C.c_int32)]
 
 
+class cwb_server_config(C.Structure):
+    _fields_ = [("device", C.c_int32), ("hbm_budget_bytes", C.c_uint64), ("max_active", C.c_int32),
+                ("slice_iterations", C.c_int32)]
+
+
 class cwb_learner_info(C.Structure):
     _fields_ = [("d", C.c_int32), ("nstar", C.c_int32), ("binning", C.c_int32), ("reserved", C.c_int32),
                 ("xmin", C.c_double), ("xmax", C.c_double), ("lam", C.c_double), ("lam_full", C.c_double)]
@@ -69,6 +74,18 @@ _SIGS = {
     "cwb_synchronize": (C.c_int, [C.c_void_p]),
     "cwb_profile": (C.c_int, [C.c_void_p, C.c_int32]),
     "cwb_get_profile": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
+    "cwb_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p]),
+    "cwb_batch_create": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_void_p)]),
+    "cwb_batch_fit": (C.c_int, [C.c_void_p, C.c_int32]),
+    "cwb_batch_synchronize": (C.c_int, [C.c_void_p]),
+    "cwb_batch_free": (None, [C.c_void_p]),
+    "cwb_server_create": (C.c_int, [C.POINTER(cwb_server_config), C.POINTER(C.c_void_p)]),
+    "cwb_server_submit": (C.c_int, [C.c_void_p, C.POINTER(cwb_config), C.c_void_p, C.c_int32, C.c_int64, C.c_int32,
+                                    C.c_void_p, C.c_void_p, C.POINTER(cwb_learner), C.c_int32, C.c_void_p]),
+    "cwb_server_poll": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p]),
+    "cwb_server_take": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_void_p)]),
+    "cwb_server_stats": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
+    "cwb_server_free": (None, [C.c_void_p]),
     "cwb_last_error": (C.c_char_p, []),
     "cwb_free": (None, [C.c_void_p]),
 }
@@ -260,8 +277,21 @@ class Model:
         self.handle = cwb_create(cfg, X, _dtype_code(X), n, p, y, w, self.learners, 1 if dev else 0)
         self._keep = None
 
+    @classmethod
+    def _adopt(cls, handle, n: int, p: int, learners):
+        """Wrap a model handle created elsewhere (a server's finished request); takes ownership."""
+        m = cls.__new__(cls)
+        m.handle, m.n, m.p, m.learners, m._keep = handle, n, p, list(learners), None
+        return m
+
     def __del__(self):
         self.free()
+
+    def autotune(self, objective: int = 0, trials: int = 5) -> float:
+        """Pick the scatter's grid and cluster size by timing candidates; returns us per scatter."""
+        t = C.c_double(0.0)
+        _check(load_library().cwb_autotune(self.handle, objective, trials, C.byref(t)), "cwb_autotune")
+        return t.value
 
     def free(self):
         h = getattr(self, "handle", None)
@@ -382,3 +412,92 @@ class Model:
 
     def force_selection(self, ks):
         cwb_force_selection(self.handle, np.ascontiguousarray(ks, dtype=np.int32))
+
+
+class Batch:
+    """Models advanced together: each batch step is one CUDA graph launch over all of them."""
+
+    def __init__(self, models, iters_per_launch: int = 32):
+        self.models = list(models)
+        arr = (C.c_void_p * len(self.models))(*[m.handle for m in self.models])
+        out = C.c_void_p()
+        _check(load_library().cwb_batch_create(arr, len(self.models), iters_per_launch, C.byref(out)),
+               "cwb_batch_create")
+        self.handle = out
+
+    def fit(self, iterations: int):
+        _check(load_library().cwb_batch_fit(self.handle, iterations), "cwb_batch_fit")
+        return self
+
+    def synchronize(self):
+        _check(load_library().cwb_batch_synchronize(self.handle), "cwb_batch_synchronize")
+
+    def free(self):
+        h = getattr(self, "handle", None)
+        if h:
+            load_library().cwb_batch_free(h)
+            self.handle = None
+
+    def __del__(self):
+        self.free()
+
+
+SERVER_STATS = ("pending", "active", "admitted", "completed", "bytes_in_use", "budget")
+
+
+class Server:
+    """Continuous-batching fit server on one GPU (admission by device footprint)."""
+
+    def __init__(self, hbm_budget_bytes: int, device: int = 0, max_active: int = 64, slice_iterations: int = 32):
+        cfg = cwb_server_config(device=device, hbm_budget_bytes=hbm_budget_bytes, max_active=max_active,
+                                slice_iterations=slice_iterations)
+        out = C.c_void_p()
+        _check(load_library().cwb_server_create(C.byref(cfg), C.byref(out)), "cwb_server_create")
+        self.handle = out
+        self._requests = {}
+
+    def submit(self, X, y, learners, *, loss=LOSS_L2, opt=OPT_CWB, nu=0.1, gamma=0.0, iterations=100, patience=5,
+               val_mask=None, w=None) -> int:
+        X = np.ascontiguousarray(X)
+        if X.ndim == 1:
+            X = X.reshape(1, -1)
+        y = np.ascontiguousarray(y, dtype=X.dtype)
+        w = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
+        vm = None if val_mask is None else np.ascontiguousarray(val_mask, dtype=np.uint8)
+        p, n = int(X.shape[0]), int(X.shape[1])
+        cfg = cwb_config(loss=loss, opt=opt, nu=nu, gamma=gamma, iterations=iterations, patience=patience,
+                         val_mask=None if vm is None else _ptr(vm).value, stream=None, device=0)
+        arr = (cwb_learner * len(learners))(*learners)
+        rid = C.c_int64(0)
+        _check(load_library().cwb_server_submit(self.handle, C.byref(cfg), _ptr(X), _dtype_code(X), n, p, _ptr(y),
+                                                _ptr(w), arr, len(learners), C.byref(rid)), "cwb_server_submit")
+        self._requests[rid.value] = (X, y, w, n, p, list(learners))     # buffers stay alive until done
+        return rid.value
+
+    def poll(self, wait: bool = False, cap: int = 1024) -> list:
+        ids = np.zeros(cap, dtype=np.int64)
+        got = C.c_int32(0)
+        _check(load_library().cwb_server_poll(self.handle, 1 if wait else 0, _ptr(ids), cap, C.byref(got)),
+               "cwb_server_poll")
+        return [int(i) for i in ids[: got.value]]
+
+    def take(self, rid: int) -> "Model":
+        out = C.c_void_p()
+        st = load_library().cwb_server_take(self.handle, rid, C.byref(out))
+        X, y, w, n, p, learners = self._requests.pop(rid, (None, None, None, 0, 0, []))
+        _check(st, "cwb_server_take")
+        return Model._adopt(out, n, p, learners)
+
+    def stats(self) -> dict:
+        v = np.zeros(len(SERVER_STATS), dtype=np.int64)
+        _check(load_library().cwb_server_stats(self.handle, _ptr(v), v.size), "cwb_server_stats")
+        return {k: int(x) for k, x in zip(SERVER_STATS, v)}
+
+    def free(self):
+        h = getattr(self, "handle", None)
+        if h:
+            load_library().cwb_server_free(h)
+            self.handle = None
+
+    def __del__(self):
+        self.free()

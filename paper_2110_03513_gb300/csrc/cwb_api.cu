@@ -259,8 +259,7 @@ cwb_status create_impl(const cwb_config* cfg, const void* X, int32_t x_dtype, in
         std::vector<int32_t> feat(K);
         for (int k = 0; k < K; ++k) feat[k] = bl[k].feature;
         int32_t* l_feat = nullptr;
-        st = dev_alloc((void**)&m->part, sizeof(float) * std::max<size_t>(m->plan.part_floats, 1), m->stream);
-        if (st == CWB_OK) st = dev_alloc((void**)&m->theta_it, sizeof(double) * 2 * K * D, m->stream);
+        st = dev_alloc((void**)&m->theta_it, sizeof(double) * 2 * K * D, m->stream);
         if (st == CWB_OK) st = dev_alloc((void**)&m->q_it, sizeof(double) * 2 * K, m->stream);
         if (st == CWB_OK) st = dev_alloc((void**)&m->v, sizeof(float) * 2 * (size_t)K * S, m->stream);
         if (st == CWB_OK) st = dev_alloc((void**)&m->state, sizeof(DevState), m->stream);
@@ -575,6 +574,16 @@ cwb_status cwb_force_selection(cwb_model* m, const int32_t* k_forced, int32_t co
     if (!m || (count > 0 && !k_forced) || count < 0) { set_error("bad argument"); return CWB_EINVAL; }
     m->forced_host.assign(k_forced, k_forced + count);
     return CWB_OK;
+}
+
+cwb_status cwb_autotune(cwb_model* m, int32_t objective, int32_t trials, double* best_us)
+{
+    set_error("");
+    if (!m) { set_error("model is NULL"); return CWB_EINVAL; }
+    if (objective != 0 && objective != 1) { set_error("objective must be 0 or 1"); return CWB_EINVAL; }
+    DeviceGuard guard(m->device);
+    CWB_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    return autotune_scatter(m, objective, trials, best_us);
 }
 
 cwb_status cwb_profile(cwb_model* m, int32_t enable)

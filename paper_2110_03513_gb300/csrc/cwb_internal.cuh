@@ -181,6 +181,8 @@ struct cwb_model {
     cudaGraph_t prof_graph = nullptr;     // kept alive: its event-record nodes address the exec's nodes
     std::vector<std::pair<int, std::pair<cudaGraphNode_t, cudaGraphNode_t>>> prof_nodes;
     int graph_iters = 0;
+    bool graph_valid_for_batch = false;   // set by a batch capture, cleared when buffers or plans change
+    bool use_pdl = true;                  // launch the iteration kernels with programmatic dependencies
 };
 
 namespace cwb {
@@ -202,6 +204,19 @@ cwb_status cuda_status(cudaError_t e, const char* what);
     } while (0)
 
 cwb_status dev_alloc(void** p, size_t bytes, cudaStream_t s);
+
+// Raises a kernel's dynamic shared-memory cap to the most the device allows next to the kernel's
+// static shared memory.  The cap is per kernel and process-wide, while models need different amounts.
+inline cudaError_t allow_max_dynamic_smem(const void* func, int device)
+{
+    int optin = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, func);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+}
 void dev_free(void* p);
 
 // Setup (cwb_setup.cu)
@@ -209,10 +224,15 @@ cwb_status setup_model(cwb_model* m, const void* X, int x_dtype, const void* y, 
                        const uint8_t* val_mask, int device_ptrs);
 
 // Iterations (cwb_iter.cu)
-cwb_status plan_scatter(cwb_model* m);
+cwb_status plan_scatter(cwb_model* m, int max_ctas = 0, int cs_req = 0);
+void release_scatter_plan(cwb_model* m);
+cwb_status autotune_scatter(cwb_model* m, int objective, int trials, double* best_us);
 cwb_status scatter_count_pass(cwb_model* m);
 cwb_status ensure_trace(cwb_model* m, int32_t cap);
 cwb_status launch_iterations(cwb_model* m, int32_t iters);
+cwb_status prepare_launch(cwb_model* m, int32_t iters);
+void note_iterations_queued(cwb_model* m, int32_t iters);
+void enqueue_iteration(cwb_model* m, cudaStream_t s, int mask);
 cwb_status launch_final_update(cwb_model* m);
 cwb_status materialize(cwb_model* m);
 void release_graphs(cwb_model* m);

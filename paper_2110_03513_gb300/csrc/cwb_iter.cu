@@ -1352,7 +1352,7 @@ void launch_rows(cwb_model* m, cudaStream_t s)
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = m->use_pdl ? 1 : 0;
     if (m->ind_bytes == 1) cudaLaunchKernelEx(&cfg, k_rows<KIND, uint8_t>, a);
     else cudaLaunchKernelEx(&cfg, k_rows<KIND, uint16_t>, a);
 }
@@ -1374,7 +1374,7 @@ cudaError_t launch_scatter_t(cwb_model* m, cudaStream_t s, const ScatterArgs& a)
     attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 2;
+    cfg.numAttrs = m->use_pdl ? 2 : 1;
     if (P.bin_ranges > 1) return cudaLaunchKernelEx(&cfg, k_scatter<IndT, CMAX, INT_ACC, true, -1>, m->tmap, a);
     if (P.f_lane == 32) return cudaLaunchKernelEx(&cfg, k_scatter<IndT, CMAX, INT_ACC, false, 5>, m->tmap, a);
     if (P.f_lane == 16) return cudaLaunchKernelEx(&cfg, k_scatter<IndT, CMAX, INT_ACC, false, 4>, m->tmap, a);
@@ -1490,34 +1490,9 @@ void launch_solve(cwb_model* m, cudaStream_t s)
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = m->use_pdl ? 1 : 0;
     if (P.int_acc) cudaLaunchKernelEx(&cfg, k_solve<true>, a);
     else cudaLaunchKernelEx(&cfg, k_solve<false>, a);
-}
-
-// One iteration's launches.  With a profiling mask (only while capturing the
-// profiling graph) the kernels of the selected classes are bracketed by external
-// event-record nodes on placeholder events; the placeholders are replaced by fresh
-// events before every launch of that graph.
-void enqueue_iteration(cwb_model* m, cudaStream_t s, int mask)
-{
-    auto mark = [&](int cls, int edge) {
-        if (mask & (1 << cls)) cudaEventRecordWithFlags(m->prof_ph[2 * cls + edge], s, cudaEventRecordExternal);
-    };
-    mark(0, 0);
-    if (m->hybrid) {
-        launch_rows<kRowsUpdate>(m, s);
-        launch_rows<kRowsResid>(m, s);
-    } else {
-        launch_rows<kRowsFused>(m, s);
-    }
-    mark(0, 1);
-    mark(1, 0);
-    launch_scatter(m, s);
-    mark(1, 1);
-    mark(2, 0);
-    launch_solve(m, s);
-    mark(2, 1);
 }
 
 template <typename IndT, int CMAX>
@@ -1531,7 +1506,7 @@ cwb_status prepare_scatter_kernel(cwb_model* m, int cs, int* active_clusters)
         (const void*)k_scatter<IndT, CMAX, true, false, 4>,  (const void*)k_scatter<IndT, CMAX, false, false, 4>,
         (const void*)k_scatter<IndT, CMAX, true, false, -1>, (const void*)k_scatter<IndT, CMAX, false, false, -1>};
     for (const void* kf : kernels) {
-        CWB_CUDA_TRY(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem));
+        CWB_CUDA_TRY(allow_max_dynamic_smem(kf, m->device));
         if (cs > 8) CWB_CUDA_TRY(cudaFuncSetAttribute(kf, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     }
     cudaLaunchConfig_t cfg = {};
@@ -1585,7 +1560,52 @@ EncodeTiledFn encode_tiled_fn()
 
 }  // namespace
 
-cwb_status plan_scatter(cwb_model* m)
+// One iteration's launches.  With a profiling mask (only while capturing the
+// profiling graph) the kernels of the selected classes are bracketed by external
+// event-record nodes on placeholder events; the placeholders are replaced by fresh
+// events before every launch of that graph.
+void enqueue_iteration(cwb_model* m, cudaStream_t s, int mask)
+{
+    auto mark = [&](int cls, int edge) {
+        if (mask & (1 << cls)) cudaEventRecordWithFlags(m->prof_ph[2 * cls + edge], s, cudaEventRecordExternal);
+    };
+    mark(0, 0);
+    if (m->hybrid) {
+        launch_rows<kRowsUpdate>(m, s);
+        launch_rows<kRowsResid>(m, s);
+    } else {
+        launch_rows<kRowsFused>(m, s);
+    }
+    mark(0, 1);
+    mark(1, 0);
+    launch_scatter(m, s);
+    mark(1, 1);
+    mark(2, 0);
+    launch_solve(m, s);
+    mark(2, 1);
+}
+
+
+// Frees the buffers a scatter plan owns (cluster tables, partial histograms) and the graphs
+// that captured them.
+void release_scatter_plan(cwb_model* m)
+{
+    if (m->stream) cudaStreamSynchronize(m->stream);
+    dev_free(m->cluster_slot);
+    dev_free(m->slot_c0);
+    dev_free(m->part);
+    m->cluster_slot = nullptr;
+    m->slot_c0 = nullptr;
+    m->part = nullptr;
+    release_graphs(m);
+}
+
+// Scatter decomposition.  max_ctas > 0 caps the grid (the autotuner's knob); 0 sizes it by the
+// work: every resident CTA for large inputs, about kTilesPerCta tile-slots per CTA for small ones,
+// so that small fits leave SMs to others.  cs_req > 0 forces the cluster size when it can be resident.
+constexpr int kTilesPerCta = 8;
+
+cwb_status plan_scatter(cwb_model* m, int max_ctas, int cs_req)
 {
     int optin = 0, sms = num_sms(m->device);
     CWB_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, m->device));
@@ -1655,8 +1675,10 @@ cwb_status plan_scatter(cwb_model* m)
             best_cs = cs;
         }
     }
-    if (const char* env = std::getenv("CWB_CLUSTER_SIZE")) {
-        const int want = std::atoi(env);
+    int want = cs_req;
+    if (want <= 0)
+        if (const char* env = std::getenv("CWB_CLUSTER_SIZE")) want = std::atoi(env);
+    if (want > 0) {
         if (want == 1 || want == 2 || want == 4 || want == 8 || want == 16) {
             int act = 0;
             CWB_TRY(active_clusters_for(m, want, &act));
@@ -1672,7 +1694,15 @@ cwb_status plan_scatter(cwb_model* m)
     }
     P.cs = best_cs;
     // clusters spread evenly over the slots (groups hold balanced numbers of binnings)
-    int total = std::max(best_used / best_cs, P.slots);
+    int ctas = best_used;
+    {
+        const int64_t tiles = (m->n + kStageRows - 1) / kStageRows;
+        const int64_t by_work = (tiles * P.slots + kTilesPerCta - 1) / kTilesPerCta;
+        if (max_ctas > 0) ctas = std::min(ctas, max_ctas);
+        else ctas = (int)std::min<int64_t>(ctas, by_work);
+        ctas = std::max(ctas, P.slots * best_cs);
+    }
+    int total = std::max(ctas / best_cs, P.slots);
     std::vector<int> per(P.slots, total / P.slots);
     for (int sl = 0; sl < total % P.slots; ++sl) per[sl] += 1;
     // clusters are dealt to the slots in turn, so neighbouring CTAs stream the same rows of
@@ -1712,12 +1742,14 @@ cwb_status plan_scatter(cwb_model* m)
             set_error("solve kernel: basis dimension too large for shared memory");
             return CWB_EINVAL;
         }
-        CWB_CUDA_TRY(cudaFuncSetAttribute(k_solve<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, need));
-        CWB_CUDA_TRY(cudaFuncSetAttribute(k_solve<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, need));
+        CWB_CUDA_TRY(allow_max_dynamic_smem((const void*)k_solve<true>, m->device));
+        CWB_CUDA_TRY(allow_max_dynamic_smem((const void*)k_solve<false>, m->device));
     }
     m->plan = P;
+    release_scatter_plan(m);
     CWB_TRY(dev_alloc((void**)&m->cluster_slot, sizeof(int32_t) * cl_slot.size(), m->stream));
     CWB_TRY(dev_alloc((void**)&m->slot_c0, sizeof(int32_t) * slot_c0.size(), m->stream));
+    CWB_TRY(dev_alloc((void**)&m->part, sizeof(float) * std::max<size_t>(P.part_floats, 1), m->stream));
     CWB_CUDA_TRY(cudaMemcpyAsync(m->cluster_slot, cl_slot.data(), sizeof(int32_t) * cl_slot.size(),
                                  cudaMemcpyHostToDevice, m->stream));
     CWB_CUDA_TRY(cudaMemcpyAsync(m->slot_c0, slot_c0.data(), sizeof(int32_t) * slot_c0.size(), cudaMemcpyHostToDevice,
@@ -1754,6 +1786,7 @@ cwb_status scatter_count_pass(cwb_model* m)
 {
     const ScatterPlan& P = m->plan;
     const int passes = m->hybrid ? 2 : 1;
+    CWB_CUDA_TRY(cudaMemsetAsync(&m->state->cnt_max[0], 0, sizeof(m->state->cnt_max), m->stream));
     for (int idx = 0; idx < passes; ++idx) {
         ScatterArgs a = scatter_args(m);
         a.count_rows = idx == 1 ? m->n_tr : m->n;
@@ -1775,6 +1808,63 @@ cwb_status scatter_count_pass(cwb_model* m)
     const int worst = std::max(st.cnt_log2[0], passes > 1 ? st.cnt_log2[1] : 0);
     m->plan.int_acc = worst <= 13;
     return CWB_OK;
+}
+
+// Autotuner of the scatter decomposition: times `trials` scatter launches for each candidate
+// grid size x cluster size on the model's own data and keeps the best.  objective 0 minimises the
+// scatter's time (one fit on the GPU); 1 minimises its SM-time (CTAs x time), for fits that share
+// the GPU.  The scatter alone changes no model state (its partial histograms are rewritten by the
+// next iteration before they are read).
+cwb_status autotune_scatter(cwb_model* m, int objective, int trials, double* best_us)
+{
+    const int sms = num_sms(m->device);
+    trials = std::max(trials, 1);
+    const int64_t tiles = (m->n + kStageRows - 1) / kStageRows;
+    std::vector<std::pair<int, int>> cand;
+    for (int cs : {2, 1})
+        for (int ctas : {0, sms, sms / 2, sms / 4, sms / 8}) cand.push_back({ctas, cs});
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CWB_CUDA_TRY(cudaEventCreate(&e0));
+    CWB_CUDA_TRY(cudaEventCreate(&e1));
+    double best = INFINITY, best_t = 0.0;
+    std::pair<int, int> pick = {0, 0};
+    cwb_status st = CWB_OK;
+    std::vector<std::pair<int, int>> seen;
+    for (auto c : cand) {
+        if (c.first > 0 && (int64_t)c.first > tiles * 4 * m->plan.slots) continue;   // mostly idle CTAs
+        st = plan_scatter(m, c.first, c.second);
+        if (st != CWB_OK) break;
+        const std::pair<int, int> got = {m->plan.clusters, m->plan.cs};
+        if (std::find(seen.begin(), seen.end(), got) != seen.end()) continue;
+        seen.push_back(got);
+        st = scatter_count_pass(m);
+        if (st != CWB_OK) break;
+        launch_scatter(m, m->stream);                      // warm-up
+        cudaEventRecord(e0, m->stream);
+        for (int t = 0; t < trials; ++t) launch_scatter(m, m->stream);
+        cudaEventRecord(e1, m->stream);
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) {
+            st = cuda_status(e, "autotune");
+            break;
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double t_us = 1e3 * ms / trials;
+        const double cost = objective == 1 ? t_us * m->plan.clusters * m->plan.cs / sms : t_us;
+        if (cost < best) {
+            best = cost;
+            best_t = t_us;
+            pick = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CWB_TRY(st);
+    CWB_TRY(plan_scatter(m, pick.first, pick.second));
+    CWB_TRY(scatter_count_pass(m));
+    if (best_us) *best_us = best_t;
+    return read_device_error(m);
 }
 
 cwb_status ensure_trace(cwb_model* m, int32_t need)
@@ -1817,6 +1907,7 @@ cwb_status ensure_trace(cwb_model* m, int32_t need)
 
 void release_graphs(cwb_model* m)
 {
+    m->graph_valid_for_batch = false;    // batches that captured this model capture it again
     if (m->graph_exec) cudaGraphExecDestroy(m->graph_exec);
     if (m->graph1_exec) cudaGraphExecDestroy(m->graph1_exec);
     if (m->prof_exec) cudaGraphExecDestroy(m->prof_exec);
@@ -1879,9 +1970,9 @@ static cudaEvent_t take_event(cwb_model* m)
     return e;
 }
 
-cwb_status launch_iterations(cwb_model* m, int32_t iters)
+// Trace capacity for `iters` more iterations and any pending forced selections on the device.
+cwb_status prepare_launch(cwb_model* m, int32_t iters)
 {
-    if (iters <= 0) return CWB_OK;
     CWB_TRY(ensure_trace(m, m->done + iters));
     if (!m->forced_host.empty()) {
         int32_t cnt = (int32_t)std::min<size_t>(m->forced_host.size(), (size_t)(m->trace_cap - m->done));
@@ -1890,6 +1981,20 @@ cwb_status launch_iterations(cwb_model* m, int32_t iters)
         CWB_CUDA_TRY(cudaStreamSynchronize(m->stream));
         m->forced_host.clear();
     }
+    return CWB_OK;
+}
+
+void note_iterations_queued(cwb_model* m, int32_t iters)
+{
+    m->done += iters;
+    m->coef_valid_at = -1;
+    m->update_pending = true;
+}
+
+cwb_status launch_iterations(cwb_model* m, int32_t iters)
+{
+    if (iters <= 0) return CWB_OK;
+    CWB_TRY(prepare_launch(m, iters));
     if (m->prof_on) {
         if (!m->prof_exec) CWB_TRY(capture_graph(m, 1, m->prof_mask, &m->prof_exec));
         for (int32_t i = 0; i < iters; ++i) {
@@ -1914,9 +2019,7 @@ cwb_status launch_iterations(cwb_model* m, int32_t iters)
         for (int32_t i = 0; i < left; ++i) CWB_CUDA_TRY(cudaGraphLaunch(m->graph1_exec, m->stream));
     }
     CWB_CUDA_TRY(cudaGetLastError());
-    m->done += iters;
-    m->coef_valid_at = -1;
-    m->update_pending = true;
+    note_iterations_queued(m, iters);
     return CWB_OK;
 }
 

@@ -1071,7 +1071,7 @@ cwb_status setup_model(cwb_model* m, const void* X_in, int x_dtype, const void* 
     {
         LamArgs a{K, D, m->l_type, m->l_d, ldiff_d, ldf_d, llam_d, m->G, m->P, m->lambda, lstat, phases};
         size_t smem = sizeof(double) * (4 * dd + D);
-        CWB_CUDA_TRY(cudaFuncSetAttribute(k_lambda, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        CWB_CUDA_TRY(allow_max_dynamic_smem((const void*)k_lambda, m->device));
         k_lambda<<<dim3(K, phases), kLamThreads, smem, s>>>(a);
         if (phases == 1) {           // one cache serves both phases
             CWB_CUDA_TRY(cudaMemcpyAsync(m->P + (size_t)K * dd, m->P, sizeof(double) * K * dd, cudaMemcpyDeviceToDevice, s));

@@ -279,3 +279,12 @@ def test_full_size_binned_l2_first_iterations(cwb):
     data = S.sim_binned_l2(seed=1)
     specs = [dict(feature=j, n_bins=-1) for j in range(50)]
     run_pair(cwb, data.X, data.y, specs, M=12, check_predict=False)
+
+
+def test_full_size_hcwb_binomial_first_iterations(cwb):
+    """n = 2,000,000, p = 200 (U[0,1] and N(0,1)), binomial, ACWB with the hybrid switch, 20 % validation
+    rows, n* = 1414 (uint16): the first 6 iterations (two fits each) against the oracle."""
+    data = S.sim_binomial_hybrid(seed=2)
+    specs = [dict(feature=j, n_bins=1414) for j in range(200)]
+    run_pair(cwb, data.X, data.y, specs, M=6, loss=1, opt=2, nu=0.1, gamma=0.001, patience=5,
+             val_mask=data.val_mask, check_predict=False)
