@@ -81,6 +81,11 @@ def parse_args():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--skip-cpu-baseline", action="store_true", help="do not time the CPU oracle")
     ap.add_argument("--skip-e2e", action="store_true", help="do not run the end-to-end fit")
+    ap.add_argument("--skip-batched", action="store_true", help="do not run the batched-fits measurement")
+    ap.add_argument("--skip-served", action="store_true", help="do not run the served-requests measurement")
+    ap.add_argument("--batched-fits", type=int, default=512,
+                    help="fits in the batched measurement (the first of the 512 seeded specs)")
+    ap.add_argument("--served-requests", type=int, default=96, help="requests in the served measurement")
     ap.add_argument("--workload", choices=["binned_l2", "hcwb_binomial"], default="binned_l2",
                     help="binned_l2: the headline line (n=1M, p=50); hcwb_binomial: ACWB with the hybrid "
                          "switch, binomial loss, n=2M, p=200, n*=1414 (a separate line)")
@@ -339,6 +344,12 @@ def run_ours(args):
 
     if not args.skip_e2e:
         line["e2e"] = run_e2e(cwb, data, stream, dev, local)
+    if rank == 0 and world == 1:
+        del data
+        if not args.skip_batched:
+            line["batched"] = run_batched(cwb, args)
+        if not args.skip_served:
+            line["served"] = run_served(cwb, args)
     if rank == 0 and world == 1 and not args.skip_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_full(data)
     model.free()
@@ -346,6 +357,147 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def _percentile(xs, q):
+    import numpy as np
+    return float(np.percentile(np.asarray(xs, dtype=np.float64), q)) if xs else None
+
+
+def run_batched(cwb, args):
+    """Uneven fits shaped like CV folds x a df/nu grid: n log-uniform 5k-500k, p uniform 5-100,
+    n* = floor(sqrt(n)), L2, M = 1000.  Arm 1 (sequential): each fit alone, one after another,
+    through cwb_fit (its own graphs).  Arm 2 (batched): every model autotuned for SM-time, then all
+    advanced together by cwb_batch_fit (one graph launch per 32 iterations of all fits).  Setup
+    (data, create, autotune) is not timed; both arms start from identical models."""
+    import numpy as np
+    import torch
+    import synthetic_inputs as S
+    M = 1000
+    specs = S.batched_fit_specs(count=512)[: max(1, args.batched_fits)]
+    seq_models, bat_models = [], []
+    for sp in specs:
+        d = S.request_dataset(sp)
+        lrn = [cwb.learner(j, n_bins=-1, df=sp["df"]) for j in range(sp["p"])]
+        seq_models.append(cwb.Model(d.X, d.y, lrn, nu=sp["nu"], iterations=M, device=0))
+        bat_models.append(cwb.Model(d.X, d.y, lrn, nu=sp["nu"], iterations=M, device=0))
+    torch.cuda.synchronize()
+    # sequential arm
+    t_seq, coef_seq = 0.0, []
+    for m in seq_models:
+        m.synchronize()
+        t0 = time.perf_counter()
+        m.fit(M)
+        m.synchronize()
+        t_seq += time.perf_counter() - t0
+        coef_seq.append(m.all_coefficients(0, dmax=24))
+        m.free()
+    # batched arm
+    t0 = time.perf_counter()
+    for m in bat_models:
+        m.autotune(objective=1, trials=2)
+    t_tune = time.perf_counter() - t0
+    batch = cwb.Batch(bat_models, iters_per_launch=32)
+    batch.synchronize()
+    t0 = time.perf_counter()
+    batch.fit(M)
+    batch.synchronize()
+    t_bat = time.perf_counter() - t0
+    worst = 0.0
+    for m, ref in zip(bat_models, coef_seq):
+        th = m.all_coefficients(0, dmax=24)
+        den = float(np.abs(ref).max()) or 1.0
+        worst = max(worst, float(np.abs(th - ref).max()) / den)
+    batch.free()
+    for m in bat_models:
+        m.free()
+    nf = len(specs)
+    return {"fits": nf, "iterations": M, "fits_per_s": nf / t_bat, "sequential_fits_per_s": nf / t_seq,
+            "speedup_vs_sequential": t_seq / t_bat, "batched_s": t_bat, "sequential_s": t_seq,
+            "autotune_s": t_tune, "max_rel_coef_diff_vs_sequential": worst,
+            "what": "n log-uniform 5k-500k, p uniform 5-100, n*=floor(sqrt n), L2, df in {4,5,6,8}, nu in "
+                    "{0.05,0.1,0.2,0.3}, M=1000; wall clock of fit + synchronize, setup excluded"}
+
+
+def run_served(cwb, args):
+    """Poisson stream of fit requests (variant CWB/ACWB/HCWB, loss L2/binomial) through the fit server.
+    The configured stream (n up to 5M, p up to 500, M up to 5000) needs an estimated 10+ minutes of GPU
+    work per 1000 requests, so this measurement replays the first R requests of the stream with n, p
+    and M scaled by 1/10 (n 1k-500k, p 1-50, M 50-500).  Arm 1: the requests one after another
+    (sequential capacity).  Arm 2: the server at offered loads 0.8x and 1.0x of that capacity and a
+    burst (all requests at t = 0); latency = completion - arrival, including creation (setup)."""
+    import numpy as np
+    import torch
+    import synthetic_inputs as S
+    R = max(1, args.served_requests)
+    stream = S.served_request_stream(count=R, seed=4)
+    reqs = []
+    for r in stream:
+        sp = dict(r, n=max(1000, r["n"] // 10), p=max(1, r["p"] // 10), iterations=max(50, r["iterations"] // 10))
+        d = S.request_dataset(sp)
+        reqs.append((sp, d))
+    opts = {0: cwb.OPT_CWB, 1: cwb.OPT_ACWB, 2: cwb.OPT_HCWB}
+
+    def kwargs(sp, d):
+        return dict(loss=cwb.LOSS_BINOMIAL if sp["loss"] == 1 else cwb.LOSS_L2, opt=opts[sp["variant"]], nu=0.1,
+                    gamma=0.001, iterations=sp["iterations"], patience=5, val_mask=d.val_mask)
+
+    def learners(sp):
+        return [cwb.learner(j, n_bins=-1, df=5.0) for j in range(sp["p"])]
+
+    # sequential arm: create + fit + read back, one request at a time
+    service, coef_alone = [], []
+    for sp, d in reqs:
+        t0 = time.perf_counter()
+        m = cwb.Model(d.X, d.y, learners(sp), device=0, **kwargs(sp, d))
+        m.fit(sp["iterations"])
+        coef_alone.append(m.all_coefficients(0, dmax=24))
+        service.append(time.perf_counter() - t0)
+        m.free()
+    cap = R / sum(service)
+
+    def replay(load):
+        srv = cwb.Server(hbm_budget_bytes=64 << 30, device=0, max_active=32, slice_iterations=32)
+        gaps = np.array([r["arrival_s"] for r in stream])
+        # rescale the Poisson arrivals to the offered load (mean rate = load x sequential capacity)
+        if load is None:
+            arrival = np.zeros(R)
+        else:
+            mean_gap = float(np.mean(np.diff(np.concatenate([[0.0], gaps])))) or 1.0
+            arrival = gaps / mean_gap / (load * cap)
+        t0 = time.perf_counter()
+        submitted, done_at, ids = 0, {}, {}
+        while len(done_at) < R:
+            now = time.perf_counter() - t0
+            while submitted < R and arrival[submitted] <= now:
+                sp, d = reqs[submitted]
+                ids[srv.submit(d.X, d.y, learners(sp), **kwargs(sp, d))] = submitted
+                submitted += 1
+            for rid in srv.poll(wait=False):
+                done_at[rid] = time.perf_counter() - t0
+            if submitted == R and len(done_at) < R:
+                for rid in srv.poll(wait=True):
+                    done_at[rid] = time.perf_counter() - t0
+        makespan = max(done_at.values())
+        lat = [done_at[rid] - arrival[i] for rid, i in ids.items()]
+        worst = 0.0
+        for rid, i in ids.items():
+            m = srv.take(rid)
+            th = m.all_coefficients(0, dmax=24)
+            ref = coef_alone[i]
+            worst = max(worst, float(np.abs(th - ref).max()) / (float(np.abs(ref).max()) or 1.0))
+            m.free()
+        srv.free()
+        return {"offered_load": load if load is not None else "burst", "fits_per_s": R / makespan,
+                "p50_latency_s": _percentile(lat, 50), "p99_latency_s": _percentile(lat, 99),
+                "max_rel_coef_diff_vs_alone": worst}
+
+    runs = [replay(0.8), replay(1.0), replay(None)]
+    return {"requests": R, "sequential_fits_per_s": cap, "sequential_p50_service_s": _percentile(service, 50),
+            "sequential_p99_service_s": _percentile(service, 99), "runs": runs,
+            "hbm_budget_bytes": 64 << 30,
+            "what": "first R requests of the seeded Poisson stream, n, p, M scaled by 1/10; latency includes "
+                    "creation; admission by estimated device footprint"}
 
 
 def run_e2e(cwb, data, stream, dev, local):

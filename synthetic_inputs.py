@@ -27,6 +27,7 @@ __all__ = [
     "sim_binomial_hybrid",
     "batched_fit_specs",
     "served_request_stream",
+    "request_dataset",
     "paper_style_simulation",
 ]
 
@@ -163,6 +164,27 @@ def served_request_stream(count: int = 10_000, seed: int = 4, rate_per_s: float 
                         iterations=int(rng.integers(m_lo, m_hi + 1)),
                         seed=int(rng.integers(0, 2**31 - 1))))
     return out
+
+
+def request_dataset(spec: dict, dtype=np.float32) -> Dataset:
+    """Data of one fit request (served or batched workloads): ``spec`` carries n, p and seed, and
+    optionally loss (0 L2, 1 binomial) and variant (2 = hybrid, which draws a 20% validation mask).
+
+    Features are U[0, 1]; min(p, 10) of them carry the additive effects of ``additive_regression``.
+    For the binomial loss the signal is centred, scaled to unit standard deviation and y is drawn as
+    Bernoulli(sigmoid(signal)).
+    """
+    n, p, seed = int(spec["n"]), int(spec["p"]), int(spec["seed"])
+    d = additive_regression(n, p, min(p, 10), seed, dtype=np.float64)
+    rng = np.random.Generator(np.random.PCG64(seed ^ 0x5EED))
+    y = d.y
+    if int(spec.get("loss", 0)) == 1:
+        eta = d.eta - d.eta.mean()
+        eta /= max(float(eta.std()), 1e-12)
+        y = (rng.random(n) < 1.0 / (1.0 + np.exp(-eta))).astype(np.float64)
+    val = (rng.random(n) < 0.2).astype(np.uint8) if int(spec.get("variant", 0)) == 2 else None
+    return Dataset(X=d.X.astype(dtype), y=y.astype(dtype), val_mask=val, eta=d.eta,
+                   description=f"request n={n} p={p} seed={seed}")
 
 
 def paper_style_simulation(n: int, p: int, p_noise: int, snr: float, seed: int) -> Dataset:

@@ -133,3 +133,30 @@ def test_server_rejects_requests_above_the_budget(cwb):
     with pytest.raises(cwb.CwbError):
         srv.submit(data.X, data.y, [cwb.learner(j) for j in range(10)], iterations=10)
     srv.free()
+
+
+def test_batched_fit_specs_match_the_oracle(cwb):
+    """Fits drawn from the batched workload's seeded specs (the smaller ones), advanced as one batch with
+    autotuned plans, each against the FP64 oracle."""
+    specs = [s for s in S.batched_fit_specs(count=512) if s["n"] <= 20_000][:4]
+    assert len(specs) == 4
+    M = 150
+    models, refs = [], []
+    for sp in specs:
+        d = S.request_dataset(sp)
+        lspecs = [dict(feature=j, n_bins=-1, df=sp["df"]) for j in range(sp["p"])]
+        m = cwb.Model(d.X, d.y, _learners(cwb, lspecs), nu=sp["nu"], iterations=M, device=0)
+        m.autotune(objective=1, trials=2)
+        models.append(m)
+        refs.append((O.fit(d.X.astype(np.float64), d.y.astype(np.float64), lspecs, nu=sp["nu"], iterations=M), d))
+    batch = cwb.Batch(models, iters_per_launch=32)
+    batch.fit(M)
+    batch.synchronize()
+    for m, (ref, d) in zip(models, refs):
+        k_sel, _, _ = m.trace()
+        assert check_sequences(k_sel, ref) < 0
+        check_coefficients(m.all_coefficients(0, dmax=ref.dmax), ref.theta_f)
+        assert rel_err(m.fitted(), ref.f) <= REL_TOL
+    batch.free()
+    for m in models:
+        m.free()
