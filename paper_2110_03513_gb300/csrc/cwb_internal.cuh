@@ -139,6 +139,7 @@ struct cwb_model {
     int32_t* toff = nullptr;              // [K][D] offset of column j in ztab
     float* ztab = nullptr;                // [K][4 S] column-major reduced design
     double *G = nullptr, *P = nullptr, *lambda = nullptr;
+    double* Acrit = nullptr;              // [2][K][D][D] criterion matrix P G P - 2 P
     int32_t *l_bin = nullptr, *l_d = nullptr, *l_nstar = nullptr, *l_type = nullptr;
     double *l_xmin = nullptr, *l_xmax = nullptr;
     int32_t *l_degree = nullptr, *l_nknots = nullptr, *l_feat = nullptr;

@@ -875,7 +875,7 @@ __global__ void k_count_log2(DevState* state, int idx)
 // iteration state.
 
 constexpr int kSolveChunk = 1024;      // bins of u held in shared memory per pass
-constexpr int kSolveBatch = 8;         // partial-histogram rows per thread and batch (per channel)
+constexpr int kSolveBatch = 12;        // partial-histogram rows per thread and batch (per channel)
 
 struct SolveArgs {
     DevState* state;
@@ -893,7 +893,7 @@ struct SolveArgs {
     const int32_t* l_bin;
     const int32_t* l_d;
     const int32_t* l_nstar;
-    const double* G;          // [2][K][D][D]
+    const double* A;          // [2][K][D][D] criterion matrix P G P - 2 P
     const double* P;
     double* theta_it;         // [2][K][D]
     double* q_it;             // [2][K]
@@ -974,8 +974,8 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(SolveArgs a)
     // when it fits, the column-major design
     extern __shared__ __align__(16) double dsm[];
     double* Ps = dsm;
-    double* Gs = Ps + (size_t)D * D;
-    float* u_s = reinterpret_cast<float*>(Gs + (size_t)D * D);                    // [2][kSolveChunk]
+    double* As = Ps + (size_t)D * D;
+    float* u_s = reinterpret_cast<float*>(As + (size_t)D * D);                    // [2][kSolveChunk]
     long long* pb = reinterpret_cast<long long*>(u_s + 2 * kSolveChunk);          // [2][kSolveChunk]
     float4* zb_s = reinterpret_cast<float4*>(pb + 2 * kSolveChunk);              // [nst] when staged
     int* zc_s = reinterpret_cast<int*>(zb_s + (a.stage_v ? S : 0));
@@ -1007,10 +1007,10 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(SolveArgs a)
     const int ph = (mode == kModeACWB) ? 0 : st.phase;    // P and G of the cache this iteration uses
     {
         const double* Pk = a.P + ((int64_t)ph * a.K + k) * D * D;
-        const double* Gk = a.G + ((int64_t)ph * a.K + k) * D * D;
+        const double* Ak = a.A + ((int64_t)ph * a.K + k) * D * D;
         for (int e = tid; e < D * D; e += blockDim.x) {
             cp_async8(Ps + e, Pk + e);
-            cp_async8(Gs + e, Gk + e);
+            cp_async8(As + e, Ak + e);
         }
     }
     const float* zt = a.stage_z ? zt_s : a.ztab + (int64_t)k * kMaxNnz * S;
@@ -1149,38 +1149,31 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(SolveArgs a)
     }
     __syncthreads();
 
-    // ---- theta = P s and the criterion terms (FP64): four lanes per row, partial sums over j = q mod 4
+    // ---- theta = P s and t = A s together (FP64): four lanes per row, partial sums over j = q mod 4;
+    // the criterion Q = theta^T G theta - 2 theta^T s = s^T A s = s . t
     const int rows4 = C * d * 4;
-    for (int base = 0; base < rows4; base += blockDim.x) {
+    for (int base = 0; base < 2 * rows4; base += blockDim.x) {
         const int e = base + tid;
-        const bool valid = e < rows4;
-        const int ch = valid ? e / (4 * d) : 0;
-        const int rem = e - ch * 4 * d;
+        const bool valid = e < 2 * rows4;
+        const int mat = valid && e >= rows4 ? 1 : 0;
+        const int r = e - mat * rows4;
+        const int ch = valid ? r / (4 * d) : 0;
+        const int rem = r - ch * 4 * d;
         const int i = rem >> 2, q = rem & 3;
+        const double* Mx = mat ? As : Ps;
         double p = 0.0;
         if (valid)
-            for (int j = q; j < d; j += 4) p = fma(Ps[i * D + j], s_s[ch][j], p);
+            for (int j = q; j < d; j += 4) p = fma(Mx[i * D + j], s_s[ch][j], p);
         p += __shfl_xor_sync(0xffffffffu, p, 1);
         p += __shfl_xor_sync(0xffffffffu, p, 2);
-        if (valid && q == 0) th_s[ch][i] = p;
-    }
-    __syncthreads();
-    for (int base = 0; base < rows4; base += blockDim.x) {
-        const int e = base + tid;
-        const bool valid = e < rows4;
-        const int ch = valid ? e / (4 * d) : 0;
-        const int rem = e - ch * 4 * d;
-        const int i = rem >> 2, q = rem & 3;
-        double p = 0.0;
-        if (valid)
-            for (int j = q; j < d; j += 4) p = fma(Gs[i * D + j], th_s[ch][j], p);
-        p += __shfl_xor_sync(0xffffffffu, p, 1);
-        p += __shfl_xor_sync(0xffffffffu, p, 2);
-        if (valid && q == 0) term[ch][i] = th_s[ch][i] * (p - 2.0 * s_s[ch][i]);
+        if (valid && q == 0) {
+            if (mat) term[ch][i] = s_s[ch][i] * p;
+            else th_s[ch][i] = p;
+        }
     }
     __syncthreads();
     if (warp < C) {
-        // Q = sum_i term_i: fixed-order tree over the warp
+        // Q = sum_i s_i t_i: fixed-order tree over the warp
         double x = 0.0;
         for (int i = lane; i < d; i += 32) x += term[warp][i];
         for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
@@ -1471,7 +1464,7 @@ void launch_solve(cwb_model* m, cudaStream_t s)
     a.l_bin = m->l_bin;
     a.l_d = m->l_d;
     a.l_nstar = m->l_nstar;
-    a.G = m->G;
+    a.A = m->Acrit;
     a.P = m->P;
     a.theta_it = m->theta_it;
     a.q_it = m->q_it;

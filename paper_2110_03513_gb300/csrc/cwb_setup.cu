@@ -441,6 +441,7 @@ struct LamArgs {
     const double* l_lambda;
     const double* G;        // [2][K][D][D]
     double* P;              // [2][K][D][D]
+    double* A;              // [2][K][D][D] criterion matrix P G P - 2 P
     double* lambda;         // [2][K]
     int32_t* status;        // [2][K]: 0 ok, 1 not positive definite, 2 df unreachable
     int phases;
@@ -657,6 +658,27 @@ __global__ void __launch_bounds__(kLamThreads) k_lambda(LamArgs a)
                     col[i] = t * rinv[i];
                 }
                 for (int i = 0; i < d; ++i) Pout[i * a.D + j] = col[i];
+            }
+            __syncthreads();
+            // criterion matrix Acrit = P G P - 2 P: with theta = P s, theta^T G theta - 2 theta^T s =
+            // s^T Acrit s, so the iteration's criterion needs no second product after theta.
+            // T = G P overwrites the factor (no longer needed); Y holds P column by column.
+            for (int e = tid; e < d * d; e += blockDim.x) {
+                const int i = e / d, j = e % d;
+                double t = 0.0;
+                for (int q = 0; q < d; ++q) t += G[i * d + q] * Y[j * d + q];
+                A[i * d + j] = t;
+            }
+            __syncthreads();
+            double* Aout = a.A + ((int64_t)ph * a.K + k) * a.D * a.D;
+            for (int e = tid; e < a.D * a.D; e += blockDim.x) {
+                const int i = e / a.D, j = e % a.D;
+                double v = 0.0;
+                if (i < d && j < d) {
+                    for (int q = 0; q < d; ++q) v += Y[q * d + i] * A[q * d + j];     // (P T)_ij, P symmetric
+                    v -= 2.0 * Y[j * d + i];
+                }
+                Aout[e] = v;
             }
         }
     }
@@ -1064,17 +1086,20 @@ cwb_status setup_model(cwb_model* m, const void* X_in, int x_dtype, const void* 
     const size_t dd = (size_t)D * D;
     CWB_TRY(dev_alloc((void**)&m->G, sizeof(double) * 2 * K * dd, s));
     CWB_TRY(dev_alloc((void**)&m->P, sizeof(double) * 2 * K * dd, s));
+    CWB_TRY(dev_alloc((void**)&m->Acrit, sizeof(double) * 2 * K * dd, s));
     CWB_TRY(dev_alloc((void**)&m->lambda, sizeof(double) * 2 * K, s));
     int32_t* lstat = nullptr;
     CWB_TRY(tmp.get(&lstat, (size_t)2 * K, s));
     k_gram<<<dim3(K, 2), kThreads, 0, s>>>(S, D, K, m->l_bin, m->l_d, nnz_d, m->zb64, m->zcol, m->crange, cnt, B, m->G);
     {
-        LamArgs a{K, D, m->l_type, m->l_d, ldiff_d, ldf_d, llam_d, m->G, m->P, m->lambda, lstat, phases};
+        LamArgs a{K, D, m->l_type, m->l_d, ldiff_d, ldf_d, llam_d, m->G, m->P, m->Acrit, m->lambda, lstat, phases};
         size_t smem = sizeof(double) * (4 * dd + D);
         CWB_CUDA_TRY(allow_max_dynamic_smem((const void*)k_lambda, m->device));
         k_lambda<<<dim3(K, phases), kLamThreads, smem, s>>>(a);
         if (phases == 1) {           // one cache serves both phases
             CWB_CUDA_TRY(cudaMemcpyAsync(m->P + (size_t)K * dd, m->P, sizeof(double) * K * dd, cudaMemcpyDeviceToDevice, s));
+            CWB_CUDA_TRY(cudaMemcpyAsync(m->Acrit + (size_t)K * dd, m->Acrit, sizeof(double) * K * dd,
+                                         cudaMemcpyDeviceToDevice, s));
             CWB_CUDA_TRY(cudaMemcpyAsync(m->lambda + K, m->lambda, sizeof(double) * K, cudaMemcpyDeviceToDevice, s));
             CWB_CUDA_TRY(cudaMemsetAsync(lstat + K, 0, sizeof(int32_t) * K, s));
         }
