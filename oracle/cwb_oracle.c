@@ -392,14 +392,15 @@ double orc_pseudo_residual(int loss, double y, double f) { return pseudo_residua
 /* ------------------------------------------------------------------------ */
 
 typedef struct {
-    int32_t type;        /* 0: P-spline, 1: linear */
+    int32_t type;        /* 0: P-spline, 1: linear, 2: categorical ridge, 3: categorical binary (App. B.1) */
     int32_t feature;
     int32_t degree;
-    int32_t n_knots;
+    int32_t n_knots;     /* categorical: number of classes c; the feature holds the codes 0..c-1 */
     int32_t diff_order;
     double df;           /* > 0: choose lambda so that df1 = df */
     double lambda;       /* used when df <= 0 */
     int32_t n_bins;      /* 0: exact (unique values), -1: floor(sqrt n), -2: unbinned (dense), >1: explicit */
+    int32_t level;       /* categorical binary: the class the learner indicates, 0 <= level < c */
 } orc_learner;
 
 typedef struct {
@@ -448,6 +449,8 @@ typedef struct {
 
 static int learner_d(const orc_learner* b)
 {
+    if (b->type == 2) return b->n_knots;            /* one coefficient per class */
+    if (b->type == 3) return 1;                     /* one coefficient for one class */
     return b->type == 1 ? 2 : b->n_knots + b->degree + 1;
 }
 
@@ -468,6 +471,31 @@ static int setup_design(const orc_learner* b, const double* x, int64_t n, bl_sta
     s->xmin = xmin; s->xmax = xmax;
     s->ind = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
     if (!s->ind) return ORC_ENOMEM;
+    if (b->type == 2 || b->type == 3) {
+        /* categorical learners: the values are class codes 0..c-1 and each class is one bin, so
+           the lookup k_i is the code itself.  Ridge: the design is the dummy matrix (identity on
+           the bins) and the penalty the identity.  Binary: one column, the indicator of `level`,
+           unpenalised. */
+        const int c = b->n_knots;
+        if (c < 2 || (b->type == 3 && (b->level < 0 || b->level >= c))) return ORC_EINVAL;
+        for (int64_t i = 0; i < n; ++i) {
+            if (!(x[i] >= 0.0 && x[i] < (double)c && x[i] == floor(x[i]))) return ORC_EINVAL;
+            s->ind[i] = (int32_t)x[i];
+        }
+        s->nstar = c;
+        s->Zb = (double*)calloc((size_t)c * d, sizeof(double));
+        s->K = (double*)calloc((size_t)d * d, sizeof(double));
+        if (!s->Zb || !s->K) return ORC_ENOMEM;
+        if (b->type == 2) {
+            for (int j = 0; j < c; ++j) {
+                s->Zb[(int64_t)j * c + j] = 1.0;
+                s->K[(int64_t)j * c + j] = 1.0;
+            }
+        } else {
+            s->Zb[b->level] = 1.0;
+        }
+        return ORC_OK;
+    }
     double* pts;
     int64_t npts;
     if (b->n_bins == -2) {
@@ -516,7 +544,7 @@ static int setup_phase(const orc_learner* b, bl_state* s, int64_t n, const doubl
     if (!s->G[a] || !s->P[a]) return ORC_ENOMEM;
     orc_bin_matmat(s->ind, n, w, rows, s->nstar, s->Zb, d, s->G[a]);
     double lam = 0.0;
-    if (b->type == 0) {
+    if (b->type == 0 || b->type == 2) {             /* penalised learners */
         if (b->df > 0.0) {
             int st = orc_lambda_for_df(s->G[a], s->K, d, b->df, &lam);
             if (st) return st;
@@ -596,7 +624,10 @@ int orc_fit(int64_t n, int32_t p, const double* X /* p x n */, const double* y, 
     }
     int dmax = 0;
     for (int32_t k = 0; k < K; ++k) {
-        if (bl[k].feature < 0 || bl[k].feature >= p) { free(train); return ORC_EINVAL; }
+        if (bl[k].feature < 0 || bl[k].feature >= p || bl[k].type < 0 || bl[k].type > 3) {
+            free(train);
+            return ORC_EINVAL;
+        }
         int d = learner_d(&bl[k]);
         if (d > dmax) dmax = d;
     }
@@ -735,6 +766,15 @@ int orc_predict(int64_t n_new, int32_t p, const double* Xnew /* p x n_new */, in
         int d = learner_d(&bl[k]);
         for (int64_t i = 0; i < n_new; ++i) {
             double x = Xnew[(int64_t)bl[k].feature * n_new + i];
+            if (bl[k].type == 2 || bl[k].type == 3) {
+                /* a valid class code contributes its coefficient, anything else (an unknown
+                   code, a non-integer) nothing */
+                if (x >= 0.0 && x < (double)bl[k].n_knots && x == floor(x)) {
+                    if (bl[k].type == 2) out[i] += theta[(int64_t)k * dmax + (int64_t)x];
+                    else if ((int32_t)x == bl[k].level) out[i] += theta[(int64_t)k * dmax];
+                }
+                continue;
+            }
             if (x < xmin[k]) x = xmin[k];
             if (x > xmax[k]) x = xmax[k];
             if (bl[k].type == 1) orc_linear_basis(&x, 1, row);

@@ -24,7 +24,7 @@ _lib = None
 
 LOSS_L2, LOSS_BINOMIAL = 0, 1
 OPT_CWB, OPT_ACWB, OPT_HCWB = 0, 1, 2
-BL_PSPLINE, BL_LINEAR = 0, 1
+BL_PSPLINE, BL_LINEAR, BL_CATEGORICAL, BL_CATEGORICAL_BINARY = 0, 1, 2, 3
 BINS_EXACT, BINS_SQRT, BINS_DENSE = 0, -1, -2
 
 
@@ -41,7 +41,7 @@ def build(force: bool = False) -> str:
 class Learner(C.Structure):
     _fields_ = [("type", C.c_int32), ("feature", C.c_int32), ("degree", C.c_int32),
                 ("n_knots", C.c_int32), ("diff_order", C.c_int32), ("df", C.c_double),
-                ("lam", C.c_double), ("n_bins", C.c_int32)]
+                ("lam", C.c_double), ("n_bins", C.c_int32), ("level", C.c_int32)]
 
 
 class Config(C.Structure):
@@ -88,7 +88,12 @@ def _check(st, what):
 
 
 def learner_d(spec: dict) -> int:
-    return 2 if spec.get("type", BL_PSPLINE) == BL_LINEAR else spec.get("n_knots", 20) + spec.get("degree", 3) + 1
+    t = spec.get("type", BL_PSPLINE)
+    if t == BL_CATEGORICAL:
+        return spec["n_knots"]
+    if t == BL_CATEGORICAL_BINARY:
+        return 1
+    return 2 if t == BL_LINEAR else spec.get("n_knots", 20) + spec.get("degree", 3) + 1
 
 
 # --- building blocks -------------------------------------------------------
@@ -218,7 +223,8 @@ def pseudo_residual(kind, y, f):
 def make_learner(spec: dict) -> Learner:
     return Learner(type=spec.get("type", BL_PSPLINE), feature=spec["feature"], degree=spec.get("degree", 3),
                    n_knots=spec.get("n_knots", 20), diff_order=spec.get("diff_order", 2),
-                   df=spec.get("df", 5.0), lam=spec.get("lam", 0.0), n_bins=spec.get("n_bins", BINS_SQRT))
+                   df=spec.get("df", 5.0), lam=spec.get("lam", 0.0), n_bins=spec.get("n_bins", BINS_SQRT),
+                   level=spec.get("level", 0))
 
 
 @dataclasses.dataclass

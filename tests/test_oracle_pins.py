@@ -410,3 +410,108 @@ def test_binomial_fit_decreases_risk():
     risk = np.mean([O.loss(1, a, b) for a, b in zip(y, res.f)])
     assert risk < risk0
     assert set(res.k_sel.tolist()) <= {0, 2}
+
+
+# --------------------------------------------------------------- categorical learners (App. B.1)
+
+def _categorical_data(seed=21, n=900, c=7):
+    rng = np.random.default_rng(seed)
+    probs = rng.dirichlet(np.full(c, 0.7))
+    codes = rng.choice(c, size=n, p=probs).astype(np.float64)
+    codes[:c] = np.arange(c)                        # every class present at least once
+    effect = rng.normal(size=c)
+    y = effect[codes.astype(int)] + 0.5 * rng.normal(size=n)
+    w = rng.uniform(0.5, 2.0, size=n)
+    return codes, y, w, c
+
+
+def test_categorical_ridge_closed_form_over_iterations():
+    """Ridge learner: (Z^T W Z + lambda I) is diagonal with entries n_k + lambda (App. B.1), so for
+    L2 and one learner theta after M steps is (1 - (1 - nu n_k / (n_k + lambda))^M) u_k / n_k per
+    class, with n_k the class weight and u_k the class sum of w r_0."""
+    codes, y, w, c = _categorical_data()
+    lam, nu = 3.5, 0.3
+    spec = dict(type=O.BL_CATEGORICAL, feature=0, n_knots=c, df=0.0, lam=lam)
+    r0 = y - np.sum(w * y) / np.sum(w)
+    nk = np.bincount(codes.astype(int), weights=w, minlength=c)
+    uk = np.bincount(codes.astype(int), weights=w * r0, minlength=c)
+    for M in (1, 17):
+        res = O.fit(codes[None, :], y, [spec], w=w, nu=nu, iterations=M)
+        want = (1.0 - (1.0 - nu * nk / (nk + lam)) ** M) * uk / nk
+        np.testing.assert_allclose(res.theta_f[0, :c], want, rtol=1e-10, atol=1e-13)
+        assert res.nstar[0] == c and res.lam[0] == lam
+        np.testing.assert_allclose(res.f, res.offset + res.theta_f[0, codes.astype(int)], atol=1e-12)
+
+
+def test_categorical_ridge_df_matches_scalar_closed_form():
+    """df1 of the ridge learner is sum_k n_k / (n_k + lambda) (App. B.1); the oracle's lambda, found
+    by its general matrix search, must solve that scalar equation."""
+    from scipy.optimize import brentq
+    codes, y, _, c = _categorical_data(22, n=2000, c=9)
+    nk = np.bincount(codes.astype(int), minlength=c).astype(np.float64)
+    for df in (1.5, 4.0, 8.5):
+        res = O.fit(codes[None, :], y, [dict(type=O.BL_CATEGORICAL, feature=0, n_knots=c, df=df)],
+                    iterations=1)
+        want = brentq(lambda lam: np.sum(nk / (nk + lam)) - df, 1e-12, 1e12, xtol=1e-14, rtol=1e-15)
+        assert abs(res.lam[0] - want) <= 1e-9 * want
+    # df at or above c (all classes free) gives the unpenalised fit
+    res = O.fit(codes[None, :], y, [dict(type=O.BL_CATEGORICAL, feature=0, n_knots=c, df=c)], iterations=1)
+    assert res.lam[0] == 0.0
+
+
+def test_categorical_binary_learner_is_class_mean_and_selects_largest_reduction():
+    """Binary learner of class k: theta = class mean of r (App. B.1); among binary learners of one
+    feature the argmin of the SSE is the class with the largest u_k^2 / n_k (brute force)."""
+    codes, y, w, c = _categorical_data(23)
+    specs = [dict(type=O.BL_CATEGORICAL_BINARY, feature=0, n_knots=c, level=k) for k in range(c)]
+    res = O.fit(codes[None, :], y, specs, w=w, nu=1.0, iterations=1)
+    r0 = y - np.sum(w * y) / np.sum(w)
+    nk = np.bincount(codes.astype(int), weights=w, minlength=c)
+    uk = np.bincount(codes.astype(int), weights=w * r0, minlength=c)
+    best = int(np.argmax(uk ** 2 / nk))
+    assert res.k_sel[0] == best
+    assert abs(res.theta_f[best, 0] - uk[best] / nk[best]) <= 1e-12 * abs(uk[best] / nk[best])
+    assert (res.theta_f[np.arange(c) != best, 0] == 0.0).all()
+    assert (res.lam == 0.0).all()
+    # a binary learner's SSE is sum w r^2 - u_k^2 / n_k
+    assert abs(res.sse_best[0] - (np.sum(w * r0 ** 2) - uk[best] ** 2 / nk[best])) <= 1e-9 * np.sum(w * r0 ** 2)
+
+
+def test_categorical_ridge_unpenalised_equals_sum_of_binary_steps():
+    """With lambda = 0 and nu = 1, one ridge step fits every class mean at once, i.e. the sum of the
+    c binary learners' one-step fits (they touch disjoint rows)."""
+    codes, y, w, c = _categorical_data(24)
+    ridge = O.fit(codes[None, :], y, [dict(type=O.BL_CATEGORICAL, feature=0, n_knots=c, df=0.0, lam=0.0)],
+                  w=w, nu=1.0, iterations=1)
+    specs = [dict(type=O.BL_CATEGORICAL_BINARY, feature=0, n_knots=c, level=k) for k in range(c)]
+    binary = O.fit(codes[None, :], y, specs, w=w, nu=1.0, iterations=c)
+    assert sorted(binary.k_sel.tolist()) == list(range(c))     # each class once, then done
+    np.testing.assert_allclose(binary.theta_f[:, 0], ridge.theta_f[0, :c], rtol=1e-10, atol=1e-13)
+    np.testing.assert_allclose(binary.f, ridge.f, atol=1e-12)
+
+
+def test_categorical_prediction_of_unknown_codes_is_offset_only():
+    codes, y, w, c = _categorical_data(25)
+    specs = [dict(type=O.BL_CATEGORICAL, feature=0, n_knots=c, df=3.0),
+             dict(type=O.BL_CATEGORICAL_BINARY, feature=0, n_knots=c, level=2)]
+    res = O.fit(codes[None, :], y, specs, w=w, iterations=20)
+    Xn = np.array([[0.0, 2.0, c - 1.0, -1.0, float(c), 2.5, np.nan]])
+    pred = O.predict(Xn, specs, [0.0, 0.0], [c - 1.0, c - 1.0], res.theta_f, res.offset)
+    want = res.offset + np.array([res.theta_f[0, 0], res.theta_f[0, 2] + res.theta_f[1, 0], res.theta_f[0, c - 1],
+                                  0.0, 0.0, 0.0, 0.0])
+    np.testing.assert_allclose(pred, want, atol=1e-14)
+    # at the training rows the prediction is the fitted vector
+    np.testing.assert_allclose(O.predict(codes[None, :], specs, [0.0, 0.0], [c - 1.0, c - 1.0], res.theta_f,
+                                         res.offset), res.f, atol=1e-12)
+
+
+@pytest.mark.parametrize("bad", [2.5, -1.0, 7.0])
+def test_categorical_rejects_codes_outside_the_classes(bad):
+    codes, y, _, c = _categorical_data(26)
+    codes = codes.copy()
+    codes[5] = bad
+    with pytest.raises(RuntimeError):
+        O.fit(codes[None, :], y, [dict(type=O.BL_CATEGORICAL, feature=0, n_knots=c)], iterations=1)
+    with pytest.raises(RuntimeError):
+        O.fit(np.arange(900.0)[None, :] % 7, y, [dict(type=O.BL_CATEGORICAL_BINARY, feature=0, n_knots=7,
+                                                        level=7)], iterations=1)
