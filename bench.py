@@ -344,14 +344,14 @@ def run_ours(args):
 
     if not args.skip_e2e:
         line["e2e"] = run_e2e(cwb, data, stream, dev, local)
+    if rank == 0 and world == 1 and not args.skip_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_full(data)
     if rank == 0 and world == 1:
         del data
         if not args.skip_batched:
             line["batched"] = run_batched(cwb, args)
         if not args.skip_served:
             line["served"] = run_served(cwb, args)
-    if rank == 0 and world == 1 and not args.skip_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_full(data)
     model.free()
     if rank == 0:
         print(json.dumps(line), flush=True)

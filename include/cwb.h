@@ -57,7 +57,12 @@ typedef enum {
 
 typedef enum { CWB_LOSS_L2 = 0, CWB_LOSS_BINOMIAL = 1 } cwb_loss;
 typedef enum { CWB_OPT_CWB = 0, CWB_OPT_ACWB = 1, CWB_OPT_HCWB = 2 } cwb_optimizer;
-typedef enum { CWB_BL_PSPLINE = 0, CWB_BL_LINEAR = 1 } cwb_bl_type;
+typedef enum {
+    CWB_BL_PSPLINE = 0,             /* P-spline (Sec. 2.2) */
+    CWB_BL_LINEAR = 1,              /* linear effect (1, x) */
+    CWB_BL_CATEGORICAL = 2,         /* ridge representation of a categorical feature (App. B.1) */
+    CWB_BL_CATEGORICAL_BINARY = 3   /* sparse binary representation: one class of a categorical feature */
+} cwb_bl_type;
 typedef enum { CWB_F32 = 0, CWB_F64 = 1 } cwb_dtype;
 
 /* n_bins codes (cwb_learner.n_bins) */
@@ -68,16 +73,32 @@ typedef enum { CWB_F32 = 0, CWB_F64 = 1 } cwb_dtype;
 #define CWB_MAX_D 64          /* basis dimension per learner */
 #define CWB_MAX_BINS 65535    /* design points per learner (uint16 index vector) */
 
-/* One univariate base learner (Sec. 2.2). */
+/*
+ * One univariate base learner (Sec. 2.2; categorical learners App. B.1).
+ *
+ * Categorical learners read their feature as class codes: every value must be an
+ * integer in [0, c) with c = n_knots (CWB_EINVAL otherwise).  Each class is one
+ * design point, so the lookup k_i is the code itself and n_bins is ignored.  The
+ * ridge learner has d = c coefficients, the dummy design and the identity penalty
+ * (so (Z^T W Z + lambda I) is diagonal with the class weights n_k + lambda, and
+ * df1 = sum_k n_k / (n_k + lambda)); c <= CWB_MAX_D.  The binary learner has one
+ * unpenalised coefficient for the class `level` (its class mean); c <= CWB_MAX_BINS.
+ * Learners of either kind on the same feature with the same c share one binning,
+ * i.e. one histogram per iteration.  Prediction maps any value that is not a valid
+ * code to a zero contribution.
+ */
 typedef struct {
     int32_t type;        /* cwb_bl_type */
     int32_t feature;     /* column of X, 0 <= feature < p */
     int32_t degree;      /* B-spline degree, 0..3 (P-spline only; 3 = cubic) */
-    int32_t n_knots;     /* interior equidistant knots (P-spline only); d = n_knots + degree + 1 */
+    int32_t n_knots;     /* P-spline: interior equidistant knots, d = n_knots + degree + 1;
+                            categorical: number of classes c >= 2 */
     int32_t diff_order;  /* order of the difference penalty, 1 <= diff_order < d (P-spline only) */
     double df;           /* > 0: lambda is chosen so that tr(H_k) = df (App. A.2, Eq. df1) */
-    double lambda;       /* used when df <= 0 (P-spline only); linear learners are unpenalised */
-    int32_t n_bins;      /* CWB_BINS_EXACT, CWB_BINS_SQRT, or an explicit n* >= 2 */
+    double lambda;       /* used when df <= 0 (P-spline, categorical ridge); linear and binary
+                            learners are unpenalised */
+    int32_t n_bins;      /* CWB_BINS_EXACT, CWB_BINS_SQRT, or an explicit n* >= 2 (numeric learners) */
+    int32_t level;       /* categorical binary: the class it indicates, 0 <= level < n_knots */
 } cwb_learner;
 
 /* Optimiser settings (Algorithm 1, 3, 4 inputs). */

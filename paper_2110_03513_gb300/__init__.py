@@ -6,7 +6,7 @@ them.  Every step of the method runs in the CUDA library; importing this
 package fails loudly if ``libcwb.so`` has not been built.
 """
 from .binding import (  # noqa: F401
-    BINS_EXACT, BINS_SQRT, BL_LINEAR, BL_PSPLINE, LOSS_BINOMIAL, LOSS_L2, OPT_ACWB, OPT_CWB, OPT_HCWB,
+    BINS_EXACT, BINS_SQRT, BL_CATEGORICAL, BL_CATEGORICAL_BINARY, BL_LINEAR, BL_PSPLINE, LOSS_BINOMIAL, LOSS_L2, OPT_ACWB, OPT_CWB, OPT_HCWB,
     Batch, CwbError, Model, Server, cwb_create, cwb_fit, cwb_force_selection, cwb_free, cwb_get_bin_index, cwb_get_coefficients,
     cwb_get_criteria, cwb_get_fitted, cwb_get_learner_info, cwb_get_learner_matrices, cwb_get_trace,
     cwb_get_profile, cwb_get_residuals, cwb_get_scatter_plan, cwb_last_error, cwb_predict, cwb_predict_noalloc, cwb_profile, cwb_synchronize, learner, library_path, load_library,

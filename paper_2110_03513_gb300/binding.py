@@ -16,7 +16,7 @@ _LIB_PATH = os.path.join(_HERE, "libcwb.so")
 
 LOSS_L2, LOSS_BINOMIAL = 0, 1
 OPT_CWB, OPT_ACWB, OPT_HCWB = 0, 1, 2
-BL_PSPLINE, BL_LINEAR = 0, 1
+BL_PSPLINE, BL_LINEAR, BL_CATEGORICAL, BL_CATEGORICAL_BINARY = 0, 1, 2, 3
 F32, F64 = 0, 1
 BINS_EXACT, BINS_SQRT = 0, -1
 PROF_ALL = 1
@@ -34,7 +34,8 @@ class CwbError(RuntimeError):
 
 class cwb_learner(C.Structure):
     _fields_ = [("type", C.c_int32), ("feature", C.c_int32), ("degree", C.c_int32), ("n_knots", C.c_int32),
-                ("diff_order", C.c_int32), ("df", C.c_double), ("lam", C.c_double), ("n_bins", C.c_int32)]
+                ("diff_order", C.c_int32), ("df", C.c_double), ("lam", C.c_double), ("n_bins", C.c_int32),
+                ("level", C.c_int32)]
 
 
 class cwb_config(C.Structure):
@@ -142,9 +143,10 @@ def _dtype_code(a) -> int:
 
 
 def learner(feature: int, *, type: int = BL_PSPLINE, degree: int = 3, n_knots: int = 20, diff_order: int = 2,
-            df: float = 5.0, lam: float = 0.0, n_bins: int = BINS_SQRT) -> cwb_learner:
+            df: float = 5.0, lam: float = 0.0, n_bins: int = BINS_SQRT, level: int = 0) -> cwb_learner:
+    """One base learner; for the categorical types n_knots is the number of classes c."""
     return cwb_learner(type=type, feature=feature, degree=degree, n_knots=n_knots, diff_order=diff_order, df=df,
-                       lam=lam, n_bins=n_bins)
+                       lam=lam, n_bins=n_bins, level=level)
 
 
 # ---- one wrapper per C entry point -------------------------------------------------

@@ -8,6 +8,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -55,8 +56,18 @@ __device__ __forceinline__ double knot_at(double xmin, double delta, int i_minus
     return __dadd_rn(xmin, __dmul_rn((double)i_minus_q, delta));
 }
 
+// Categorical learners (App. B.1) take the raw value: a valid class code selects its
+// coefficient, anything else contributes nothing.  Numeric learners clamp x to the
+// training range.  For a binary learner q holds the class it indicates.
 __device__ double learner_eval(double x, int type, int q, int nk, double xmin, double xmax, const double* theta)
 {
+    if (type == CWB_BL_CATEGORICAL || type == CWB_BL_CATEGORICAL_BINARY) {
+        if (!(x >= 0.0 && x < (double)nk && x == floor(x))) return 0.0;
+        const int code = (int)x;
+        if (type == CWB_BL_CATEGORICAL) return theta[code];
+        return code == q ? theta[0] : 0.0;
+    }
+    x = fmin(fmax(x, xmin), xmax);
     if (type == CWB_BL_LINEAR) return theta[0] + theta[1] * x;
     const double delta = __ddiv_rn(__dsub_rn(xmax, xmin), (double)(nk + 1));
     const int last = nk + q;
@@ -93,10 +104,8 @@ __global__ void k_predict(const T* __restrict__ X, int64_t n_new, int K, int D, 
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_new; i += (int64_t)gridDim.x * blockDim.x) {
         double acc = offset;
         for (int k = 0; k < K; ++k) {
-            double x = (double)X[(int64_t)l_feat[k] * n_new + i];
-            const double lo = l_xmin[k], hi = l_xmax[k];
-            x = fmin(fmax(x, lo), hi);
-            acc += learner_eval(x, l_type[k], l_degree[k], l_nknots[k], lo, hi, coef + (int64_t)k * D);
+            const double x = (double)X[(int64_t)l_feat[k] * n_new + i];
+            acc += learner_eval(x, l_type[k], l_degree[k], l_nknots[k], l_xmin[k], l_xmax[k], coef + (int64_t)k * D);
         }
         out[i] = (float)acc;
     }
@@ -158,7 +167,17 @@ cwb_status validate_learner(const cwb_learner& b, int32_t p, int k)
         return CWB_EINVAL;
     };
     if (b.feature < 0 || b.feature >= p) return bad("feature index out of range");
-    if (b.type != CWB_BL_PSPLINE && b.type != CWB_BL_LINEAR) return bad("unknown base-learner type");
+    if (b.type < CWB_BL_PSPLINE || b.type > CWB_BL_CATEGORICAL_BINARY) return bad("unknown base-learner type");
+    if (b.type == CWB_BL_CATEGORICAL) {
+        if (b.n_knots < 2 || b.n_knots > CWB_MAX_D) return bad("a ridge learner needs 2 <= classes <= CWB_MAX_D");
+        if (!(b.df > 0.0) && !(b.lambda >= 0.0)) return bad("need df > 0 or lambda >= 0");
+        return CWB_OK;
+    }
+    if (b.type == CWB_BL_CATEGORICAL_BINARY) {
+        if (b.n_knots < 2 || b.n_knots > CWB_MAX_BINS) return bad("a binary learner needs 2 <= classes <= 65535");
+        if (b.level < 0 || b.level >= b.n_knots) return bad("level must be in [0, classes)");
+        return CWB_OK;
+    }
     if (b.n_bins != CWB_BINS_EXACT && b.n_bins != CWB_BINS_SQRT && (b.n_bins < 2 || b.n_bins > CWB_MAX_BINS))
         return bad("n_bins must be CWB_BINS_EXACT, CWB_BINS_SQRT or in [2, 65535]");
     if (b.type == CWB_BL_PSPLINE) {
@@ -220,17 +239,20 @@ cwb_status create_impl(const cwb_config* cfg, const void* X, int32_t x_dtype, in
         }
         m->own_stream = true;
     }
-    // learners on the same feature with the same binning share one index vector
-    std::map<std::pair<int, int>, int> bmap;
+    // learners on the same feature with the same binning share one index vector; categorical
+    // learners on one feature with the same number of classes share the class-code binning
+    std::map<std::tuple<int, int, int>, int> bmap;
     for (int k = 0; k < K; ++k) {
         HostLearner L;
         L.spec = bl[k];
-        auto key = std::make_pair(bl[k].feature, bl[k].n_bins);
+        const bool cat = bl[k].type == CWB_BL_CATEGORICAL || bl[k].type == CWB_BL_CATEGORICAL_BINARY;
+        auto key = std::make_tuple(bl[k].feature, cat ? 1 : 0, cat ? bl[k].n_knots : bl[k].n_bins);
         auto it = bmap.find(key);
         if (it == bmap.end()) {
             HostBinning hb{};
             hb.feature = bl[k].feature;
-            hb.nbins_spec = bl[k].n_bins;
+            hb.nbins_spec = cat ? bl[k].n_knots : bl[k].n_bins;
+            hb.categories = cat ? bl[k].n_knots : 0;
             it = bmap.emplace(key, (int)m->bins.size()).first;
             m->bins.push_back(hb);
         }
@@ -238,6 +260,12 @@ cwb_status create_impl(const cwb_config* cfg, const void* X, int32_t x_dtype, in
         if (bl[k].type == CWB_BL_LINEAR) {
             L.d = 2;
             L.nnz = 2;
+        } else if (bl[k].type == CWB_BL_CATEGORICAL) {
+            L.d = bl[k].n_knots;
+            L.nnz = 1;
+        } else if (bl[k].type == CWB_BL_CATEGORICAL_BINARY) {
+            L.d = 1;
+            L.nnz = 1;
         } else {
             L.d = bl[k].n_knots + bl[k].degree + 1;
             L.nnz = bl[k].degree + 1;

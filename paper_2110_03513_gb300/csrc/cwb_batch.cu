@@ -252,9 +252,15 @@ uint64_t estimate_footprint(const Request& r)
     int d_max = 2;
     uint64_t nstar_max = 2;
     for (const cwb_learner& l : r.bl) {
-        if (std::find(bins.begin(), bins.end(), std::make_pair(l.feature, l.n_bins)) == bins.end())
-            bins.push_back({l.feature, l.n_bins});
+        const bool cat = l.type == CWB_BL_CATEGORICAL || l.type == CWB_BL_CATEGORICAL_BINARY;
+        const auto key = std::make_pair(l.feature, cat ? -3 - l.n_knots : l.n_bins);   // categorical: by classes
+        if (std::find(bins.begin(), bins.end(), key) == bins.end()) bins.push_back(key);
         if (l.type == CWB_BL_PSPLINE) d_max = std::max(d_max, l.n_knots + l.degree + 1);
+        if (l.type == CWB_BL_CATEGORICAL) d_max = std::max(d_max, l.n_knots);
+        if (cat) {
+            nstar_max = std::max(nstar_max, (uint64_t)l.n_knots);
+            continue;
+        }
         uint64_t ns = l.n_bins > 1 ? (uint64_t)l.n_bins : (l.n_bins == CWB_BINS_SQRT ? 1 : (uint64_t)r.n);
         if (l.n_bins == CWB_BINS_SQRT) {
             ns = 1;

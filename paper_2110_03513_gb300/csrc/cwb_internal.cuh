@@ -97,6 +97,7 @@ struct ScatterPlan {
 struct HostBinning {
     int feature;
     int nbins_spec;      // n_bins code requested
+    int categories;      // > 0: categorical codes 0..categories-1, one design point per class
     int nstar;
     int exact;
     double xmin, xmax;
@@ -142,7 +143,7 @@ struct cwb_model {
     double* Acrit = nullptr;              // [2][K][D][D] criterion matrix P G P - 2 P
     int32_t *l_bin = nullptr, *l_d = nullptr, *l_nstar = nullptr, *l_type = nullptr;
     double *l_xmin = nullptr, *l_xmax = nullptr;
-    int32_t *l_degree = nullptr, *l_nknots = nullptr, *l_feat = nullptr;
+    int32_t *l_degree = nullptr, *l_nknots = nullptr, *l_feat = nullptr;   // l_degree: the class of a binary learner
     float* part = nullptr;                // [clusters][cmax][f_lane][nb_cta] per-cluster histograms
     int32_t* cluster_slot = nullptr;      // [clusters]
     int32_t* slot_c0 = nullptr;           // [slots + 1]

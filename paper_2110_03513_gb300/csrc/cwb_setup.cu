@@ -80,6 +80,17 @@ __global__ void k_check_weights(const T* __restrict__ w, int64_t n, uint32_t* ba
     }
 }
 
+// Categorical feature: every value must be an integer class code in [0, c).
+template <typename T>
+__global__ void k_check_codes(const T* __restrict__ X, int64_t feat, int64_t n, int c, uint32_t* bad)
+{
+    const T* x = X + feat * n;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = (double)x[i];
+        if (!(v >= 0.0 && v < (double)c && v == floor(v))) atomicOr(bad, 1u);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Feature range: per binning min and max over all rows (FP64 compare).
 
@@ -329,6 +340,11 @@ __global__ void k_basis(BasisArgs a)
             if (a.l_type[k] == CWB_BL_LINEAR) {
                 N[0] = 1.0;
                 N[1] = z;
+            } else if (a.l_type[k] == CWB_BL_CATEGORICAL) {
+                N[0] = 1.0;                            // dummy design: class l has column l
+                col = l;
+            } else if (a.l_type[k] == CWB_BL_CATEGORICAL_BINARY) {
+                N[0] = l == a.l_degree[k] ? 1.0 : 0.0; // indicator of the learner's class
             } else {
                 col = bspline_nonzero(z, xmin, xmax, a.l_degree[k], a.l_nknots[k], N);
             }
@@ -513,8 +529,10 @@ __global__ void __launch_bounds__(kLamThreads) k_lambda(LamArgs a)
     __shared__ int sh_done, sh_status;
     const double* Gs = a.G + ((int64_t)ph * a.K + k) * a.D * a.D;
     for (int e = tid; e < d * d; e += blockDim.x) G[e] = Gs[(e / d) * a.D + e % d];
-    const bool pspline = a.l_type[k] == CWB_BL_PSPLINE;
-    const int ord = pspline ? a.l_diff[k] : 0;
+    // P-splines: difference penalty of order diff_order; categorical ridge: the identity
+    // (difference matrix of order 0); linear and binary learners: unpenalised
+    const bool pspline = a.l_type[k] == CWB_BL_PSPLINE || a.l_type[k] == CWB_BL_CATEGORICAL;
+    const int ord = a.l_type[k] == CWB_BL_PSPLINE ? a.l_diff[k] : 0;
     const int nr = d - ord;
     if (pspline) {
         // row r of the order-`ord` difference matrix: (-1)^(ord - t) binom(ord, t) at column r + t
@@ -848,8 +866,8 @@ cwb_status setup_model(cwb_model* m, const void* X_in, int x_dtype, const void* 
 
     // --- validity checks on the data
     uint32_t* flags = nullptr;
-    CWB_TRY(tmp.get(&flags, 4, s));
-    CWB_CUDA_TRY(cudaMemsetAsync(flags, 0, 16, s));
+    CWB_TRY(tmp.get(&flags, 8, s));
+    CWB_CUDA_TRY(cudaMemsetAsync(flags, 0, 32, s));
     if (m->cfg.loss == CWB_LOSS_BINOMIAL) {
         if (x_dtype == CWB_F64) k_check_binary<<<g_rows, kThreads, 0, s>>>((const double*)yd, n, flags);
         else k_check_binary<<<g_rows, kThreads, 0, s>>>((const float*)yd, n, flags);
@@ -893,8 +911,14 @@ cwb_status setup_model(cwb_model* m, const void* X_in, int x_dtype, const void* 
         else k_minmax_partial<<<grid, kThreads, 0, s>>>((const float*)Xd, feat_d, n, pmin, pmax, flags + 2);
         k_minmax_final<<<B, 32, 0, s>>>(pmin, pmax, nblk, xmin_d, xmax_d);
     }
+    for (int b = 0; b < B; ++b) {
+        const HostBinning& hb = m->bins[b];
+        if (!hb.categories) continue;
+        if (x_dtype == CWB_F64) k_check_codes<<<g_rows, kThreads, 0, s>>>((const double*)Xd, hb.feature, n, hb.categories, flags + 4);
+        else k_check_codes<<<g_rows, kThreads, 0, s>>>((const float*)Xd, hb.feature, n, hb.categories, flags + 4);
+    }
     std::vector<double> xmin_h(B), xmax_h(B);
-    uint32_t flags_h[4] = {0, 0, 0, 0};
+    uint32_t flags_h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     CWB_CUDA_TRY(cudaMemcpyAsync(xmin_h.data(), xmin_d, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
     CWB_CUDA_TRY(cudaMemcpyAsync(xmax_h.data(), xmax_d, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
     CWB_CUDA_TRY(cudaMemcpyAsync(flags_h, flags, sizeof(flags_h), cudaMemcpyDeviceToHost, s));
@@ -902,13 +926,19 @@ cwb_status setup_model(cwb_model* m, const void* X_in, int x_dtype, const void* 
     if (flags_h[0]) { set_error("binomial loss needs targets in {0, 1}"); return CWB_EINVAL; }
     if (flags_h[1]) { set_error("observation weights must be finite and > 0"); return CWB_EINVAL; }
     if (flags_h[2]) { set_error("features must be finite"); return CWB_EINVAL; }
+    if (flags_h[4]) { set_error("a categorical feature holds a value that is not a class code 0..c-1"); return CWB_EINVAL; }
     for (int b = 0; b < B; ++b) {
-        m->bins[b].xmin = xmin_h[b];
-        m->bins[b].xmax = xmax_h[b];
         if (!(xmax_h[b] > xmin_h[b])) {
             set_error("feature " + std::to_string(m->bins[b].feature) + " is constant (max == min)");
             return CWB_EINVAL;
         }
+        if (m->bins[b].categories) {
+            // class codes: design point l is class l, i.e. equidistant points 0, 1, ..., c-1
+            xmin_h[b] = 0.0;
+            xmax_h[b] = (double)(m->bins[b].categories - 1);
+        }
+        m->bins[b].xmin = xmin_h[b];
+        m->bins[b].xmax = xmax_h[b];
     }
 
     // --- exact binnings: sorted unique values on the device
@@ -918,7 +948,10 @@ cwb_status setup_model(cwb_model* m, const void* X_in, int x_dtype, const void* 
     bool any_exact = false;
     for (int b = 0; b < B; ++b) {
         HostBinning& hb = m->bins[b];
-        if (hb.nbins_spec == CWB_BINS_EXACT) {
+        if (hb.categories) {
+            hb.exact = 0;
+            hb.nstar = hb.categories;
+        } else if (hb.nbins_spec == CWB_BINS_EXACT) {
             hb.exact = 1;
             any_exact = true;
         } else {
@@ -1003,7 +1036,7 @@ cwb_status setup_model(cwb_model* m, const void* X_in, int x_dtype, const void* 
         const HostLearner& L = m->lrn[k];
         lb[k] = L.binning;
         lt[k] = L.spec.type;
-        ldeg[k] = L.spec.degree;
+        ldeg[k] = L.spec.type == CWB_BL_CATEGORICAL_BINARY ? L.spec.level : L.spec.degree;   // binary: its class
         lnk[k] = L.spec.n_knots;
         lns[k] = m->bins[L.binning].nstar;
         ld[k] = L.d;

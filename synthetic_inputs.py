@@ -22,6 +22,7 @@ import numpy as np
 __all__ = [
     "Dataset",
     "additive_regression",
+    "mixed_categorical",
     "sim_small_exact",
     "sim_binned_l2",
     "sim_binomial_hybrid",
@@ -85,6 +86,42 @@ def additive_regression(n: int, p: int, n_informative: int, seed: int, *,
     y = eta + noise
     return Dataset(X=X.astype(dtype), y=y.astype(dtype), eta=eta,
                    description=f"additive regression n={n} p={p} inf={n_informative} seed={seed}")
+
+
+def mixed_categorical(n: int, p_num: int, classes: list[int], seed: int, *, n_informative_num: int = 2,
+                      n_informative_cat: int = 1, dtype=np.float32, snr: float = 1.0,
+                      binomial: bool = False) -> Dataset:
+    """Numerical plus categorical features (the setting of the paper's categorical simulation,
+    App. B.2, with the numerical effects of Sec. 4.1.1 added).
+
+    Rows 0..p_num-1 of X are U[0, 1] features, the first ``n_informative_num`` with the effects of
+    :func:`additive_regression`.  Then one row per entry of ``classes``: integer class codes
+    0..c-1 stored as floats, class frequencies drawn from a Dirichlet(0.7) (so some classes are
+    rare), every class present at least once.  The first ``n_informative_cat`` categorical features
+    carry class effects drawn from N(0, 1); the others are noise.  ``binomial`` turns the linear
+    predictor into y ~ Bernoulli(sigmoid(eta)).
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    p = p_num + len(classes)
+    X = np.empty((p, n), dtype=np.float64)
+    X[:p_num] = rng.random((p_num, n))
+    eta = np.zeros(n, dtype=np.float64)
+    for j in range(min(n_informative_num, p_num)):
+        eta += _effect((j % 10) + 1, X[j])
+    for t, c in enumerate(classes):
+        probs = rng.dirichlet(np.full(c, 0.7))
+        codes = rng.choice(c, size=n, p=probs)
+        codes[rng.choice(n, size=c, replace=False)] = np.arange(c)
+        X[p_num + t] = codes
+        if t < n_informative_cat:
+            eta += rng.standard_normal(c)[codes]
+    if binomial:
+        y = (rng.random(n) < 1.0 / (1.0 + np.exp(-eta))).astype(np.float64)
+    else:
+        sd = float(np.std(eta)) if n > 1 else 1.0
+        y = eta + rng.standard_normal(n) * (sd / snr if snr > 0 else 0.0)
+    return Dataset(X=X.astype(dtype), y=y.astype(dtype), eta=eta,
+                   description=f"numerical + categorical n={n} p_num={p_num} classes={classes} seed={seed}")
 
 
 def sim_small_exact(seed: int = 0, n: int = 10_000, p: int = 10) -> Dataset:

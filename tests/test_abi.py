@@ -56,3 +56,29 @@ def test_null_and_invalid_arguments_fail_without_gpu(lib):
     assert "NULL" in binding.cwb_last_error()
     L.cwb_free(None)          # NULL-safe
     assert L.cwb_fit(None, 5) == 1
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """The ctypes structs of the binding have the C compiler's size and field offsets for every
+    struct include/cwb.h declares (compiled here with gcc as plain C)."""
+    import subprocess
+    from paper_2110_03513_gb300 import binding
+    structs = {name: getattr(binding, name) for name in ("cwb_learner", "cwb_config", "cwb_learner_info",
+                                                          "cwb_server_config")}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "cwb.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            cname = {"lam": "lambda", "lam_full": "lambda_full"}.get(field, field)
+            lines.append(f'printf("{name} {field} %zu\\n", offsetof({name}, {cname}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    out = subprocess.check_output([str(exe)], text=True).split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert got[(name, field)] == getattr(cls, field).offset, (name, field)

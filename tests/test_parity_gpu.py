@@ -27,7 +27,8 @@ def _specs_to_gpu(cwb, specs):
     for s in specs:
         out.append(cwb.learner(s["feature"], type=s.get("type", 0), degree=s.get("degree", 3),
                                n_knots=s.get("n_knots", 20), diff_order=s.get("diff_order", 2),
-                               df=s.get("df", 5.0), lam=s.get("lam", 0.0), n_bins=s.get("n_bins", -1)))
+                               df=s.get("df", 5.0), lam=s.get("lam", 0.0), n_bins=s.get("n_bins", -1),
+                               level=s.get("level", 0)))
     return out
 
 
@@ -65,6 +66,13 @@ def run_pair(cwb, X, y, specs, *, M, loss=0, opt=0, nu=0.1, gamma=0.0, patience=
         p, n = X.shape
         idx = rng.integers(0, n, size=min(n, 3000))
         Xn = X[:, idx].astype(np.float64) + rng.normal(scale=0.01, size=(p, idx.size))
+        for sp in specs:
+            if sp.get("type", 0) in (O.BL_CATEGORICAL, O.BL_CATEGORICAL_BINARY):
+                # class codes, a few replaced by an unseen code, a negative one or a non-integer
+                row = X[sp["feature"], idx].astype(np.float64)
+                odd = rng.random(idx.size) < 0.05
+                row[odd] = rng.choice([float(sp["n_knots"]), -1.0, 1.5], size=int(odd.sum()))
+                Xn[sp["feature"]] = row
         xmin = [X[s["feature"]].min() for s in specs]
         xmax = [X[s["feature"]].max() for s in specs]
         pred_ref = O.predict(Xn, specs, xmin, xmax, ref.theta_f, ref.offset)
@@ -193,6 +201,63 @@ def test_cwb_weights_and_mixed_learners(cwb):
     specs = [dict(feature=j, n_bins=-1) for j in range(5)] + [dict(feature=j, n_bins=-1, type=1) for j in range(5)]
     specs += [dict(feature=1, n_bins=50, degree=2, n_knots=10, df=4.0)]
     run_pair(cwb, data.X, data.y, specs, M=120, w=w)
+
+
+def _categorical_specs(p_num, classes, *, binary_of=()):
+    specs = [dict(feature=j, n_bins=-1) for j in range(p_num)]
+    for t, c in enumerate(classes):
+        specs.append(dict(type=O.BL_CATEGORICAL, feature=p_num + t, n_knots=c, df=min(5.0, c - 0.5)))
+    for t in binary_of:
+        specs += [dict(type=O.BL_CATEGORICAL_BINARY, feature=p_num + t, n_knots=classes[t], level=k)
+                  for k in range(classes[t])]
+    return specs
+
+
+def test_categorical_ridge_and_binary_l2(cwb):
+    """Ridge and binary categorical learners (App. B.1) beside P-splines, L2, uint8 bins."""
+    classes = [6, 13, 40, 3]
+    data = S.mixed_categorical(20_011, 3, classes, seed=31, n_informative_cat=2)
+    specs = _categorical_specs(3, classes, binary_of=(1,))
+    model, ref = run_pair(cwb, data.X, data.y, specs, M=150)
+    # a ridge learner and the binary learners of one feature share that feature's class binning
+    info = [model.learner_info(k) for k in range(len(specs))]
+    assert info[4].nstar == 13 and info[4].d == 13
+    assert {info[k].binning for k in range(7, 7 + 13)} == {info[4].binning}
+    assert all(info[k].d == 1 for k in range(7, 7 + 13))
+
+
+def test_categorical_fixed_lambda_binomial_uint16(cwb):
+    """Binomial loss, a ridge learner with a fixed lambda, and P-splines at n* = 1500 (uint16)."""
+    classes = [9, 64]
+    data = S.mixed_categorical(60_000, 4, classes, seed=32, binomial=True)
+    specs = [dict(feature=j, n_bins=1500) for j in range(4)]
+    specs += [dict(type=O.BL_CATEGORICAL, feature=4, n_knots=9, df=0.0, lam=250.0),
+              dict(type=O.BL_CATEGORICAL, feature=5, n_knots=64, df=12.0)]
+    run_pair(cwb, data.X, data.y, specs, M=120, loss=1)
+
+
+def test_categorical_acwb_and_hcwb(cwb):
+    classes = [7, 20]
+    data = S.mixed_categorical(30_000, 3, classes, seed=33, binomial=True)
+    rng = np.random.default_rng(5)
+    val = (rng.random(data.n) < 0.25).astype(np.uint8)
+    specs = _categorical_specs(3, classes, binary_of=(0,))
+    run_pair(cwb, data.X, data.y, specs, M=100, loss=1, opt=1, gamma=0.01)
+    run_pair(cwb, data.X, data.y, specs, M=160, loss=1, opt=2, gamma=0.01, patience=3, val_mask=val)
+
+
+def test_categorical_invalid_codes_are_rejected(cwb):
+    data = S.mixed_categorical(2_000, 1, [5], seed=34)
+    for bad in (2.5, -1.0, 5.0):
+        X = data.X.copy()
+        X[1, 17] = bad
+        with pytest.raises(cwb.CwbError) as e:
+            cwb.Model(X, data.y, [cwb.learner(1, type=cwb.BL_CATEGORICAL, n_knots=5)], device=0)
+        assert e.value.status == 1 and "class code" in str(e.value)
+    with pytest.raises(cwb.CwbError):
+        cwb.Model(data.X, data.y, [cwb.learner(1, type=cwb.BL_CATEGORICAL_BINARY, n_knots=5, level=5)], device=0)
+    with pytest.raises(cwb.CwbError):
+        cwb.Model(data.X, data.y, [cwb.learner(1, type=cwb.BL_CATEGORICAL, n_knots=65)], device=0)
 
 
 def test_duplicate_learners_tie_to_lowest_index(cwb):
