@@ -147,7 +147,7 @@ void free_model(cwb_model* m)
     if (!m) return;
     if (m->stream) cudaStreamSynchronize(m->stream);
     void* bufs[] = {m->ind, m->y, m->y_lo, m->w, m->f, m->h, m->c, m->rw, m->perm, m->zb, m->zb64, m->zcol, m->crange, m->toff, m->ztab, m->G,
-                    m->P, m->Acrit, m->lambda, m->l_bin, m->l_d, m->l_nstar, m->l_type, m->l_xmin, m->l_xmax, m->l_degree,
+                    m->P, m->Acrit, m->Pdf, m->Adf, m->lambda, m->l_bin, m->l_d, m->l_nstar, m->l_type, m->l_xmin, m->l_xmax, m->l_degree,
                     m->l_nknots, m->l_feat, m->part, m->cluster_slot, m->slot_c0, m->theta_it, m->q_it, m->v, m->state, m->risk_part, m->tr_k,
                     m->tr_mode, m->tr_theta, m->tr_q, m->forced, m->coef};
     for (void* p : bufs) dev_free(p);

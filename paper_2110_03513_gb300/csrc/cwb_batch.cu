@@ -275,7 +275,7 @@ uint64_t estimate_footprint(const Request& r)
     bytes += n_pad * (4 + 4 + 4 + 8 + 8);                               // y, y_lo, w, f, rw
     if (accel) bytes += n_pad * (8 + 4 + 4 + 4);                        // h, c, second channel, perm
     bytes += K * nstar_max * (16 + 4 + 16 + 8 + 8);                     // zb, zcol, ztab, v, zb64
-    bytes += 4 * K * (uint64_t)d_max * d_max * 8;                       // G, P per phase
+    bytes += 8 * K * (uint64_t)d_max * d_max * 8;                       // G, P, A and their float pairs per phase
     bytes += 152ull * 32 * nstar_max * 4 * (accel ? 2 : 1);             // cluster partial histograms
     bytes += (uint64_t)r.p * r.n * (r.x_dtype == CWB_F64 ? 8 : 4);      // staged features during creation
     bytes += 64ull << 20;                                               // traces, tables, slack

@@ -141,6 +141,8 @@ struct cwb_model {
     float* ztab = nullptr;                // [K][4 S] column-major reduced design
     double *G = nullptr, *P = nullptr, *lambda = nullptr;
     double* Acrit = nullptr;              // [2][K][D][D] criterion matrix P G P - 2 P
+    float2* Pdf = nullptr;                // [2][K][D][D] P as float-float pairs (hi, lo) for the solve
+    float2* Adf = nullptr;                // [2][K][D][D] Acrit as float-float pairs
     int32_t *l_bin = nullptr, *l_d = nullptr, *l_nstar = nullptr, *l_type = nullptr;
     double *l_xmin = nullptr, *l_xmax = nullptr;
     int32_t *l_degree = nullptr, *l_nknots = nullptr, *l_feat = nullptr;   // l_degree: the class of a binary learner

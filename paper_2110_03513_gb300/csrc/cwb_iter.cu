@@ -43,6 +43,9 @@ enum { kRowsFused = 0, kRowsUpdate = 1, kRowsResid = 2 };
 // the successor grid be scheduled.
 __device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+// Release / acquire fence at GPU scope for the last-block tickets (the data behind a ticket is
+// read with L2 loads); cheaper than the sequentially consistent fence of __threadfence().
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
 struct RowArgs {
     DevState* state;
@@ -187,14 +190,51 @@ __device__ __forceinline__ void store_df4(float* p, int64_t i4, const DF v[4])
     *reinterpret_cast<float4*>(p + 2 * i4 + 4) = make_float4(v[2].hi, v[2].lo, v[3].hi, v[3].lo);
 }
 
-template <int KIND, typename IndT>
+// Inputs of one group of 4 rows that do not depend on the iteration state (the low parts of
+// FP64 targets and the weights, absent in the common case, are loaded with the selected bins).
+struct RowIn {
+    DF f[4], h[4];
+    float4 y;
+};
+
+// need_y: targets (residual passes and the validation risk)
+template <bool ACC>
+__device__ __forceinline__ void load_row_in(const RowArgs& a, int64_t i4, RowIn& in, bool need_y)
+{
+    load_df4(a.f, i4, in.f);
+    if (ACC && a.h) load_df4(a.h, i4, in.h);
+    else for (int t = 0; t < 4; ++t) in.h[t] = {0.0f, 0.0f};
+    in.y = need_y ? *reinterpret_cast<const float4*>(a.y + i4) : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// A thread handles row_groups(ACC) groups of 4 rows per pass (blockDim.x * 4 rows apart); the
+// loads of a pass are all issued before any of its arithmetic, and those of the first pass
+// before the iteration state is read, so a pass costs about one memory round trip.  Models
+// with accelerated iterations carry twice the row state and take one group.
+__host__ __device__ constexpr int row_groups(bool acc) { return acc ? 1 : 2; }
+
+// ACC: the model runs accelerated iterations (ACWB / HCWB); plain CWB models compile without
+// the momentum sequence, the error-corrected residual and their loads.
+template <int KIND, typename IndT, bool ACC>
 __global__ void __launch_bounds__(kRowThreads, 4) k_rows(RowArgs a)
 {
+    constexpr int kRowGroups = row_groups(ACC);
     grid_dep_wait();
     grid_dep_launch();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x * 4 * kRowGroups;
+    const int64_t first = (int64_t)blockIdx.x * blockDim.x * 4 * kRowGroups + threadIdx.x * 4;
+    const bool need_y = KIND != kRowsUpdate || a.hybrid, need_w = KIND != kRowsUpdate;
+    const bool need_ylo = need_y && a.y_lo != nullptr, load_w = need_w && a.w != nullptr;
+    RowIn in[kRowGroups];
+#pragma unroll
+    for (int u = 0; u < kRowGroups; ++u) {
+        const int64_t i4 = first + (int64_t)u * blockDim.x * 4;
+        if (i4 < a.n_pad) load_row_in<ACC>(a, i4, in[u], need_y);
+    }
     const DevState st = *a.state;
     const bool pend = (KIND != kRowsResid) && (st.m > st.m_applied);
     const int pm = st.pend_mode;
+    const bool pm_acwb = ACC && pm == kModeACWB;
     const IndT* ind = static_cast<const IndT*>(a.ind);
     const IndT* ind_sel = (st.k_sel >= 0) ? ind + (int64_t)a.l_bin[st.k_sel] * a.n_pad : nullptr;
     const IndT* ind_cor = (st.k_cor >= 0) ? ind + (int64_t)a.l_bin[st.k_cor] * a.n_pad : nullptr;
@@ -216,10 +256,10 @@ __global__ void __launch_bounds__(kRowThreads, 4) k_rows(RowArgs a)
     __shared__ DF sc_df[7];
     const int mode_n = st.mode;
     const int m_n = st.m + 1;
-    const bool acwb_n = (mode_n == kModeACWB);
+    const bool acwb_n = ACC && (mode_n == kModeACWB);
     if (threadIdx.x == 0) {
         DF om_p = {1.0f, 0.0f}, th_p = {0.0f, 0.0f}, eta_p = {0.0f, 0.0f};
-        if (pend && pm == kModeACWB) {
+        if (pend && pm_acwb) {
             const double thm = 2.0 / ((double)st.m + 1.0);
             om_p = df_of(1.0 - thm);
             th_p = df_of(thm);
@@ -240,97 +280,110 @@ __global__ void __launch_bounds__(kRowThreads, 4) k_rows(RowArgs a)
     const int64_t n_act = (acwb_n && a.hybrid) ? a.n_tr : a.n;
     const bool first_acwb = (m_n == 1);
     const DF nu = sc_df[6];
-    const bool need_bc = pend && pm == kModeACWB;
+    const bool need_bc = pend && pm_acwb;
     const bool need_bc_resid = (KIND != kRowsUpdate) && acwb_n && !first_acwb;
-    const bool eval_risk = (KIND == kRowsUpdate) && a.hybrid && (!st.risk_valid || (pend && pm == kModeACWB));
+    const bool eval_risk = (KIND == kRowsUpdate) && a.hybrid && (!st.risk_valid || (pend && pm_acwb));
 
     double risk_acc = 0.0;
     float rmax0 = 0.0f, rmax1 = 0.0f;
     bool nonfinite = false;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x * 4;
-    for (int64_t i4 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; i4 < a.n_pad; i4 += stride) {
-        DF fv[4], hv[4];
-        load_df4(a.f, i4, fv);
-        if (a.h) load_df4(a.h, i4, hv);
-        else for (int t = 0; t < 4; ++t) hv[t] = {0.0f, 0.0f};
-        float bc[4] = {0.f, 0.f, 0.f, 0.f};
-        if ((need_bc || need_bc_resid) && ind_cor) {
-            int kc[4];
-            load_ind4<IndT>(ind_cor, i4, kc);
+    for (int64_t p0 = first; p0 < a.n_pad; p0 += stride) {
+        if (p0 != first) {
 #pragma unroll
-            for (int t = 0; t < 4; ++t) bc[t] = __ldg(v1 + kc[t]);
+            for (int u = 0; u < kRowGroups; ++u) {
+                const int64_t i4 = p0 + (int64_t)u * blockDim.x * 4;
+                if (i4 < a.n_pad) load_row_in<ACC>(a, i4, in[u], need_y);
+            }
         }
-        if (pend && ind_sel) {
-            int ks[4];
-            load_ind4<IndT>(ind_sel, i4, ks);
+        // state-dependent loads of the pass: selected bins, then their fitted values
+        int ks[kRowGroups][4], kc[kRowGroups][4];
+        float4 c4in[kRowGroups], yl4in[kRowGroups], w4in[kRowGroups];
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const float b0 = __ldg(v0 + ks[t]);
-                if (pm == kModeCWB) {
-                    fv[t] = df_add(fv[t], df_mul_f(nu, b0));
-                } else {
-                    DF g = df_add(df_mul(fv[t], om_p), df_mul(hv[t], th_p));
-                    fv[t] = df_add(g, df_mul_f(nu, b0));
-                    hv[t] = df_add(hv[t], df_mul_f(eta_p, bc[t]));
+        for (int u = 0; u < kRowGroups; ++u) {
+            const int64_t i4 = p0 + (int64_t)u * blockDim.x * 4;
+            yl4in[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            w4in[u] = make_float4(1.f, 1.f, 1.f, 1.f);
+            if (i4 >= a.n_pad) continue;
+            if ((need_bc || need_bc_resid) && ind_cor) load_ind4<IndT>(ind_cor, i4, kc[u]);
+            if (pend && ind_sel) load_ind4<IndT>(ind_sel, i4, ks[u]);
+            if (KIND != kRowsUpdate && acwb_n) c4in[u] = *reinterpret_cast<const float4*>(a.c + i4);
+            if (need_ylo) yl4in[u] = *reinterpret_cast<const float4*>(a.y_lo + i4);
+            if (load_w) w4in[u] = *reinterpret_cast<const float4*>(a.w + i4);
+        }
+#pragma unroll
+        for (int u = 0; u < kRowGroups; ++u) {
+            const int64_t i4 = p0 + (int64_t)u * blockDim.x * 4;
+            if (i4 >= a.n_pad) continue;
+            DF* fv = in[u].f;
+            DF* hv = in[u].h;
+            float bc[4] = {0.f, 0.f, 0.f, 0.f};
+            if ((need_bc || need_bc_resid) && ind_cor) {
+#pragma unroll
+                for (int t = 0; t < 4; ++t) bc[t] = __ldg(v1 + kc[u][t]);
+            }
+            if (pend && ind_sel) {
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const float b0 = __ldg(v0 + ks[u][t]);
+                    if (!pm_acwb) {
+                        fv[t] = df_add(fv[t], df_mul_f(nu, b0));
+                    } else {
+                        DF g = df_add(df_mul(fv[t], om_p), df_mul(hv[t], th_p));
+                        fv[t] = df_add(g, df_mul_f(nu, b0));
+                        hv[t] = df_add(hv[t], df_mul_f(eta_p, bc[t]));
+                    }
+                }
+                store_df4(a.f, i4, fv);
+                if (pm_acwb && a.h) store_df4(a.h, i4, hv);
+            }
+            const float4 y4 = in[u].y, yl4 = yl4in[u], w4 = w4in[u];
+            if (eval_risk) {
+                if (i4 + 4 > a.n_tr && i4 < a.n) {
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        int64_t i = i4 + t;
+                        if (i >= a.n_tr && i < a.n)
+                            risk_acc += (double)loss_value(a.loss, get4(y4, t), get4(yl4, t), fv[t]);
+                    }
                 }
             }
-            store_df4(a.f, i4, fv);
-            if (pm == kModeACWB && a.h) store_df4(a.h, i4, hv);
-        }
-        if (eval_risk) {
-            if (i4 + 4 > a.n_tr && i4 < a.n) {
-                float4 y4 = *reinterpret_cast<const float4*>(a.y + i4);
-                float4 yl4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (a.y_lo) yl4 = *reinterpret_cast<const float4*>(a.y_lo + i4);
+            if (KIND != kRowsUpdate) {
+                float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
+                float4 c4 = r0;
+                if (acwb_n) c4 = c4in[u];
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
                     int64_t i = i4 + t;
-                    if (i >= a.n_tr && i < a.n)
-                        risk_acc += (double)loss_value(a.loss, get4(y4, t), get4(yl4, t), fv[t]);
-                }
-            }
-        }
-        if (KIND != kRowsUpdate) {
-            float4 y4 = *reinterpret_cast<const float4*>(a.y + i4);
-            float4 yl4 = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (a.y_lo) yl4 = *reinterpret_cast<const float4*>(a.y_lo + i4);
-            float4 w4 = make_float4(1.f, 1.f, 1.f, 1.f);
-            if (a.w) w4 = *reinterpret_cast<const float4*>(a.w + i4);
-            float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
-            float4 c4 = r0;
-            if (acwb_n) c4 = *reinterpret_cast<const float4*>(a.c + i4);
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                int64_t i = i4 + t;
-                if (i >= n_act) continue;
-                float yv = get4(y4, t), ylo = get4(yl4, t), wv = get4(w4, t);
-                if (!acwb_n) {
-                    set4(r0, t, wv * neg_gradient(a.loss, yv, ylo, fv[t]));
-                } else {
-                    DF g = df_add(df_mul(fv[t], om_n), df_mul(hv[t], th_n));
-                    float r = neg_gradient(a.loss, yv, ylo, g);
-                    float cv = r;
-                    if (!first_acwb) {
-                        DF ct = df_mul_f(cmul, get4(c4, t) - bc[t]);
-                        DF cs = df_add(ct, DF{r, 0.0f});
-                        cv = cs.hi + cs.lo;
+                    if (i >= n_act) continue;
+                    float yv = get4(y4, t), ylo = get4(yl4, t), wv = get4(w4, t);
+                    if (!acwb_n) {
+                        set4(r0, t, wv * neg_gradient(a.loss, yv, ylo, fv[t]));
+                    } else {
+                        DF g = df_add(df_mul(fv[t], om_n), df_mul(hv[t], th_n));
+                        float r = neg_gradient(a.loss, yv, ylo, g);
+                        float cv = r;
+                        if (!first_acwb) {
+                            DF ct = df_mul_f(cmul, get4(c4, t) - bc[t]);
+                            DF cs = df_add(ct, DF{r, 0.0f});
+                            cv = cs.hi + cs.lo;
+                        }
+                        set4(c4, t, cv);
+                        set4(r0, t, wv * r);
+                        set4(r1, t, wv * cv);
                     }
-                    set4(c4, t, cv);
-                    set4(r0, t, wv * r);
-                    set4(r1, t, wv * cv);
                 }
-            }
-            const float m0 = fmaxf(fmaxf(fabsf(r0.x), fabsf(r0.y)), fmaxf(fabsf(r0.z), fabsf(r0.w)));
-            const float m1 = fmaxf(fmaxf(fabsf(r1.x), fabsf(r1.y)), fmaxf(fabsf(r1.z), fabsf(r1.w)));
-            if (!(fabsf(r0.x) + fabsf(r0.y) + fabsf(r0.z) + fabsf(r0.w) + fabsf(r1.x) + fabsf(r1.y) + fabsf(r1.z) +
-                  fabsf(r1.w) <= 3.0e38f))
-                nonfinite = true;
-            rmax0 = fmaxf(rmax0, m0);
-            rmax1 = fmaxf(rmax1, m1);
-            *reinterpret_cast<float4*>(a.rw + i4) = r0;
-            if (acwb_n) {
-                *reinterpret_cast<float4*>(a.rw + a.n_pad + i4) = r1;
-                *reinterpret_cast<float4*>(a.c + i4) = c4;
+                const float m0 = fmaxf(fmaxf(fabsf(r0.x), fabsf(r0.y)), fmaxf(fabsf(r0.z), fabsf(r0.w)));
+                const float m1 = fmaxf(fmaxf(fabsf(r1.x), fabsf(r1.y)), fmaxf(fabsf(r1.z), fabsf(r1.w)));
+                if (!(fabsf(r0.x) + fabsf(r0.y) + fabsf(r0.z) + fabsf(r0.w) + fabsf(r1.x) + fabsf(r1.y) + fabsf(r1.z) +
+                      fabsf(r1.w) <= 3.0e38f))
+                    nonfinite = true;
+                rmax0 = fmaxf(rmax0, m0);
+                rmax1 = fmaxf(rmax1, m1);
+                *reinterpret_cast<float4*>(a.rw + i4) = r0;
+                if (acwb_n) {
+                    *reinterpret_cast<float4*>(a.rw + a.n_pad + i4) = r1;
+                    *reinterpret_cast<float4*>(a.c + i4) = c4;
+                }
             }
         }
     }
@@ -385,13 +438,13 @@ __global__ void __launch_bounds__(kRowThreads, 4) k_rows(RowArgs a)
     if (threadIdx.x == 0) {
         if (bad_blk) atomicOr(&a.state->err, kErrNonFinite);
         if (eval_risk && a.risk_part) a.risk_part[blockIdx.x] = red[0];
-        __threadfence();
+        fence_acq_rel_gpu();
         unsigned t = atomicAdd(&a.state->ticket_rows, 1u);
         is_last = (t == gridDim.x - 1);
     }
     __syncthreads();
     if (!is_last) return;
-    __threadfence();
+    fence_acq_rel_gpu();
     // last block (update pass): block-parallel, fixed-order reduction of the validation risk partials
     {
         double rs = 0.0;
@@ -875,7 +928,7 @@ __global__ void k_count_log2(DevState* state, int idx)
 // iteration state.
 
 constexpr int kSolveChunk = 1024;      // bins of u held in shared memory per pass
-constexpr int kSolveBatch = 12;        // partial-histogram rows per thread and batch (per channel)
+constexpr int kSolveBatch = 20;        // partial-histogram rows per thread and batch (per channel)
 
 struct SolveArgs {
     DevState* state;
@@ -893,8 +946,8 @@ struct SolveArgs {
     const int32_t* l_bin;
     const int32_t* l_d;
     const int32_t* l_nstar;
-    const double* A;          // [2][K][D][D] criterion matrix P G P - 2 P
-    const double* P;
+    const float2* A;          // [2][K][D][D] criterion matrix P G P - 2 P, float-float pairs
+    const float2* P;          // [2][K][D][D] cached inverse, float-float pairs
     double* theta_it;         // [2][K][D]
     double* q_it;             // [2][K]
     float* v;                 // [2][K][S]
@@ -961,7 +1014,7 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src)
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 template <bool INT_ACC>
-__global__ void __launch_bounds__(kSolveThreads) k_solve(SolveArgs a)
+__global__ void __launch_bounds__(kSolveThreads, 1) k_solve(SolveArgs a)
 {
     constexpr int NW = kSolveThreads / 32;
     constexpr int kColsPerWarp = (kMaxD + NW - 1) / NW;
@@ -973,18 +1026,22 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(SolveArgs a)
     // column per bin), u for one chunk of bins, the second cluster half's partial sums and,
     // when it fits, the column-major design
     extern __shared__ __align__(16) double dsm[];
-    double* Ps = dsm;
-    double* As = Ps + (size_t)D * D;
+    float2* Ps = reinterpret_cast<float2*>(dsm);            // float-float pairs (hi, lo)
+    float2* As = Ps + (size_t)D * D;
     float* u_s = reinterpret_cast<float*>(As + (size_t)D * D);                    // [2][kSolveChunk]
     long long* pb = reinterpret_cast<long long*>(u_s + 2 * kSolveChunk);          // [2][kSolveChunk]
     float4* zb_s = reinterpret_cast<float4*>(pb + 2 * kSolveChunk);              // [nst] when staged
     int* zc_s = reinterpret_cast<int*>(zb_s + (a.stage_v ? S : 0));
     float* zt_s = reinterpret_cast<float*>(zc_s + (a.stage_v ? ((S + 3) & ~3) : 0));   // [4 nst] when staged
-    __shared__ double s_s[2][kMaxD], th_s[2][kMaxD], term[2][kMaxD];
+    __shared__ float s_s[2][kMaxD];
+    __shared__ double th_s[2][kMaxD];
+    __shared__ DF term[2][kMaxD];
     __shared__ bool is_last;
 
-    // ---- static per-learner data (independent of this iteration): asynchronous copies issued
-    // before waiting for the scatter, so they overlap its tail
+    // ---- static per-learner data (independent of this iteration), fetched before waiting for
+    // the scatter so that it overlaps the scatter's tail: the design (asynchronous copies), its
+    // column ranges, the first chunk's cluster range and, when the model never switches caches
+    // (no HCWB), P and A of phase 0
     {
         if (a.stage_v) {
             const float4* zb_g = reinterpret_cast<const float4*>(a.zb) + (int64_t)k * S;
@@ -999,20 +1056,15 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(SolveArgs a)
             for (int e = tid; e < nst; e += blockDim.x) cp_async16(reinterpret_cast<float4*>(zt_s) + e, zt4 + e);
         }
     }
-    grid_dep_wait();                   // histograms and iteration state from here on
-    grid_dep_launch();                 // the next row pass may be scheduled on idle SMs
-    const DevState st = *a.state;
-    const int mode = st.mode;
-    const int C = (mode == kModeACWB) ? 2 : 1;
-    const int ph = (mode == kModeACWB) ? 0 : st.phase;    // P and G of the cache this iteration uses
-    {
-        const double* Pk = a.P + ((int64_t)ph * a.K + k) * D * D;
-        const double* Ak = a.A + ((int64_t)ph * a.K + k) * D * D;
+    auto stage_pa = [&](int ph) {          // P and A of the cache `ph`
+        const float2* Pk = a.P + ((int64_t)ph * a.K + k) * D * D;
+        const float2* Ak = a.A + ((int64_t)ph * a.K + k) * D * D;
         for (int e = tid; e < D * D; e += blockDim.x) {
             cp_async8(Ps + e, Pk + e);
             cp_async8(As + e, Ak + e);
         }
-    }
+    };
+    if (!a.hybrid) stage_pa(0);
     const float* zt = a.stage_z ? zt_s : a.ztab + (int64_t)k * kMaxNnz * S;
     const float4* zbp = a.stage_v ? zb_s : reinterpret_cast<const float4*>(a.zb) + (int64_t)k * S;
     const int* zcp = a.stage_v ? zc_s : a.zcol + (int64_t)k * S;
@@ -1031,28 +1083,15 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(SolveArgs a)
     }
     if (tid < 2 * kMaxD) {
         th_s[tid / kMaxD][tid % kMaxD] = 0.0;
-        s_s[tid / kMaxD][tid % kMaxD] = 0.0;
+        s_s[tid / kMaxD][tid % kMaxD] = 0.0f;
     }
-
-    // ---- u = sum of the slot's partial histograms, then s = Z^b^T u, in chunks of bins.
-    // Thread (i, half): bins 4i..4i+3 of the chunk, clusters of parity `half`.
+    // Thread (i, half) sums bins 4i..4i+3 of a chunk over the clusters of parity `half`; the
+    // clusters holding a bin are those of its slot (binning group x bin range)
     const int g = b / a.FE, f = b - g * a.FE;
-    const int64_t cl_stride = (int64_t)a.cmax * a.F * a.nb_cta;
-    const int cidx = (a.hybrid && mode == kModeACWB) ? 1 : 0;
-    float scl0 = 1.0f, scl1 = 1.0f;
-    if (INT_ACC) {
-        scl0 = pow2f(-fixed_scale(st.rmax_bits[0], st.cnt_log2[cidx]));
-        scl1 = pow2f(-fixed_scale(st.rmax_bits[1], st.cnt_log2[cidx]));
-    }
     const int gi = tid & (kSolveThreads / 2 - 1), half = tid / (kSolveThreads / 2);
-    float acc0[kColsPerWarp], acc1[kColsPerWarp];
-#pragma unroll
-    for (int c = 0; c < kColsPerWarp; ++c) acc0[c] = acc1[c] = 0.0f;
-    for (int L0 = 0; L0 < nst; L0 += kSolveChunk) {
-        const int L1 = min(nst, L0 + kSolveChunk);
-        const bool mine = 4 * gi < L1 - L0;
-        int c0 = 0, c1 = 0, lb = 0;
-        if (mine) {
+    auto chunk_clusters = [&](int L0, int L1, int& c0, int& c1, int& lb) {
+        c0 = c1 = lb = 0;
+        if (4 * gi < L1 - L0) {
             const int l0 = L0 + 4 * gi;
             const int br = l0 / a.nb_cta;
             lb = l0 - br * a.nb_cta;
@@ -1060,13 +1099,35 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(SolveArgs a)
             c0 = __ldg(a.slot_c0 + slot);
             c1 = __ldg(a.slot_c0 + slot + 1);
         }
+    };
+    int c0n, c1n, lbn;
+    chunk_clusters(0, min(nst, kSolveChunk), c0n, c1n, lbn);
+
+    grid_dep_wait();                   // histograms and iteration state from here on
+    grid_dep_launch();                 // the next row pass may be scheduled on idle SMs
+    const DevState st = *a.state;      // first used once the first chunk's loads are in flight
+    const int mode = st.mode;
+    // without HCWB the channel count never changes (CWB one, ACWB two) and needs no state
+    const int C = a.hybrid ? ((mode == kModeACWB) ? 2 : 1) : a.cmax;
+    if (a.hybrid) stage_pa((mode == kModeACWB) ? 0 : st.phase);
+
+    // ---- u = sum of the slot's partial histograms, then s = Z^b^T u, in chunks of bins
+    const int64_t cl_stride = (int64_t)a.cmax * a.F * a.nb_cta;
+    float acc0[kColsPerWarp], acc1[kColsPerWarp];
+#pragma unroll
+    for (int c = 0; c < kColsPerWarp; ++c) acc0[c] = acc1[c] = 0.0f;
+    for (int L0 = 0; L0 < nst; L0 += kSolveChunk) {
+        const int L1 = min(nst, L0 + kSolveChunk);
+        const bool mine = 4 * gi < L1 - L0;
+        int c0 = c0n, c1 = c1n, lb = lbn;
+        if (L0 > 0) chunk_clusters(L0, L1, c0, c1, lb);
         long long it0[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
         float ft[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
         float fc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
         for (int cc = c0 + half; cc < c1; cc += 2 * kSolveBatch) {
 #pragma unroll
             for (int ch = 0; ch < 2; ++ch) {
-                if (ch >= C) break;
+                if (ch < C) {           // a guard, not a break: the loop stays unrolled, the sums in registers
                 const float* base = a.part + ((int64_t)ch * a.F + f) * a.nb_cta + lb;
                 int4 x[kSolveBatch];
 #pragma unroll
@@ -1090,6 +1151,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(SolveArgs a)
                         }
                     }
                 }
+                }
             }
         }
         // the odd-cluster half hands its sums to the even half
@@ -1098,16 +1160,23 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(SolveArgs a)
             for (int ch = 0; ch < 2; ++ch)
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
-                    if (ch >= C) break;
+                    if (ch >= C) continue;
                     if (INT_ACC) pb[ch * kSolveChunk + 4 * gi + t] = it0[ch][t];
                     else reinterpret_cast<float*>(pb)[ch * kSolveChunk + 4 * gi + t] = ft[ch][t] - fc[ch][t];
                 }
         }
         __syncthreads();
         if (half == 0 && mine) {
+            float scl0 = 1.0f, scl1 = 1.0f;
+            if (INT_ACC) {
+                // (selects, not an index: a run-time index into the state copy would put it in local memory)
+                const int cl2 = (a.hybrid && mode == kModeACWB) ? st.cnt_log2[1] : st.cnt_log2[0];
+                scl0 = pow2f(-fixed_scale(st.rmax_bits[0], cl2));
+                scl1 = pow2f(-fixed_scale(st.rmax_bits[1], cl2));
+            }
 #pragma unroll
             for (int ch = 0; ch < 2; ++ch) {
-                if (ch >= C) break;
+                if (ch >= C) continue;
                 float o[4];
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
@@ -1143,41 +1212,52 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(SolveArgs a)
         if (C == 2)
             for (int o = 16; o > 0; o >>= 1) acc1[c] += __shfl_xor_sync(0xffffffffu, acc1[c], o);
         if (lane == 0) {
-            s_s[0][j] = (double)acc0[c];
-            s_s[1][j] = (double)acc1[c];
+            s_s[0][j] = acc0[c];
+            s_s[1][j] = acc1[c];
         }
     }
     __syncthreads();
 
-    // ---- theta = P s and t = A s together (FP64): four lanes per row, partial sums over j = q mod 4;
-    // the criterion Q = theta^T G theta - 2 theta^T s = s^T A s = s . t
-    const int rows4 = C * d * 4;
-    for (int base = 0; base < 2 * rows4; base += blockDim.x) {
+    // ---- theta = P s and t = A s together in float-float arithmetic (s is an FP32 vector; P and A
+    // are float-float pairs, so every product and sum carries about 44 bits and the FP64 pipe,
+    // a small fraction of the FP32 rate here, stays out of the loop): eight lanes per row,
+    // partial sums over j = q mod 8.  The criterion Q = theta^T G theta - 2 theta^T s = s^T A s = s . t
+    const int rows8 = C * d * 8;
+    for (int base = 0; base < 2 * rows8; base += blockDim.x) {
         const int e = base + tid;
-        const bool valid = e < 2 * rows4;
-        const int mat = valid && e >= rows4 ? 1 : 0;
-        const int r = e - mat * rows4;
-        const int ch = valid ? r / (4 * d) : 0;
-        const int rem = r - ch * 4 * d;
-        const int i = rem >> 2, q = rem & 3;
-        const double* Mx = mat ? As : Ps;
-        double p = 0.0;
+        const bool valid = e < 2 * rows8;
+        const int mat = valid && e >= rows8 ? 1 : 0;
+        const int r = e - mat * rows8;
+        const int ch = valid ? r / (8 * d) : 0;
+        const int rem = r - ch * 8 * d;
+        const int i = rem >> 3, q = rem & 7;
+        const float2* Mx = mat ? As : Ps;
+        DF p = {0.0f, 0.0f};
         if (valid)
-            for (int j = q; j < d; j += 4) p = fma(Mx[i * D + j], s_s[ch][j], p);
-        p += __shfl_xor_sync(0xffffffffu, p, 1);
-        p += __shfl_xor_sync(0xffffffffu, p, 2);
+            for (int j = q; j < d; j += 8) {
+                const float2 mij = Mx[i * D + j];
+                p = df_add(p, df_mul_f(DF{mij.x, mij.y}, s_s[ch][j]));
+            }
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            const DF other = {__shfl_xor_sync(0xffffffffu, p.hi, o), __shfl_xor_sync(0xffffffffu, p.lo, o)};
+            p = df_add(p, other);
+        }
         if (valid && q == 0) {
-            if (mat) term[ch][i] = s_s[ch][i] * p;
-            else th_s[ch][i] = p;
+            if (mat) term[ch][i] = df_mul_f(p, s_s[ch][i]);
+            else th_s[ch][i] = (double)p.hi + (double)p.lo;
         }
     }
     __syncthreads();
     if (warp < C) {
         // Q = sum_i s_i t_i: fixed-order tree over the warp
-        double x = 0.0;
-        for (int i = lane; i < d; i += 32) x += term[warp][i];
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-        if (lane == 0) a.q_it[(int64_t)warp * a.K + k] = x;
+        DF x = {0.0f, 0.0f};
+        for (int i = lane; i < d; i += 32) x = df_add(x, term[warp][i]);
+        for (int o = 16; o > 0; o >>= 1) {
+            const DF other = {__shfl_xor_sync(0xffffffffu, x.hi, o), __shfl_xor_sync(0xffffffffu, x.lo, o)};
+            x = df_add(x, other);
+        }
+        if (lane == 0) a.q_it[(int64_t)warp * a.K + k] = (double)x.hi + (double)x.lo;
     }
     for (int e = tid; e < C * D; e += blockDim.x) {
         const int ch = e / D, i = e - (e / D) * D;
@@ -1197,42 +1277,44 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(SolveArgs a)
     }
     __syncthreads();
     if (tid == 0) {
-        __threadfence();
+        fence_acq_rel_gpu();
         unsigned t = atomicAdd(&a.state->ticket_solve, 1u);
         is_last = (t == gridDim.x - 1);
     }
     __syncthreads();
-    if (!is_last) return;
-    __threadfence();
-    // ---- last CTA: argmin per channel, trace, state
-    __shared__ Best2 cand[2][NW];
-    __shared__ uint32_t bad;
-    if (tid == 0) bad = 0;
-    __syncthreads();
+    // ---- last CTA: argmin per channel, trace, state -- one warp (no block barriers on the
+    // iteration's critical path)
+    if (!is_last || warp != 0) return;
+    fence_acq_rel_gpu();
     const long long kInf = order_key(INFINITY);
-    for (int ch = 0; ch < C; ++ch) {
+    Best2 cand[2] = {{kInf, kInf, -1}, {kInf, kInf, -1}};
+    bool bad = false;
+#pragma unroll
+    for (int ch = 0; ch < 2; ++ch) {
+        if (ch >= C) continue;
         Best2 x = {kInf, kInf, -1};
-        for (int kk = tid; kk < a.K; kk += blockDim.x) {
+        for (int kk = lane; kk < a.K; kk += 32) {
             const double q = __ldcg(a.q_it + (int64_t)ch * a.K + kk);
             long long key = q == 0.0 ? 0LL : order_key(q);                                 // -0 ties with +0
             if ((__double_as_longlong(q) & 0x7ff0000000000000LL) == 0x7ff0000000000000LL) {   // inf or NaN
-                atomicOr(&bad, 1u);
+                bad = true;
                 key = kInf;
             }
             x = best2_merge(x, Best2{key, kInf, kk});
         }
         for (int o = 16; o > 0; o >>= 1) x = best2_merge(x, best2_shfl(x, o));
-        if (lane == 0) cand[ch][warp] = x;
+        cand[ch] = x;
     }
-    __syncthreads();
-    if (tid == 0) {
+    bad = __any_sync(0xffffffffu, bad);
+    if (lane == 0) {
         const int it = st.m;
         const bool trace_ok = it < a.trace_cap;
         DevState* S_ = a.state;
         int best_k[2] = {-1, -1};
-        for (int ch = 0; ch < C; ++ch) {
-            Best2 x = cand[ch][0];
-            for (int w = 1; w < NW; ++w) x = best2_merge(x, cand[ch][w]);
+#pragma unroll
+        for (int ch = 0; ch < 2; ++ch) {
+            if (ch >= C) continue;
+            const Best2 x = cand[ch];
             int i1 = x.k1 < 0 ? 0 : x.k1;
             if (ch == 0 && trace_ok && a.forced) {
                 const int fk = a.forced[it];
@@ -1296,7 +1378,7 @@ int num_sms(int device)
 
 int rows_grid(const cwb_model* m)
 {
-    int64_t g = (m->n_pad / 4 + kRowThreads - 1) / kRowThreads;
+    int64_t g = (m->n_pad / (4 * row_groups(m->accel)) + kRowThreads - 1) / kRowThreads;
     int64_t cap = (int64_t)num_sms(m->device) * 4;
     return (int)std::max<int64_t>(1, std::min(g, cap));
 }
@@ -1346,8 +1428,13 @@ void launch_rows(cwb_model* m, cudaStream_t s)
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = m->use_pdl ? 1 : 0;
-    if (m->ind_bytes == 1) cudaLaunchKernelEx(&cfg, k_rows<KIND, uint8_t>, a);
-    else cudaLaunchKernelEx(&cfg, k_rows<KIND, uint16_t>, a);
+    if (m->accel) {
+        if (m->ind_bytes == 1) cudaLaunchKernelEx(&cfg, k_rows<KIND, uint8_t, true>, a);
+        else cudaLaunchKernelEx(&cfg, k_rows<KIND, uint16_t, true>, a);
+    } else {
+        if (m->ind_bytes == 1) cudaLaunchKernelEx(&cfg, k_rows<KIND, uint8_t, false>, a);
+        else cudaLaunchKernelEx(&cfg, k_rows<KIND, uint16_t, false>, a);
+    }
 }
 
 template <typename IndT, int CMAX, bool INT_ACC>
@@ -1431,7 +1518,7 @@ void launch_scatter(cwb_model* m, cudaStream_t s)
 size_t solve_smem(const cwb_model* m, bool stage_v, bool stage_z)
 {
     const size_t S = m->nstar_max;
-    size_t b = sizeof(double) * 2 * (size_t)m->d_max * m->d_max;        // P, G
+    size_t b = sizeof(float2) * 2 * (size_t)m->d_max * m->d_max;        // P, A (float-float pairs)
     b += sizeof(float) * 2 * kSolveChunk + sizeof(long long) * 2 * kSolveChunk;   // u chunk, half sums
     if (stage_v) b += 16 * S + 4 * ((S + 3) & ~size_t(3));              // design rows, first columns
     if (stage_z) b += sizeof(float) * kMaxNnz * S;                       // column-major design
@@ -1464,8 +1551,8 @@ void launch_solve(cwb_model* m, cudaStream_t s)
     a.l_bin = m->l_bin;
     a.l_d = m->l_d;
     a.l_nstar = m->l_nstar;
-    a.A = m->Acrit;
-    a.P = m->P;
+    a.A = m->Adf;
+    a.P = m->Pdf;
     a.theta_it = m->theta_it;
     a.q_it = m->q_it;
     a.v = m->v;

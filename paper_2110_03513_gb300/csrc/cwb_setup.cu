@@ -706,6 +706,17 @@ __global__ void __launch_bounds__(kLamThreads) k_lambda(LamArgs a)
     }
 }
 
+// FP64 values as float-float pairs: hi = x rounded to FP32, lo = (x - hi) rounded (the solve
+// evaluates its matrix products on the FP32 pipes; FP64 is a small fraction of the FP32 rate).
+__global__ void k_split_df(const double* __restrict__ x, int64_t n, float2* __restrict__ out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = x[i];
+        const float hi = __double2float_rn(v);
+        out[i] = make_float2(hi, __double2float_rn(v - (double)hi));
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Offset: loss-optimal constant over the fitting rows (L2: weighted mean,
 // binomial: logit of the weighted mean).
@@ -1120,6 +1131,8 @@ cwb_status setup_model(cwb_model* m, const void* X_in, int x_dtype, const void* 
     CWB_TRY(dev_alloc((void**)&m->G, sizeof(double) * 2 * K * dd, s));
     CWB_TRY(dev_alloc((void**)&m->P, sizeof(double) * 2 * K * dd, s));
     CWB_TRY(dev_alloc((void**)&m->Acrit, sizeof(double) * 2 * K * dd, s));
+    CWB_TRY(dev_alloc((void**)&m->Pdf, sizeof(float2) * 2 * K * dd, s));
+    CWB_TRY(dev_alloc((void**)&m->Adf, sizeof(float2) * 2 * K * dd, s));
     CWB_TRY(dev_alloc((void**)&m->lambda, sizeof(double) * 2 * K, s));
     int32_t* lstat = nullptr;
     CWB_TRY(tmp.get(&lstat, (size_t)2 * K, s));
@@ -1136,6 +1149,9 @@ cwb_status setup_model(cwb_model* m, const void* X_in, int x_dtype, const void* 
             CWB_CUDA_TRY(cudaMemcpyAsync(m->lambda + K, m->lambda, sizeof(double) * K, cudaMemcpyDeviceToDevice, s));
             CWB_CUDA_TRY(cudaMemsetAsync(lstat + K, 0, sizeof(int32_t) * K, s));
         }
+        const int gs = (int)std::min<int64_t>(1024, ((int64_t)2 * K * dd + kThreads - 1) / kThreads);
+        k_split_df<<<gs, kThreads, 0, s>>>(m->P, (int64_t)2 * K * dd, m->Pdf);
+        k_split_df<<<gs, kThreads, 0, s>>>(m->Acrit, (int64_t)2 * K * dd, m->Adf);
     }
     CWB_CUDA_TRY(cudaGetLastError());
     std::vector<int32_t> lstat_h(2 * K);
