@@ -86,9 +86,10 @@ def parse_args():
     ap.add_argument("--batched-fits", type=int, default=512,
                     help="fits in the batched measurement (the first of the 512 seeded specs)")
     ap.add_argument("--served-requests", type=int, default=96, help="requests in the served measurement")
-    ap.add_argument("--workload", choices=["binned_l2", "hcwb_binomial"], default="binned_l2",
+    ap.add_argument("--workload", choices=["binned_l2", "hcwb_binomial", "mise"], default="binned_l2",
                     help="binned_l2: the headline line (n=1M, p=50); hcwb_binomial: ACWB with the hybrid "
-                         "switch, binomial loss, n=2M, p=200, n*=1414 (a separate line)")
+                         "switch, binomial loss, n=2M, p=200, n*=1414 (a separate line); mise: estimation "
+                         "quality of partial effects on paper-style simulated data (a separate line)")
     return ap.parse_args()
 
 
@@ -616,12 +617,112 @@ def run_hcwb(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------------------------
+# Estimation quality of partial effects (Sec. 4.1.1-4.1.2, H2/H3; App. B.3 for n* = n^(1/4) and
+# df in {5, 7, 9}).  MISE = (1/p) sum_j int_{min x_j}^{max x_j} (b_j(x, theta_j) - b_j(x, theta_hat_j))^2 dx
+# over the informative features, at the iteration chosen by early stopping on a large noise-free
+# validation set (the paper's protocol).  Partial effects are identified up to a constant (the offset
+# absorbs it), so both curves are centred at their mean over [min x_j, max x_j] before differencing.
+
+def partial_effect_mise(model, data, grid_points: int = 801) -> float:
+    """MISE of the fitted partial effects against the generator's true effects, from predictions
+    through the public API on a grid per informative feature (the other features at their medians)."""
+    import numpy as np
+    import synthetic_inputs as S
+    trapz = getattr(np, "trapezoid", None) or np.trapz
+    ref = np.median(data.X, axis=1)
+    total = 0.0
+    for j, truth_j in enumerate(data.truth):
+        lo, hi = float(data.X[j].min()), float(data.X[j].max())
+        g = np.linspace(lo, hi, grid_points)
+        Xg = np.repeat(ref[:, None], grid_points, axis=1)
+        Xg[j] = g
+        est = model.predict(np.ascontiguousarray(Xg)).astype(np.float64)
+        true = S.paper_style_effect(truth_j, g)
+        dlt = (est - trapz(est, g) / (hi - lo)) - (true - trapz(true, g) / (hi - lo))
+        total += float(trapz(dlt * dlt, g))
+    return total / len(data.truth)
+
+
+def mise_fit(cwb, data, val, *, nbins: int, df: float, opt: int, nu: float = 0.05, gamma: float = 0.001,
+             chunk: int = 25, max_iter: int = 6000, patience: int = 8, val_mask=None, device: int = 0) -> dict:
+    """Fit one model on paper-style data with early stopping on the noise-free rows `val`; returns the
+    stopping iteration, the validation MSE there and the MISE of the partial effects there."""
+    import numpy as np
+    p = data.X.shape[0]
+    learners = [cwb.learner(j, n_bins=nbins, df=df) for j in range(p)]
+    model = cwb.Model(np.ascontiguousarray(data.X), data.y, learners, opt=opt, nu=nu, gamma=gamma,
+                      patience=5, val_mask=val_mask, device=device)
+    Xv = np.ascontiguousarray(val.X)
+    best = (np.inf, 0, np.nan)
+    since = 0
+    done = 0
+    while done < max_iter and since < patience:
+        model.fit(chunk)
+        done += chunk
+        mse = float(np.mean((model.predict(Xv).astype(np.float64) - val.y) ** 2))
+        if mse < best[0]:
+            best = (mse, done, partial_effect_mise(model, data))
+            since = 0
+        else:
+            since += 1
+    model.free()
+    return {"stop_iter": best[1], "val_mse": best[0], "mise": best[2]}
+
+
+def mise_cases(cwb, *, ns=(5_000, 20_000, 50_000), snrs=(1.0, 10.0), p: int = 5, p_noise: int = 5,
+               seed: int = 11, dfs=(5.0, 7.0, 9.0), gammas=(1e-1, 1e-2, 1e-3, 1e-4)) -> list:
+    """The harness grid: for every (n, SNR), on one truth per SNR (the same effects at every n):
+    exact binning (n* = number of unique values, i.e. no binning) and n* = floor(n^(1/2)) and
+    floor(n^(1/4)) for each df (CWB), ACWB for each momentum gamma and HCWB (gamma = 1e-3) at
+    n* = floor(n^(1/2)), df = 5."""
+    import math
+    import numpy as np
+    import synthetic_inputs as S
+    rows = []
+    for n in ns:
+        for snr in snrs:
+            data = S.paper_style_simulation(n, p, p_noise, snr, seed=seed + int(snr))
+            val = S.paper_style_sample(data.truth, p_noise, 100_000, seed=seed + 100)
+            sq, qu = math.isqrt(n), int(math.floor(n ** 0.25 + 1e-9))
+            specs = [("exact", cwb.BINS_EXACT, 5.0, cwb.OPT_CWB, 0.0)]
+            specs += [(f"sqrt df{int(df)}", sq, df, cwb.OPT_CWB, 0.0) for df in dfs]
+            specs += [(f"quarter df{int(df)}", qu, df, cwb.OPT_CWB, 0.0) for df in dfs]
+            specs += [(f"sqrt ACWB gamma {g:g}", sq, 5.0, cwb.OPT_ACWB, g) for g in gammas]
+            specs += [("sqrt HCWB gamma 0.001", sq, 5.0, cwb.OPT_HCWB, 1e-3)]
+            vm = (np.random.default_rng(seed).random(n) < 0.2).astype(np.uint8)
+            for name, nb, df, opt, g in specs:
+                r = mise_fit(cwb, data, val, nbins=nb, df=df, opt=opt, gamma=g,
+                             val_mask=vm if opt == cwb.OPT_HCWB else None)
+                rows.append({"n": n, "snr": snr, "variant": name, "nstar": nb if nb > 0 else n, "df": df,
+                             "gamma": g, **r})
+    return rows
+
+
+def run_mise(args):
+    import __graft_entry__ as g
+    g.build()
+    import paper_2110_03513_gb300 as cwb
+    t0 = time.perf_counter()
+    rows = mise_cases(cwb)
+    line = {"metric": "MISE of partial effects (paper-style simulation, early stopping on noise-free data)",
+            "unit": "MISE", "higher_is_better": False, "data": "synthetic", "n_gpus": 1,
+            "config": {"workload": "paper-style simulation (Sec. 4.1.1): p=5 informative random cubic-spline "
+                                   "effects on U[a, a+b] ranges, 5 N(0,1) noise features, Gaussian noise at "
+                                   "SNR 1 and 10; nu=0.05; stopping on 100,000 noise-free rows, checked every "
+                                   "25 iterations, patience 8 checks"},
+            "cases": rows, "wall_s": time.perf_counter() - t0}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "hcwb_binomial":
         run_hcwb(args)
+    elif args.workload == "mise":
+        run_mise(args)
     else:
         run_ours(args)
 

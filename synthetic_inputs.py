@@ -30,6 +30,8 @@ __all__ = [
     "served_request_stream",
     "request_dataset",
     "paper_style_simulation",
+    "paper_style_effect",
+    "paper_style_sample",
 ]
 
 
@@ -41,6 +43,7 @@ class Dataset:
     y: np.ndarray            # shape (n,), same dtype as X
     val_mask: np.ndarray | None = None   # shape (n,), uint8 (1 = validation row)
     eta: np.ndarray | None = None        # noise-free additive signal (float64)
+    truth: list | None = None            # generator parameters of the true effects (paper-style data)
     description: str = ""
 
     @property
@@ -224,6 +227,20 @@ def request_dataset(spec: dict, dtype=np.float32) -> Dataset:
                    description=f"request n={n} p={p} seed={seed}")
 
 
+def paper_style_effect(truth_j: tuple, x: np.ndarray) -> np.ndarray:
+    """True effect of one informative feature of :func:`paper_style_simulation` at x.
+
+    ``truth_j = (lo, hi, tau)``: a cubic spline on [lo, hi] with 10 equidistant inner knots in the
+    truncated-power basis (1, u, u^2, u^3, ((x - kappa_i)_+ / (hi - lo))^3), u = (x - lo) / (hi - lo).
+    """
+    lo, hi, tau = truth_j
+    width = max(hi - lo, 1e-12)
+    knots = np.linspace(lo, hi, 12)[1:-1]
+    u = (x - lo) / width
+    cols = [np.ones_like(x), u, u ** 2, u ** 3] + [np.clip((x - k) / width, 0, None) ** 3 for k in knots]
+    return np.stack(cols, 1) @ tau
+
+
 def paper_style_simulation(n: int, p: int, p_noise: int, snr: float, seed: int) -> Dataset:
     """Variant following Sec. 4.1.1 literally: feature ranges drawn from U[0,100],
     effects are random splines (cubic, 10 inner knots, coefficients N(0, 9)),
@@ -231,23 +248,37 @@ def paper_style_simulation(n: int, p: int, p_noise: int, snr: float, seed: int) 
 
     The spline effects are drawn with a truncated-power cubic basis on the
     feature's own range, which spans the same function space as the paper's
-    order-4 B-spline basis with 10 inner knots (14 coefficients).
+    order-4 B-spline basis with 10 inner knots (14 coefficients).  ``truth``
+    holds (lo, hi, tau) per informative feature (see :func:`paper_style_effect`).
     """
     rng = np.random.Generator(np.random.PCG64(seed))
-    X = np.empty((p + p_noise, n), dtype=np.float64)
-    eta = np.zeros(n)
-    for j in range(p):
+    truth = []
+    for j in range(p):             # the truth first: the same seed gives the same effects at every n
         lo = rng.uniform(0, 100)
         hi = lo + rng.uniform(0, 100)
-        x = rng.uniform(lo, hi, n)
-        X[j] = x
-        knots = np.linspace(lo, hi, 12)[1:-1]
-        u = (x - lo) / max(hi - lo, 1e-12)
-        cols = [np.ones(n), u, u ** 2, u ** 3] + [np.clip((x - k) / max(hi - lo, 1e-12), 0, None) ** 3
-                                                 for k in knots]
-        tau = rng.normal(0.0, 3.0, len(cols))
-        eta += np.stack(cols, 1) @ tau
+        truth.append((lo, hi, rng.normal(0.0, 3.0, 14)))
+    X = np.empty((p + p_noise, n), dtype=np.float64)
+    eta = np.zeros(n)
+    for j, (lo, hi, tau) in enumerate(truth):
+        X[j] = rng.uniform(lo, hi, n)
+        eta += paper_style_effect(truth[j], X[j])
     if p_noise:
         X[p:] = rng.standard_normal((p_noise, n))
     y = eta + rng.standard_normal(n) * (float(np.std(eta)) / snr)
-    return Dataset(X=X, y=y, eta=eta, description=f"paper-style sim n={n} p={p} noise={p_noise} snr={snr}")
+    return Dataset(X=X, y=y, eta=eta, truth=truth,
+                   description=f"paper-style sim n={n} p={p} noise={p_noise} snr={snr}")
+
+
+def paper_style_sample(truth: list, p_noise: int, n: int, seed: int) -> Dataset:
+    """Fresh noise-free rows from the truth of :func:`paper_style_simulation` (y = eta): the large
+    validation set of the paper's early stopping (Sec. 4.1.1)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    p = len(truth)
+    X = np.empty((p + p_noise, n), dtype=np.float64)
+    eta = np.zeros(n)
+    for j, (lo, hi, tau) in enumerate(truth):
+        X[j] = rng.uniform(lo, hi, n)
+        eta += paper_style_effect(truth[j], X[j])
+    if p_noise:
+        X[p:] = rng.standard_normal((p_noise, n))
+    return Dataset(X=X, y=eta.copy(), eta=eta, truth=truth, description=f"paper-style noise-free sample n={n}")
