@@ -1238,7 +1238,7 @@ __global__ void __launch_bounds__(kSolveThreads, 1) k_solve(SolveArgs a)
                 const float2 mij = Mx[i * D + j];
                 p = df_add(p, df_mul_f(DF{mij.x, mij.y}, s_s[ch][j]));
             }
-#pragma unroll
+#pragma unroll 1
         for (int o = 1; o < 8; o <<= 1) {
             const DF other = {__shfl_xor_sync(0xffffffffu, p.hi, o), __shfl_xor_sync(0xffffffffu, p.lo, o)};
             p = df_add(p, other);
@@ -1249,15 +1249,31 @@ __global__ void __launch_bounds__(kSolveThreads, 1) k_solve(SolveArgs a)
         }
     }
     __syncthreads();
-    if (warp < C) {
-        // Q = sum_i s_i t_i: fixed-order tree over the warp
-        DF x = {0.0f, 0.0f};
-        for (int i = lane; i < d; i += 32) x = df_add(x, term[warp][i]);
-        for (int o = 16; o > 0; o >>= 1) {
-            const DF other = {__shfl_xor_sync(0xffffffffu, x.hi, o), __shfl_xor_sync(0xffffffffu, x.lo, o)};
-            x = df_add(x, other);
+    if (warp == 0) {
+        // Q = sum_i s_i t_i per channel: fixed-order tree over the warp.  The criteria are all
+        // the argmin needs, so the ticket is taken right after they are stored and its round
+        // trip overlaps the update table below.
+        double qv[2] = {0.0, 0.0};
+#pragma unroll
+        for (int ch = 0; ch < 2; ++ch) {
+            if (ch >= C) continue;
+            DF x = {0.0f, 0.0f};
+#pragma unroll 1
+            for (int i = lane; i < d; i += 32) x = df_add(x, term[ch][i]);
+#pragma unroll 1
+            for (int o = 16; o > 0; o >>= 1) {
+                const DF other = {__shfl_xor_sync(0xffffffffu, x.hi, o), __shfl_xor_sync(0xffffffffu, x.lo, o)};
+                x = df_add(x, other);
+            }
+            qv[ch] = (double)x.hi + (double)x.lo;
         }
-        if (lane == 0) a.q_it[(int64_t)warp * a.K + k] = (double)x.hi + (double)x.lo;
+        if (lane == 0) {
+            a.q_it[k] = qv[0];
+            if (C == 2) a.q_it[(int64_t)a.K + k] = qv[1];
+            fence_acq_rel_gpu();
+            const unsigned t = atomicAdd(&a.state->ticket_solve, 1u);
+            is_last = (t == gridDim.x - 1);
+        }
     }
     for (int e = tid; e < C * D; e += blockDim.x) {
         const int ch = e / D, i = e - (e / D) * D;
@@ -1275,16 +1291,11 @@ __global__ void __launch_bounds__(kSolveThreads, 1) k_solve(SolveArgs a)
         if (c0 + 3 < D) acc = fmaf(z.w, (float)th_s[ch][c0 + 3], acc);
         a.v[((int64_t)ch * a.K + k) * S + l] = acc;
     }
-    __syncthreads();
-    if (tid == 0) {
-        fence_acq_rel_gpu();
-        unsigned t = atomicAdd(&a.state->ticket_solve, 1u);
-        is_last = (t == gridDim.x - 1);
-    }
-    __syncthreads();
     // ---- last CTA: argmin per channel, trace, state -- one warp (no block barriers on the
     // iteration's critical path)
-    if (!is_last || warp != 0) return;
+    if (warp != 0) return;
+    __syncwarp();
+    if (!is_last) return;
     fence_acq_rel_gpu();
     const long long kInf = order_key(INFINITY);
     Best2 cand[2] = {{kInf, kInf, -1}, {kInf, kInf, -1}};
@@ -1293,15 +1304,31 @@ __global__ void __launch_bounds__(kSolveThreads, 1) k_solve(SolveArgs a)
     for (int ch = 0; ch < 2; ++ch) {
         if (ch >= C) continue;
         Best2 x = {kInf, kInf, -1};
-        for (int kk = lane; kk < a.K; kk += 32) {
-            const double q = __ldcg(a.q_it + (int64_t)ch * a.K + kk);
-            long long key = q == 0.0 ? 0LL : order_key(q);                                 // -0 ties with +0
-            if ((__double_as_longlong(q) & 0x7ff0000000000000LL) == 0x7ff0000000000000LL) {   // inf or NaN
-                bad = true;
-                key = kInf;
+#pragma unroll 1
+        for (int k0 = 0; k0 < a.K; k0 += 4 * 32) {
+            long long qb[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {       // the loads of a pass issued together
+                const int kk = k0 + 32 * t + lane;
+                qb[t] = kk < a.K ? __ldcg(reinterpret_cast<const long long*>(a.q_it) + (int64_t)ch * a.K + kk) : 0LL;
             }
-            x = best2_merge(x, Best2{key, kInf, kk});
+            // a rolled loop: this code runs once per iteration on one SM, where every line of it
+            // is an instruction-cache miss, so it is kept short
+#pragma unroll 1
+            for (int t = 0; t < 4; ++t) {
+                const int kk = k0 + 32 * t + lane;
+                if (kk >= a.K) continue;
+                const long long qt = t == 0 ? qb[0] : (t == 1 ? qb[1] : (t == 2 ? qb[2] : qb[3]));
+                // integer tests only: -0 ties with +0, inf and NaN are flagged
+                long long key = (qt & 0x7fffffffffffffffLL) == 0 ? 0LL : order_key(__longlong_as_double(qt));
+                if ((qt & 0x7ff0000000000000LL) == 0x7ff0000000000000LL) {
+                    bad = true;
+                    key = kInf;
+                }
+                x = best2_merge(x, Best2{key, kInf, kk});
+            }
         }
+#pragma unroll 1
         for (int o = 16; o > 0; o >>= 1) x = best2_merge(x, best2_shfl(x, o));
         cand[ch] = x;
     }
