@@ -66,6 +66,7 @@ struct RowArgs {
     int trace_cap;
     int loss;
     double nu, gamma;
+    float nu_hi, nu_lo;       // nu as a float-float pair (rounded on the host)
     int hybrid;
     int patience;
     double* risk_part;
@@ -257,7 +258,7 @@ __global__ void __launch_bounds__(kRowThreads, 4) k_rows(RowArgs a)
     const int mode_n = st.mode;
     const int m_n = st.m + 1;
     const bool acwb_n = ACC && (mode_n == kModeACWB);
-    if (threadIdx.x == 0) {
+    if (ACC && threadIdx.x == 0) {     // plain CWB needs none of these (and no FP64 divisions)
         DF om_p = {1.0f, 0.0f}, th_p = {0.0f, 0.0f}, eta_p = {0.0f, 0.0f};
         if (pend && pm_acwb) {
             const double thm = 2.0 / ((double)st.m + 1.0);
@@ -272,14 +273,14 @@ __global__ void __launch_bounds__(kRowThreads, 4) k_rows(RowArgs a)
         sc_df[3] = df_of(1.0 - thn_d);
         sc_df[4] = df_of(thn_d);
         sc_df[5] = df_of((double)m_n / ((double)m_n + 1.0));
-        sc_df[6] = df_of(a.nu);
     }
-    __syncthreads();
-    const DF om_p = sc_df[0], th_p = sc_df[1], eta_p = sc_df[2];
-    const DF om_n = sc_df[3], th_n = sc_df[4], cmul = sc_df[5];
+    if (ACC) __syncthreads();
+    const DF one = {1.0f, 0.0f}, zero = {0.0f, 0.0f};
+    const DF om_p = ACC ? sc_df[0] : one, th_p = ACC ? sc_df[1] : zero, eta_p = ACC ? sc_df[2] : zero;
+    const DF om_n = ACC ? sc_df[3] : one, th_n = ACC ? sc_df[4] : zero, cmul = ACC ? sc_df[5] : zero;
     const int64_t n_act = (acwb_n && a.hybrid) ? a.n_tr : a.n;
     const bool first_acwb = (m_n == 1);
-    const DF nu = sc_df[6];
+    const DF nu = {a.nu_hi, a.nu_lo};
     const bool need_bc = pend && pm_acwb;
     const bool need_bc_resid = (KIND != kRowsUpdate) && acwb_n && !first_acwb;
     const bool eval_risk = (KIND == kRowsUpdate) && a.hybrid && (!st.risk_valid || (pend && pm_acwb));
@@ -572,6 +573,7 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
 }
 
 constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz: a stuck pipeline reports an error
+constexpr int kEpiVec = 4;                         // 16-byte vectors per thread and pass of the cluster epilogue
 
 template <typename IndT>
 __device__ __forceinline__ void unpack16(uint4 raw, int out[16 / sizeof(IndT)]);
@@ -844,30 +846,34 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
         for (int c0 = bl0; c0 < bl1; c0 += cb) {
             const int c1 = min(bl1, c0 + cb);
             const int nvec = ((c1 - c0) * F) >> 2;
-            for (int v0 = tid; v0 < nvec; v0 += 4 * blockDim.x) {
-                Acc acc[4][4];
+            // kEpiVec vectors per thread and pass, the loads from one rank issued together (a
+            // remote rank's distributed shared memory is a long round trip)
+            for (int v0 = tid; v0 < nvec; v0 += kEpiVec * blockDim.x) {
+                Acc acc[kEpiVec][4];
 #pragma unroll
-                for (int k = 0; k < 4; ++k)
+                for (int k = 0; k < kEpiVec; ++k)
 #pragma unroll
                     for (int t = 0; t < 4; ++t) acc[k][t] = Acc(0);
                 for (int r = 0; r < a.cs; ++r) {
                     const Acc* h = cluster.map_shared_rank(hist, r) + ch * a.ch_stride + c0 * F;
+                    int4 x[kEpiVec];
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
+                    for (int k = 0; k < kEpiVec; ++k) {
                         const int v = v0 + k * blockDim.x;
-                        if (v < nvec) {
-                            if (INT_ACC) {
-                                const int4 x = reinterpret_cast<const int4*>(h)[v];
-                                acc[k][0] += x.x; acc[k][1] += x.y; acc[k][2] += x.z; acc[k][3] += x.w;
-                            } else {
-                                const float4 x = reinterpret_cast<const float4*>(h)[v];
-                                acc[k][0] += x.x; acc[k][1] += x.y; acc[k][2] += x.z; acc[k][3] += x.w;
-                            }
+                        x[k] = v < nvec ? reinterpret_cast<const int4*>(h)[v] : make_int4(0, 0, 0, 0);
+                    }
+#pragma unroll
+                    for (int k = 0; k < kEpiVec; ++k) {
+                        if (INT_ACC) {
+                            acc[k][0] += x[k].x; acc[k][1] += x[k].y; acc[k][2] += x[k].z; acc[k][3] += x[k].w;
+                        } else {
+                            acc[k][0] += __int_as_float(x[k].x); acc[k][1] += __int_as_float(x[k].y);
+                            acc[k][2] += __int_as_float(x[k].z); acc[k][3] += __int_as_float(x[k].w);
                         }
                     }
                 }
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
+                for (int k = 0; k < kEpiVec; ++k) {
                     const int v = v0 + k * blockDim.x;
                     if (v < nvec) {
 #pragma unroll
@@ -1436,6 +1442,8 @@ RowArgs row_args(cwb_model* m)
     a.loss = m->cfg.loss;
     a.nu = m->cfg.nu;
     a.gamma = m->cfg.gamma;
+    a.nu_hi = (float)m->cfg.nu;
+    a.nu_lo = (float)(m->cfg.nu - (double)a.nu_hi);
     a.hybrid = m->hybrid ? 1 : 0;
     a.patience = m->cfg.patience;
     a.risk_part = m->risk_part;
