@@ -315,6 +315,31 @@ def test_hcwb_patience_zero_starts_with_cwb(cwb):
 
 # ------------------------------------------------------------------ edge cases and errors
 
+def test_many_learners_argmin_over_several_passes(cwb):
+    """K = 300 learners (P-spline and linear per feature): the argmin's per-lane passes over the
+    criteria (128 per pass) and the solve grid of K CTAs; ACWB puts a second channel through it."""
+    data = S.additive_regression(3_001, 150, 6, seed=41, dtype=np.float32)
+    # informative features last, so the winners sit in the argmin's second pass (128..255)
+    specs = [dict(feature=j, n_bins=40, n_knots=6, df=4.0) for j in reversed(range(150))]
+    specs += [dict(feature=j, n_bins=40, type=1) for j in reversed(range(150))]
+    model, ref = run_pair(cwb, data.X, data.y, specs, M=30)
+    assert ref.k_sel.min() >= 128
+    run_pair(cwb, data.X, data.y, specs, M=20, opt=1, gamma=0.01)
+
+
+def test_heavily_skewed_bins_use_fp32_histograms(cwb):
+    """A feature with 40 % of its rows at one value puts more than 8192 rows of one cluster into one
+    bin: the plan drops the fixed-point histograms for FP32 atomics with compensated cross-cluster
+    sums, which must meet the same parity bar."""
+    data = S.additive_regression(2_000_000, 4, 3, seed=43, dtype=np.float32)
+    X = data.X.copy()
+    spike = np.random.default_rng(7).random(X.shape[1]) < 0.4
+    X[0, spike] = 0.5
+    specs = [dict(feature=j, n_bins=-1) for j in range(4)]
+    model, _ = run_pair(cwb, X, data.y, specs, M=15)
+    assert model.scatter_plan()["int_fixed_point"] == 0
+
+
 def test_tiny_problem_linear_learners(cwb):
     X = np.array([[0.0, 1.0, 2.0, 3.0, 5.0], [1.0, -1.0, 0.5, 0.25, 2.0]])
     y = np.array([1.0, 2.0, 2.5, 4.0, 7.0])
