@@ -175,16 +175,6 @@ __device__ __forceinline__ void set4(float4& v, int t, float x)
     if (t == 0) v.x = x; else if (t == 1) v.y = x; else if (t == 2) v.z = x; else v.w = x;
 }
 
-__device__ __forceinline__ void load_df4(const float* p, int64_t i4, DF out[4])
-{
-    float4 a = *reinterpret_cast<const float4*>(p + 2 * i4);
-    float4 b = *reinterpret_cast<const float4*>(p + 2 * i4 + 4);
-    out[0] = {a.x, a.y};
-    out[1] = {a.z, a.w};
-    out[2] = {b.x, b.y};
-    out[3] = {b.z, b.w};
-}
-
 __device__ __forceinline__ void store_df4(float* p, int64_t i4, const DF v[4])
 {
     *reinterpret_cast<float4*>(p + 2 * i4) = make_float4(v[0].hi, v[0].lo, v[1].hi, v[1].lo);
@@ -199,13 +189,25 @@ struct RowIn {
 };
 
 // need_y: targets (residual passes and the validation risk)
+// Loads through L2 (ld.global.cg): the first pass's loads may be issued before the kernel waits
+// for its predecessor, and only L2 is coherent with what earlier kernels wrote.
+__device__ __forceinline__ void load_df4_cg(const float* p, int64_t i4, DF out[4])
+{
+    const float4 a = __ldcg(reinterpret_cast<const float4*>(p + 2 * i4));
+    const float4 b = __ldcg(reinterpret_cast<const float4*>(p + 2 * i4 + 4));
+    out[0] = {a.x, a.y};
+    out[1] = {a.z, a.w};
+    out[2] = {b.x, b.y};
+    out[3] = {b.z, b.w};
+}
+
 template <bool ACC>
 __device__ __forceinline__ void load_row_in(const RowArgs& a, int64_t i4, RowIn& in, bool need_y)
 {
-    load_df4(a.f, i4, in.f);
-    if (ACC && a.h) load_df4(a.h, i4, in.h);
+    load_df4_cg(a.f, i4, in.f);
+    if (ACC && a.h) load_df4_cg(a.h, i4, in.h);
     else for (int t = 0; t < 4; ++t) in.h[t] = {0.0f, 0.0f};
-    in.y = need_y ? *reinterpret_cast<const float4*>(a.y + i4) : make_float4(0.f, 0.f, 0.f, 0.f);
+    in.y = need_y ? __ldcg(reinterpret_cast<const float4*>(a.y + i4)) : make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // A thread handles row_groups(ACC) groups of 4 rows per pass (blockDim.x * 4 rows apart); the
@@ -220,18 +222,26 @@ template <int KIND, typename IndT, bool ACC>
 __global__ void __launch_bounds__(kRowThreads, 4) k_rows(RowArgs a)
 {
     constexpr int kRowGroups = row_groups(ACC);
-    grid_dep_wait();
-    grid_dep_launch();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x * 4 * kRowGroups;
     const int64_t first = (int64_t)blockIdx.x * blockDim.x * 4 * kRowGroups + threadIdx.x * 4;
     const bool need_y = KIND != kRowsUpdate || a.hybrid, need_w = KIND != kRowsUpdate;
     const bool need_ylo = need_y && a.y_lo != nullptr, load_w = need_w && a.w != nullptr;
     RowIn in[kRowGroups];
+    auto first_pass_loads = [&]() {
 #pragma unroll
-    for (int u = 0; u < kRowGroups; ++u) {
-        const int64_t i4 = first + (int64_t)u * blockDim.x * 4;
-        if (i4 < a.n_pad) load_row_in<ACC>(a, i4, in[u], need_y);
-    }
+        for (int u = 0; u < kRowGroups; ++u) {
+            const int64_t i4 = first + (int64_t)u * blockDim.x * 4;
+            if (i4 < a.n_pad) load_row_in<ACC>(a, i4, in[u], need_y);
+        }
+    };
+    // Without HCWB the kernel this one depends on is the solve (or nothing), which writes none of
+    // these inputs: f, h were last written by the previous row pass, which finished before the
+    // previous scatter began.  So the first pass's loads go out before the wait and overlap the
+    // solve's tail, on SMs the solve leaves idle.  (With HCWB a row pass follows another row pass.)
+    if (!a.hybrid) first_pass_loads();
+    grid_dep_wait();
+    grid_dep_launch();
+    if (a.hybrid) first_pass_loads();
     const DevState st = *a.state;
     const bool pend = (KIND != kRowsResid) && (st.m > st.m_applied);
     const int pm = st.pend_mode;
@@ -658,9 +668,16 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    // everything below reads what the row pass wrote (iteration state, residuals)
-    grid_dep_wait();
-    const int mode = a.state->mode;
+    // Without HCWB the iteration mode never changes (ACWB models use two channels, CWB models one),
+    // so the tiles can be planned without the iteration state and the loader can start on the index
+    // matrix, which no kernel writes, before the row pass has finished; every other read of what
+    // the row pass wrote waits for it.
+    const bool fixed_mode = !a.hybrid;
+    int mode = CMAX == 2 ? kModeACWB : kModeCWB;
+    if (!fixed_mode) {
+        grid_dep_wait();
+        mode = a.state->mode;
+    }
     const int C = (!counting && CMAX == 2 && mode == kModeACWB) ? 2 : 1;
     const bool train_rows = a.hybrid && mode == kModeACWB;
     const int64_t n_act = counting ? a.count_rows : (train_rows ? a.n_tr : a.n);
@@ -676,10 +693,28 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
             const uint32_t bytes = (uint32_t)(FE * row_bytes + C * kStageRows * 4);   // box bytes + residual rows
             int issued = 0;
             bool ok = true;
+            // the first ring's index boxes before the wait (their barriers expect the residual
+            // bytes too, which follow once the row pass is complete)
+            const int early = fixed_mode ? min(a.stages, ntiles) : 0;
+            for (int it = 0; it < early; ++it) {
+                const int64_t row0 = (t_lo + it) * kStageRows;
+                mbar_arrive_expect_tx(&full[it], bytes);
+                tma_load_3d(smem + a.ind_off + (size_t)it * a.stage_ind_bytes, &tmap, 0, g * FE,
+                            (int)(row0 / (128 / (int)sizeof(IndT))), &full[it]);
+            }
+            if (fixed_mode) grid_dep_wait();
+            for (int it = 0; it < early; ++it) {
+                const int64_t row0 = (t_lo + it) * kStageRows;
+                float* r_dst = reinterpret_cast<float*>(smem + a.r_off + (size_t)it * a.stage_r_bytes);
+                for (int ch = 0; ch < C; ++ch)
+                    bulk_load(r_dst + ch * kStageRows, a.rw + ch * a.n_pad + row0, (uint32_t)kStageRows * 4,
+                              &full[it]);
+                ++issued;
+            }
             // ring position kept incrementally (no division by the run-time stage count per tile)
-            int s = 0;
+            int s = early;
             uint32_t ph = 0;
-            for (int it = 0; it < ntiles; ++it, ++s) {
+            for (int it = early; it < ntiles; ++it, ++s) {
                 if (s == a.stages) {
                     s = 0;
                     ph ^= 1u;
@@ -708,6 +743,7 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
         }
     } else if (warp == W + 1) {
         // converter: residual tile -> fixed point (or a plain hand-over for FP32 accumulation)
+        if (fixed_mode) grid_dep_wait();
         float scale[2] = {1.0f, 1.0f};
         if (INT_ACC && !counting) {
             const int cidx = train_rows ? 1 : 0;
