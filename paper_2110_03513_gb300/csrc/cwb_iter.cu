@@ -8,10 +8,10 @@
 //              decides the next mode (Algorithm 4).
 //   k_scatter  binMatVec (Algorithm 2): u_k[l] = sum_{i: ind_k,i = l} w_i r_i for
 //              every binning, shared-memory histograms, one lane per binning.
-//   k_solve    per learner: u -> s = Z^b^T u -> theta = P s (FP64) -> criterion
-//              Q_k = theta^T G theta - 2 theta^T s = SSE_k - r^T W r (FP64);
-//              the last CTA takes the argmin (ties: lowest k), writes the update
-//              table v = Z^b theta of the winner and the trace.
+//   k_solve    per learner: u -> s = Z^b^T u -> theta = P s -> criterion
+//              Q_k = theta^T G theta - 2 theta^T s = SSE_k - r^T W r (float-float
+//              from the cached FP64 matrices) and the update table v_k = Z^b theta;
+//              the last CTA takes the argmin (ties: lowest k) and writes the trace.
 #include <math.h>
 
 #include <algorithm>
@@ -964,9 +964,10 @@ __global__ void k_count_log2(DevState* state, int idx)
 // One CTA per learner k on binning b: u_b[l] = sum over the clusters of b's slot
 // of the partial histograms (exact int64 sum of the fixed-point partials, or a
 // compensated FP32 sum), s = Z^b^T u (FP32, column-major design staged in shared
-// memory), theta = P s and Q = theta^T G theta - 2 theta^T s (FP64), and the
-// learner's update table v_k = Z^b theta (FP32).  The last CTA to finish takes
-// the argmin of Q per channel (ties: lowest k), writes the trace and advances the
+// memory), theta = P s and Q = theta^T G theta - 2 theta^T s = s^T A s with the
+// cached A = P G P - 2 P (float-float arithmetic, about 44 bits), and the learner's
+// update table v_k = Z^b theta (FP32).  The last CTA to take the ticket finds the
+// argmin of Q per channel (ties: lowest k), writes the trace and advances the
 // iteration state.
 
 constexpr int kSolveChunk = 1024;      // bins of u held in shared memory per pass
@@ -1064,7 +1065,7 @@ __global__ void __launch_bounds__(kSolveThreads, 1) k_solve(SolveArgs a)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int b = a.l_bin[k], d = a.l_d[k], nst = a.l_nstar[k];
     const int D = a.D, S = a.S;
-    // dynamic shared memory: P, G (D x D, FP64), the learner's design rows (float4 + first
+    // dynamic shared memory: P, A (D x D float-float pairs), the learner's design rows (float4 + first
     // column per bin), u for one chunk of bins, the second cluster half's partial sums and,
     // when it fits, the column-major design
     extern __shared__ __align__(16) double dsm[];
