@@ -762,8 +762,9 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
                 break;
             }
             if (INT_ACC) {
-                // fixed-point copy into a separate buffer: the TMA landing zone only ever sees
-                // async-proxy writes and generic reads
+                // fixed point in place of the residuals (every lane rewrites the values it read):
+                // the stage holds one copy, which leaves room for one more ring stage; a proxy fence
+                // orders these generic writes before the stage's next bulk copy
                 const float* rt = reinterpret_cast<const float*>(smem + a.r_off + (size_t)s * a.stage_r_bytes);
                 int* qt = reinterpret_cast<int*>(smem + a.q_off + (size_t)s * a.stage_r_bytes);
                 const int64_t row0 = (t_lo + jt) * kStageRows;
@@ -786,6 +787,7 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
                     }
                     *reinterpret_cast<int4*>(qt + i0) = q;
                 }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&ready[s]);
@@ -1780,7 +1782,7 @@ cwb_status plan_scatter(cwb_model* m, int max_ctas, int cs_req)
     };
     auto hist_bytes = [&](int nb, int F) { return ((cmax * ch_stride_for(nb, F) * 4 + 1023) / 1024) * 1024; };
     // a stage's index box starts on a 1024-byte boundary (the 128-byte swizzle pattern repeats every 1 KB)
-    auto stage_bytes = [&](int F) { return ((F * P.stage_rows * elem + 1023) / 1024) * 1024 + 2 * cmax * P.stage_rows * 4; };
+    auto stage_bytes = [&](int F) { return ((F * P.stage_rows * elem + 1023) / 1024) * 1024 + cmax * P.stage_rows * 4; };
     P.f_lane = 0;
     for (int F = 32; F >= 1; F >>= 1) {
         if (F * cmax > 32 || F > pow2B) continue;
@@ -1806,7 +1808,7 @@ cwb_status plan_scatter(cwb_model* m, int max_ctas, int cs_req)
     P.stages = std::min(8, (budget - hb) / stage_bytes(P.fe));
     P.ind_off = 0;
     P.r_off = P.ind_off + (uint32_t)P.stages * P.stage_ind_bytes;
-    P.q_off = P.r_off + (uint32_t)P.stages * P.stage_r_bytes;
+    P.q_off = P.r_off;                              // fixed point replaces the residuals in place
     P.hist_off = ((P.q_off + (uint32_t)P.stages * P.stage_r_bytes + 1023) / 1024) * 1024;
     P.bar_off = P.hist_off + (uint32_t)hb;
     P.smem = (size_t)P.bar_off + 3 * 8 * P.stages + 1024;
