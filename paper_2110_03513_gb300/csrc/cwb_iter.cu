@@ -29,7 +29,6 @@ namespace cwb {
 namespace {
 
 constexpr int kRowThreads = 256;
-constexpr int kSolveThreads = 512;
 constexpr int kScatterWarps = 16;      // consumer warps of a scatter CTA
 constexpr int kScatterThreads = (kScatterWarps + 2) * 32;   // + 1 loader warp + 1 converter warp
 constexpr int kStageRows = 256;        // rows per pipeline stage (tile)
@@ -972,7 +971,11 @@ __global__ void k_count_log2(DevState* state, int idx)
 // argmin of Q per channel (ties: lowest k), writes the trace and advances the
 // iteration state.
 
-constexpr int kSolveChunk = 1024;      // bins of u held in shared memory per pass
+// Solve block sizes: 512 threads for models with more than 512 design points (a pass over the
+// partial histograms covers 1024 bins, two halves of 256 threads x 4 bins), 256 threads otherwise,
+// so that two solve CTAs share an SM: fits that run side by side (batches, the server) are bound by
+// the solve's SM occupancy, not its latency.  A pass covers 2 x threads bins (kSolveChunk).
+__host__ __device__ constexpr int solve_chunk(int threads) { return 2 * threads; }
 constexpr int kSolveBatch = 20;        // partial-histogram rows per thread and batch (per channel)
 
 struct SolveArgs {
@@ -1058,9 +1061,10 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src)
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-template <bool INT_ACC>
-__global__ void __launch_bounds__(kSolveThreads, 1) k_solve(SolveArgs a)
+template <bool INT_ACC, int kSolveThreads>
+__global__ void __launch_bounds__(kSolveThreads, 512 / kSolveThreads) k_solve(SolveArgs a)
 {
+    constexpr int kSolveChunk = solve_chunk(kSolveThreads);
     constexpr int NW = kSolveThreads / 32;
     constexpr int kColsPerWarp = (kMaxD + NW - 1) / NW;
     const int k = blockIdx.x;
@@ -1589,11 +1593,14 @@ void launch_scatter(cwb_model* m, cudaStream_t s)
     launch_scatter_args(m, s, scatter_args(m), m->plan.int_acc);
 }
 
+int solve_threads(const cwb_model* m) { return m->nstar_max > solve_chunk(256) ? 512 : 256; }
+
 size_t solve_smem(const cwb_model* m, bool stage_v, bool stage_z)
 {
     const size_t S = m->nstar_max;
+    const size_t chunk = solve_chunk(solve_threads(m));
     size_t b = sizeof(float2) * 2 * (size_t)m->d_max * m->d_max;        // P, A (float-float pairs)
-    b += sizeof(float) * 2 * kSolveChunk + sizeof(long long) * 2 * kSolveChunk;   // u chunk, half sums
+    b += sizeof(float) * 2 * chunk + sizeof(long long) * 2 * chunk;      // u chunk, half sums
     if (stage_v) b += 16 * S + 4 * ((S + 3) & ~size_t(3));              // design rows, first columns
     if (stage_z) b += sizeof(float) * kMaxNnz * S;                       // column-major design
     return b;
@@ -1637,7 +1644,8 @@ void launch_solve(cwb_model* m, cudaStream_t s)
     a.trace_cap = m->trace_cap;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(m->K, 1, 1);
-    cfg.blockDim = dim3(kSolveThreads, 1, 1);
+    const int threads = solve_threads(m);
+    cfg.blockDim = dim3(threads, 1, 1);
     cfg.dynamicSmemBytes = solve_smem(m, P.solve_stage_v, P.solve_stage_z);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -1645,8 +1653,13 @@ void launch_solve(cwb_model* m, cudaStream_t s)
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = m->use_pdl ? 1 : 0;
-    if (P.int_acc) cudaLaunchKernelEx(&cfg, k_solve<true>, a);
-    else cudaLaunchKernelEx(&cfg, k_solve<false>, a);
+    if (threads == 512) {
+        if (P.int_acc) cudaLaunchKernelEx(&cfg, k_solve<true, 512>, a);
+        else cudaLaunchKernelEx(&cfg, k_solve<false, 512>, a);
+    } else {
+        if (P.int_acc) cudaLaunchKernelEx(&cfg, k_solve<true, 256>, a);
+        else cudaLaunchKernelEx(&cfg, k_solve<false, 256>, a);
+    }
 }
 
 template <typename IndT, int CMAX>
@@ -1896,8 +1909,9 @@ cwb_status plan_scatter(cwb_model* m, int max_ctas, int cs_req)
             set_error("solve kernel: basis dimension too large for shared memory");
             return CWB_EINVAL;
         }
-        CWB_CUDA_TRY(allow_max_dynamic_smem((const void*)k_solve<true>, m->device));
-        CWB_CUDA_TRY(allow_max_dynamic_smem((const void*)k_solve<false>, m->device));
+        for (const void* kf : {(const void*)k_solve<true, 512>, (const void*)k_solve<false, 512>,
+                               (const void*)k_solve<true, 256>, (const void*)k_solve<false, 256>})
+            CWB_CUDA_TRY(allow_max_dynamic_smem(kf, m->device));
     }
     m->plan = P;
     release_scatter_plan(m);
