@@ -246,6 +246,34 @@ def test_categorical_acwb_and_hcwb(cwb):
     run_pair(cwb, data.X, data.y, specs, M=160, loss=1, opt=2, gamma=0.01, patience=3, val_mask=val)
 
 
+def test_categorical_lookup_is_the_class_code(cwb):
+    """Each class is one design point: the bin index of a categorical learner is the code itself
+    (in the caller's row order, also with HCWB's train-first row permutation), and the learner's
+    design is the dummy matrix (ridge) or the class indicator (binary)."""
+    data = S.mixed_categorical(5_000, 1, [11], seed=35)
+    codes = data.X[1].astype(np.int32)
+    val = (np.random.default_rng(2).random(data.n) < 0.3).astype(np.uint8)
+    for opt, vm in ((cwb.OPT_CWB, None), (cwb.OPT_HCWB, val)):
+        m = cwb.Model(data.X, data.y, [cwb.learner(1, type=cwb.BL_CATEGORICAL, n_knots=11, df=4.0),
+                                       cwb.learner(1, type=cwb.BL_CATEGORICAL_BINARY, n_knots=11, level=7)],
+                      opt=opt, val_mask=vm, device=0)
+        for k in (0, 1):
+            assert np.array_equal(m.bin_index(k), codes)
+        info = m.learner_info(0)
+        assert (info.nstar, info.d, info.xmin, info.xmax) == (11, 11, 0.0, 10.0)
+        assert m.learner_info(1).d == 1 and m.learner_info(1).binning == info.binning
+        # Z^T W Z = diag(n_k) on the fitting rows, P = diag(1 / (n_k + lambda)) (App. B.1)
+        rows = codes if vm is None else codes[vm == 0]
+        nk = np.bincount(rows, minlength=11).astype(np.float64)
+        G, P = m.matrices(0)
+        np.testing.assert_array_equal(G, np.diag(nk))
+        np.testing.assert_allclose(P, np.diag(1.0 / (nk + info.lam)), rtol=1e-13)
+        assert abs(np.sum(nk / (nk + info.lam)) - 4.0) < 1e-9      # df1 closed form
+        G1, P1 = m.matrices(1)
+        np.testing.assert_allclose(P1, np.diag([1.0 / G1[0, 0]]), rtol=1e-13)
+        m.free()
+
+
 def test_categorical_invalid_codes_are_rejected(cwb):
     data = S.mixed_categorical(2_000, 1, [5], seed=34)
     for bad in (2.5, -1.0, 5.0):
