@@ -671,31 +671,31 @@ def mise_fit(cwb, data, val, *, nbins: int, df: float, opt: int, nu: float = 0.0
 
 
 def mise_cases(cwb, *, ns=(5_000, 20_000, 50_000), snrs=(1.0, 10.0), p: int = 5, p_noise: int = 5,
-               seed: int = 11, dfs=(5.0, 7.0, 9.0), gammas=(1e-1, 1e-2, 1e-3, 1e-4)) -> list:
-    """The harness grid: for every (n, SNR), on one truth per SNR (the same effects at every n):
-    exact binning (n* = number of unique values, i.e. no binning) and n* = floor(n^(1/2)) and
-    floor(n^(1/4)) for each df (CWB), ACWB for each momentum gamma and HCWB (gamma = 1e-3) at
-    n* = floor(n^(1/2)), df = 5."""
+               seed: int = 11, dfs=(5.0, 7.0, 9.0), gammas=(1e-1, 1e-2, 1e-3, 1e-4), reps: int = 1) -> list:
+    """The harness grid: for every replication, (n, SNR), on one truth per replication and SNR (the
+    same effects at every n): exact binning (n* = number of unique values, i.e. no binning) and
+    n* = floor(n^(1/2)) and floor(n^(1/4)) for each df (CWB), ACWB for each momentum gamma and HCWB
+    (gamma = 1e-3) at n* = floor(n^(1/2)), df = 5."""
+    import itertools
     import math
     import numpy as np
     import synthetic_inputs as S
     rows = []
-    for n in ns:
-        for snr in snrs:
-            data = S.paper_style_simulation(n, p, p_noise, snr, seed=seed + int(snr))
-            val = S.paper_style_sample(data.truth, p_noise, 100_000, seed=seed + 100)
-            sq, qu = math.isqrt(n), int(math.floor(n ** 0.25 + 1e-9))
-            specs = [("exact", cwb.BINS_EXACT, 5.0, cwb.OPT_CWB, 0.0)]
-            specs += [(f"sqrt df{int(df)}", sq, df, cwb.OPT_CWB, 0.0) for df in dfs]
-            specs += [(f"quarter df{int(df)}", qu, df, cwb.OPT_CWB, 0.0) for df in dfs]
-            specs += [(f"sqrt ACWB gamma {g:g}", sq, 5.0, cwb.OPT_ACWB, g) for g in gammas]
-            specs += [("sqrt HCWB gamma 0.001", sq, 5.0, cwb.OPT_HCWB, 1e-3)]
-            vm = (np.random.default_rng(seed).random(n) < 0.2).astype(np.uint8)
-            for name, nb, df, opt, g in specs:
-                r = mise_fit(cwb, data, val, nbins=nb, df=df, opt=opt, gamma=g,
-                             val_mask=vm if opt == cwb.OPT_HCWB else None)
-                rows.append({"n": n, "snr": snr, "variant": name, "nstar": nb if nb > 0 else n, "df": df,
-                             "gamma": g, **r})
+    for rp, n, snr in itertools.product(range(reps), ns, snrs):
+        data = S.paper_style_simulation(n, p, p_noise, snr, seed=seed + 1000 * rp + int(snr))
+        val = S.paper_style_sample(data.truth, p_noise, 100_000, seed=seed + 1000 * rp + 100)
+        sq, qu = math.isqrt(n), int(math.floor(n ** 0.25 + 1e-9))
+        specs = [("exact", cwb.BINS_EXACT, 5.0, cwb.OPT_CWB, 0.0)]
+        specs += [(f"sqrt df{int(df)}", sq, df, cwb.OPT_CWB, 0.0) for df in dfs]
+        specs += [(f"quarter df{int(df)}", qu, df, cwb.OPT_CWB, 0.0) for df in dfs]
+        specs += [(f"sqrt ACWB gamma {g:g}", sq, 5.0, cwb.OPT_ACWB, g) for g in gammas]
+        specs += [("sqrt HCWB gamma 0.001", sq, 5.0, cwb.OPT_HCWB, 1e-3)]
+        vm = (np.random.default_rng(seed).random(n) < 0.2).astype(np.uint8)
+        for name, nb, df, opt, g in specs:
+            r = mise_fit(cwb, data, val, nbins=nb, df=df, opt=opt, gamma=g,
+                         val_mask=vm if opt == cwb.OPT_HCWB else None)
+            rows.append({"rep": rp, "n": n, "snr": snr, "variant": name, "nstar": nb if nb > 0 else n,
+                         "df": df, "gamma": g, **r})
     return rows
 
 
@@ -703,15 +703,24 @@ def run_mise(args):
     import __graft_entry__ as g
     g.build()
     import paper_2110_03513_gb300 as cwb
+    import numpy as np
     t0 = time.perf_counter()
-    rows = mise_cases(cwb)
+    reps = 5
+    rows = mise_cases(cwb, reps=reps)
+    summary = {}
+    for r in rows:
+        summary.setdefault((r["n"], r["snr"], r["variant"]), []).append(r)
+    table = [{"n": n, "snr": snr, "variant": v, "mise_mean": float(np.mean([r["mise"] for r in rs])),
+              "mise_sd": float(np.std([r["mise"] for r in rs], ddof=1)) if len(rs) > 1 else 0.0,
+              "stop_iter_mean": float(np.mean([r["stop_iter"] for r in rs]))}
+             for (n, snr, v), rs in summary.items()]
     line = {"metric": "MISE of partial effects (paper-style simulation, early stopping on noise-free data)",
             "unit": "MISE", "higher_is_better": False, "data": "synthetic", "n_gpus": 1,
             "config": {"workload": "paper-style simulation (Sec. 4.1.1): p=5 informative random cubic-spline "
                                    "effects on U[a, a+b] ranges, 5 N(0,1) noise features, Gaussian noise at "
                                    "SNR 1 and 10; nu=0.05; stopping on 100,000 noise-free rows, checked every "
-                                   "25 iterations, patience 8 checks"},
-            "cases": rows, "wall_s": time.perf_counter() - t0}
+                                   "25 iterations, patience 8 checks", "replications": reps},
+            "summary": table, "cases": rows, "wall_s": time.perf_counter() - t0}
     print(json.dumps(line), flush=True)
 
 
