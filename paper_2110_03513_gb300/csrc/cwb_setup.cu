@@ -146,20 +146,40 @@ __global__ void k_minmax_final(const double* __restrict__ pmin, const double* __
 // Index vectors (Sec. 3.1.1).
 
 // Equidistant design points z_l = xmin + l h: closest point, half-way values to the
-// lower one, i.e. l = ceil((x - xmin)/h - 1/2) clamped to [0, n*-1].  Correctly
-// rounded FP64 operations only, so the index is reproducible bit for bit.
+// lower one, i.e. l = ceil((x - xmin)/h - 1/2) clamped to [0, n*-1], defined on correctly
+// rounded FP64 operations so that the index is reproducible bit for bit.  The FP64
+// division is slow on this GPU, so the quotient is first formed in FP32: its relative
+// error is below 3 x 2^-24 (the rounding of x - xmin, of 1/h and of the product), so
+// when no integer lies within 4e-7 |t| + 1e-6 of t - 1/2 (the interval is evaluated in
+// FP32, whose own roundings the margin also covers) the FP32 and FP64 rules agree;
+// only values that close to a half-way point take the FP64 path.
 template <typename T, typename IndT>
 __global__ void k_bin_equidistant(const T* __restrict__ X, int64_t feat, const int32_t* __restrict__ perm,
                                   int64_t n, int64_t n_pad, double xmin, double h, int nstar,
                                   IndT* __restrict__ out)
 {
     const T* x = X + feat * n;
+    const float inv_h = (float)(1.0 / h);
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n_pad; q += (int64_t)gridDim.x * blockDim.x) {
         int l = 0;
         if (q < n) {
-            double v = (double)x[perm ? perm[q] : q];
-            double t = __ddiv_rn(__dsub_rn(v, xmin), h);
-            double c = ceil(__dsub_rn(t, 0.5));
+            const T xv = x[perm ? perm[q] : q];
+            double dv;
+            float d32;
+            if (sizeof(T) == 4) {
+                // x and xmin are FP32 values here (xmin is the feature's minimum, or 0 for class
+                // codes): the FP32 difference is the exact difference rounded once
+                dv = __dsub_rn((double)xv, xmin);
+                d32 = (float)xv - (float)xmin;
+            } else {
+                dv = __dsub_rn((double)xv, xmin);
+                d32 = (float)dv;
+            }
+            const float t32 = d32 * inv_h;
+            const float e = 4.0e-7f * fabsf(t32) + 1.0e-6f;
+            const float c_lo = ceilf(t32 - 0.5f - e), c_hi = ceilf(t32 - 0.5f + e);
+            double c = (double)c_lo;
+            if (c_lo != c_hi || !isfinite(t32)) c = ceil(__dsub_rn(__ddiv_rn(dv, h), 0.5));
             c = fmax(c, 0.0);
             c = fmin(c, (double)(nstar - 1));
             l = (int)c;
@@ -260,6 +280,28 @@ __global__ void k_bin_exact(const T* __restrict__ X, int64_t feat, const int32_t
 
 // ---------------------------------------------------------------------------
 // Weighted bin counts cnt[b][l] = sum over rows [r0, r1) with ind = l of w (binMatMat input).
+
+// Unweighted counts: a CTA counts its rows in a shared-memory histogram (int32) and adds the
+// non-zero bins to the FP64 totals; integer-valued sums, so the result is exact and does not
+// depend on the order of the additions.  nstar <= kCountSmemBins (48 KB, no opt-in needed).
+constexpr int kCountSmemBins = 12288;
+
+template <typename IndT>
+__global__ void k_counts_smem(const IndT* __restrict__ ind, int64_t n_pad, int64_t r1, int nstar, int stride,
+                              double* __restrict__ cnt)
+{
+    extern __shared__ int hc[];
+    const int b = blockIdx.y;
+    const IndT* row = ind + (int64_t)b * n_pad;
+    for (int l = threadIdx.x; l < nstar; l += blockDim.x) hc[l] = 0;
+    __syncthreads();
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < r1; q += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&hc[row[q]], 1);
+    __syncthreads();
+    double* c = cnt + (int64_t)b * stride;
+    for (int l = threadIdx.x; l < nstar; l += blockDim.x)
+        if (hc[l]) atomicAdd(&c[l], (double)hc[l]);
+}
 
 template <typename IndT>
 __global__ void k_counts(const IndT* __restrict__ ind, int64_t n_pad, int64_t r0, int64_t r1,
@@ -1117,11 +1159,18 @@ cwb_status setup_model(cwb_model* m, const void* X_in, int x_dtype, const void* 
     CWB_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(double) * (size_t)2 * B * S, s));
     for (int ph = 0; ph < phases; ++ph) {
         int64_t r1 = (ph == 0) ? m->n_tr : n;
-        dim3 grid(std::min<int>(grid_for(r1, m->device), 64), B);
-        if (m->ind_bytes == 1)
-            k_counts<<<grid, kThreads, 0, s>>>((const uint8_t*)m->ind, n_pad, 0, r1, w64, S, cnt + (int64_t)ph * B * S);
-        else
-            k_counts<<<grid, kThreads, 0, s>>>((const uint16_t*)m->ind, n_pad, 0, r1, w64, S, cnt + (int64_t)ph * B * S);
+        double* out = cnt + (int64_t)ph * B * S;
+        if (!w64 && S <= kCountSmemBins) {
+            // nstar_max bins per CTA (every binning's counts fit); a few CTAs per binning
+            dim3 grid(std::min<int>(grid_for(r1, m->device), 16), B);
+            const size_t smem = sizeof(int) * (size_t)S;
+            if (m->ind_bytes == 1) k_counts_smem<<<grid, kThreads, smem, s>>>((const uint8_t*)m->ind, n_pad, r1, S, S, out);
+            else k_counts_smem<<<grid, kThreads, smem, s>>>((const uint16_t*)m->ind, n_pad, r1, S, S, out);
+        } else {
+            dim3 grid(std::min<int>(grid_for(r1, m->device), 64), B);
+            if (m->ind_bytes == 1) k_counts<<<grid, kThreads, 0, s>>>((const uint8_t*)m->ind, n_pad, 0, r1, w64, S, out);
+            else k_counts<<<grid, kThreads, 0, s>>>((const uint16_t*)m->ind, n_pad, 0, r1, w64, S, out);
+        }
     }
     if (phases == 1)
         CWB_CUDA_TRY(cudaMemcpyAsync(cnt + (int64_t)B * S, cnt, sizeof(double) * (size_t)B * S, cudaMemcpyDeviceToDevice, s));

@@ -116,6 +116,32 @@ def test_setup_matches_oracle(cwb, n_bins, n):
     model.free()
 
 
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+@pytest.mark.parametrize("nstar", [7, 1000, 60000])
+def test_binning_at_half_way_points_is_bit_exact(cwb, dtype, nstar):
+    """Values on, and a few ulps around, the half-way points between design points (where the
+    rule sends ties to the lower point) and on the design points themselves: the device index
+    equals the oracle's bit for bit, for FP32 and FP64 features (Sec. 3.1.1)."""
+    rng = np.random.default_rng(nstar)
+    lo, hi = -3.7, 11.3
+    h = (hi - lo) / (nstar - 1)
+    l = rng.integers(0, nstar - 1, size=20_000)
+    mids = lo + (l + 0.5) * h
+    pts = lo + l * h
+    vals = [np.array([lo, hi]), mids, pts]
+    for k in (1, 2, 3):
+        vals += [np.nextafter(mids, np.inf) if k == 1 else mids + k * np.spacing(mids),
+                 mids - k * np.spacing(mids)]
+    x = np.concatenate(vals).astype(dtype)
+    x[0], x[1] = dtype(lo), dtype(hi)
+    y = rng.normal(size=x.size).astype(dtype)
+    X = np.stack([x, rng.random(x.size).astype(dtype)])
+    m = cwb.Model(X, y, [cwb.learner(0, n_bins=nstar, type=1)], iterations=1, device=0)
+    ind_ref, _ = O.bin_equidistant(x.astype(np.float64), nstar)
+    np.testing.assert_array_equal(m.bin_index(0), ind_ref)
+    m.free()
+
+
 def test_lambda_on_sparse_tail_bins(cwb):
     """N(0,1) features: nearly empty tail bins make Z^T Z ill conditioned; lambda must still match."""
     data = S.sim_binomial_hybrid(seed=30, n=40_000, p=8, n_informative=3)
