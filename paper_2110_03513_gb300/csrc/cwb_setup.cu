@@ -488,7 +488,7 @@ __global__ void k_gram(int S, int D, int K, const int32_t* __restrict__ l_bin, c
 // the bracket or does not halve the residual.  Every evaluation is a fresh
 // factorisation of A on the definition (no eigen-decomposition).
 
-constexpr int kLamThreads = 64;
+constexpr int kLamThreads = 256;
 
 struct LamArgs {
     int K, D;
