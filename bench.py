@@ -213,7 +213,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * N_ROWS / n_s * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "n": N_ROWS, "p": N_FEAT, "nstar": NSTAR},
+            "data": "synthetic", "config": {"workload": WORKLOAD, "n": N_ROWS, "p": N_FEAT, "nstar": NSTAR,
+                                            "index": "uint16", "learners": N_FEAT},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
