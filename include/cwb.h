@@ -142,8 +142,9 @@ typedef struct {
  *   out         receives the new model (NULL on failure)
  *
  * Errors: CWB_EINVAL for bad sizes, a constant feature (max == min), n* outside
- * [2, 65535], d > CWB_MAX_D, binomial targets outside {0, 1}, or HCWB without a
- * validation mask holding at least one training and one validation row;
+ * [2, 65535], d > CWB_MAX_D, binomial targets outside {0, 1}, a categorical feature
+ * holding a value that is not a class code 0..c-1, or HCWB without a validation mask
+ * holding at least one training and one validation row;
  * CWB_ENUMERIC if a Gram matrix is singular or df is not reachable;
  * CWB_ENOMEM / CWB_ECUDA on device failures.
  */
