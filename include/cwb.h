@@ -276,22 +276,24 @@ cwb_status cwb_get_scatter_plan(const cwb_model* m, int32_t* values, int32_t cap
  * cwb_predict_noalloc -- cwb_predict for host buffers that performs no device
  * memory allocation.  (The paper has no counterpart; this is a deployment aid.)
  *
- * Some callers cannot allocate device memory at prediction time: code running
- * while a CUDA stream is being captured into a graph (cudaMalloc and cudaFree are
- * not allowed there), real-time serving loops that must not stall on the
- * allocator or fragment it, and hosts that run under a fixed device-memory
- * budget handed out by another framework.  cwb_predict copies host inputs into
- * freshly allocated device buffers; this entry point instead stages Xnew and the
- * predictions through one fixed scratch array of CWB_NOALLOC_SCRATCH_BYTES
- * (16 MiB) that the library declares at file scope in device memory.  Every GPU
- * that loads the library holds that array until the process exits.
+ * Some callers cannot allocate device memory at prediction time: real-time
+ * serving loops, where cudaMalloc can stall on the driver's allocator and
+ * cudaFree waits for all work on the device; and processes whose device memory
+ * is handed out by another framework's allocator under a fixed budget, where an
+ * allocation made behind that allocator's back can fail or push the process
+ * over its budget.  cwb_predict copies host inputs into freshly allocated device
+ * buffers; this entry point instead stages Xnew and the predictions through one
+ * fixed scratch array of CWB_NOALLOC_SCRATCH_BYTES (16 MiB) that the library
+ * declares at file scope in device memory.  Every GPU that loads the library
+ * holds that array until the process exits.
  *
  *   Xnew   host, p x n_new feature-major, dtype x_dtype (CWB_F32 or CWB_F64)
  *   out    host, n_new FP32 predictions (same values as cwb_predict)
  *
  * Size limit: the Xnew bytes rounded up to 256, plus 4 * n_new bytes, must fit
- * in CWB_NOALLOC_SCRATCH_BYTES; larger requests fail with CWB_EINVAL and a
- * message naming both sizes (split the rows into several calls).
+ * in CWB_NOALLOC_SCRATCH_BYTES; larger requests (however large n_new is) fail
+ * with CWB_EINVAL before any device work, with a message naming the limit
+ * (split the rows into several calls).
  * The first call on a device looks up the scratch array's device address with
  * that device current (no allocation); make that first call before any stream
  * capture begins.  All calls in the process share the one array and it keeps the

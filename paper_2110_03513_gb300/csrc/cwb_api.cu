@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "cwb_internal.cuh"
+#include "cwb_noalloc_size.h"
 
 namespace cwb {
 
@@ -697,15 +698,17 @@ cwb_status cwb_predict_noalloc(const cwb_model* mc, const void* Xnew, int32_t x_
     if (n_new < 0) { set_error("n_new must be >= 0"); return CWB_EINVAL; }
     if (x_dtype != CWB_F32 && x_dtype != CWB_F64) { set_error("x_dtype must be CWB_F32 or CWB_F64"); return CWB_EINVAL; }
     if (n_new == 0) return CWB_OK;
-    const size_t xsz = (x_dtype == CWB_F64) ? 8 : 4;
-    const size_t x_bytes = xsz * (size_t)n_new * (size_t)m->p;
-    const size_t out_off = (x_bytes + 255) & ~(size_t)255;
-    const size_t need = out_off + sizeof(float) * (size_t)n_new;
-    if (need > (size_t)CWB_NOALLOC_SCRATCH_BYTES) {
-        set_error("cwb_predict_noalloc needs " + std::to_string(need) + " bytes of scratch for this request, the limit is " +
-                  std::to_string((size_t)CWB_NOALLOC_SCRATCH_BYTES) + " bytes; split the rows into several calls");
+    const int64_t xsz = (x_dtype == CWB_F64) ? 8 : 4;
+    uint64_t need = 0;
+    if (!cwb_noalloc_need(n_new, m->p, xsz, (uint64_t)CWB_NOALLOC_SCRATCH_BYTES, &need)) {
+        set_error("cwb_predict_noalloc: " + std::to_string(n_new) + " rows of " + std::to_string(m->p) +
+                  " features do not fit in the scratch limit of " + std::to_string((size_t)CWB_NOALLOC_SCRATCH_BYTES) +
+                  " bytes (each row takes " + std::to_string(xsz * m->p + 4) +
+                  " bytes, plus up to 255 of alignment); split the rows into several calls");
         return CWB_EINVAL;
     }
+    const size_t x_bytes = (size_t)xsz * (size_t)n_new * (size_t)m->p;     // <= need, no wrap-around
+    const size_t out_off = (x_bytes + 255) & ~(size_t)255;
     DeviceGuard guard(m->device);
     unsigned char* base = nullptr;
     CWB_TRY(noalloc_scratch(m->device, &base));

@@ -82,3 +82,41 @@ def test_binding_structs_match_the_header_layout(tmp_path):
         assert got[(name, "size")] == ctypes.sizeof(cls), name
         for field, _ in cls._fields_:
             assert got[(name, field)] == getattr(cls, field).offset, (name, field)
+
+
+def test_noalloc_size_check_rejects_wrapping_requests(tmp_path):
+    """The size check of cwb_predict_noalloc (host code, compiled here as plain C): requests whose
+    byte counts would wrap around 64 bits are rejected before any product is formed, the largest
+    request that fits is accepted with the exact byte count, and one more row is rejected."""
+    import subprocess
+    limit = 16 << 20
+    src = tmp_path / "need.c"
+    src.write_text("\n".join([
+        "#include <stdio.h>",
+        "#include <inttypes.h>",
+        '#include "cwb_noalloc_size.h"',
+        "int main(int argc, char** argv) {",
+        "  const int64_t cases[][3] = {",
+        "    {INT64_C(1) << 62, 50, 4}, {INT64_C(1) << 61, 3, 8}, {INT64_MAX, 1, 4}, {INT64_C(1) << 40, 1, 4},",
+        "    {0, 7, 4}, {1, 7, 8}, {-1, 3, 4}, {5, 0, 4}, {5, 3, 2},",
+        f"    {{({limit} - 255) / (4 * 50 + 4), 50, 4}}, {{({limit} - 255) / (4 * 50 + 4) + 1, 50, 4}},",
+        f"    {{({limit} - 255) / (8 * 3 + 4), 3, 8}}, {{({limit} - 255) / (8 * 3 + 4) + 1, 3, 8}}}};",
+        "  for (unsigned i = 0; i < sizeof cases / sizeof cases[0]; ++i) {",
+        "    uint64_t need = 0;",
+        f"    int ok = cwb_noalloc_need(cases[i][0], cases[i][1], cases[i][2], {limit}u, &need);",
+        '    printf("%d %" PRIu64 "\\n", ok, need);',
+        "  }",
+        "  return 0; }"]))
+    exe = tmp_path / "need"
+    subprocess.check_call(["gcc", "-std=c11", "-Wall", "-Werror", "-I",
+                           os.path.join(ROOT, "paper_2110_03513_gb300", "csrc"), str(src), "-o", str(exe)])
+    rows = [tuple(int(v) for v in l.split()) for l in subprocess.check_output([str(exe)], text=True).split("\n")
+            if l.strip()]
+    ok = [r[0] for r in rows]
+    assert ok == [0, 0, 0, 0, 1, 1, 0, 0, 0, 1, 0, 1, 0]
+    assert rows[4][1] == 0                                  # no rows: nothing staged
+    assert rows[5][1] == 256 + 4                            # one row of 7 FP64 values: 56 -> 256, + 4
+    for i, (p, xsz) in ((9, (50, 4)), (11, (3, 8))):
+        n_new = (limit - 255) // (xsz * p + 4)
+        want = -(-xsz * p * n_new // 256) * 256 + 4 * n_new
+        assert rows[i][1] == want <= limit

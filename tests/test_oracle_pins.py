@@ -298,6 +298,46 @@ def test_prediction_at_training_points_equals_fitted_vector():
         np.testing.assert_allclose(pred, res.f, atol=1e-10)
 
 
+
+def test_prediction_clamps_to_the_training_range():
+    """Prediction outside [min x, max x] evaluates each learner at the nearest end of its training
+    range (reading R19): the basis comes from scipy's B-spline design matrix at the clamped point,
+    and a linear learner gives theta_0 + theta_1 clamp(x)."""
+    from scipy.interpolate import BSpline
+    rng = np.random.default_rng(31)
+    n = 800
+    X = rng.random((3, n)) * np.array([[2.0], [1.0], [3.0]]) - np.array([[0.5], [0.0], [1.0]])
+    y = np.sin(3 * X[0]) + 0.7 * X[1] - 0.3 * X[2] ** 2 + 0.1 * rng.normal(size=n)
+    specs = [dict(feature=0, n_bins=O.BINS_SQRT), dict(type=O.BL_LINEAR, feature=1, n_bins=O.BINS_SQRT),
+             dict(feature=2, n_bins=O.BINS_SQRT, degree=2, n_knots=12)]
+    res = O.fit(X, y, specs, iterations=60)
+    assert len(set(res.k_sel.tolist())) == 3            # every learner carries coefficients
+    xmin = np.array([X[s["feature"]].min() for s in specs])
+    xmax = np.array([X[s["feature"]].max() for s in specs])
+    span = xmax - xmin
+    # rows far below, just below, at, and above the range of every feature at once
+    offsets = np.array([-3.0, -1e-3, 0.0, 1.0, 1.0 + 1e-3, 4.0])
+    Xnew = np.empty((3, offsets.size))
+    for j in range(3):
+        Xnew[j] = xmin[j] + offsets * span[j]
+    got = O.predict(Xnew, specs, xmin, xmax, res.theta_f, res.offset)
+    want = np.full(offsets.size, res.offset)
+    for k, sp in enumerate(specs):
+        xc = np.clip(Xnew[sp["feature"]], xmin[k], xmax[k])
+        th = res.theta_f[k]
+        if sp.get("type") == O.BL_LINEAR:
+            want += th[0] + th[1] * xc
+            continue
+        q, nk = sp.get("degree", 3), sp.get("n_knots", 20)
+        delta = (xmax[k] - xmin[k]) / (nk + 1)
+        t = xmin[k] + (np.arange(nk + 2 * q + 2) - q) * delta
+        Bm = BSpline.design_matrix(xc, t, q).toarray()
+        want += Bm @ th[: nk + q + 1]
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-12)
+    # outside the range the prediction is flat: equal to the prediction at the nearest end
+    np.testing.assert_allclose(got[0], got[2], rtol=1e-13, atol=1e-13)
+    np.testing.assert_allclose(got[5], got[3], rtol=1e-13, atol=1e-13)
+
 # --------------------------------------------------------------- ACWB (Algorithm 3)
 
 def _read_golden_acwb():
@@ -397,6 +437,55 @@ def test_hybrid_switch_follows_patience_rule_on_recorded_risks():
     assert (res.k_cor[res.switch_iter - 1:] == -1).all()
     assert tr.sum() > 0
 
+
+
+def _closed_form_loss(kind, y, f):
+    """L2: (y - f)^2 / 2; binomial with y in {0, 1}: log(1 + e^f) - y f (reading R17)."""
+    if kind == O.LOSS_L2:
+        return 0.5 * (y - f) ** 2
+    return np.logaddexp(0.0, f) - y * f
+
+
+@pytest.mark.parametrize("kind", [O.LOSS_L2, O.LOSS_BINOMIAL])
+def test_hybrid_validation_risk_is_mean_loss_of_f_on_validation_rows(kind):
+    """Algorithm 4's validation risk after iteration m is the empirical risk R_emp(f^[m] | D_val):
+    the mean over the validation rows of the loss at the primary model f^[m].  Recomputed here with
+    numpy from the f the oracle returns after m iterations (the fit is sequential, so a fit of m
+    iterations ends in the state the m-th iteration of a longer fit passes through), and the
+    patience rule replayed on these recomputed risks, starting from the offset model's risk."""
+    rng = np.random.default_rng(32)
+    n = 420
+    X = rng.random((2, n))
+    eta = 2.0 * np.sin(5 * X[0]) - X[1]
+    if kind == O.LOSS_L2:
+        y = eta + 1.5 * rng.normal(size=n)
+    else:
+        y = (rng.random(n) < 1 / (1 + np.exp(-eta))).astype(np.float64)
+    val = (rng.random(n) < 0.3).astype(np.uint8)
+    for j in range(2):
+        val[np.argmin(X[j])] = 0
+        val[np.argmax(X[j])] = 0
+    specs = [dict(feature=j, n_bins=16) for j in range(2)]
+    kw = dict(loss=kind, opt=O.OPT_HCWB, val_mask=val, gamma=0.5, nu=0.5)
+    pat = 2
+    M = 40
+    full = O.fit(X, y, specs, patience=pat, iterations=M, **kw)
+    vm = val == 1
+    prev = float(np.mean(_closed_form_loss(kind, y[vm], np.full(vm.sum(), full.offset))))
+    counter, switch = 0, 0
+    for m in range(1, M + 1):
+        if counter >= pat:
+            switch = m
+            break
+        f_m = O.fit(X, y, specs, patience=pat, iterations=m, **kw).f
+        risk = float(np.mean(_closed_form_loss(kind, y[vm], f_m[vm])))
+        np.testing.assert_allclose(full.val_risk[m - 1], risk, rtol=1e-12, atol=0.0)
+        # not the training rows' risk (the two differ on this data)
+        assert abs(risk - float(np.mean(_closed_form_loss(kind, y[~vm], f_m[~vm])))) > 1e-6 * risk
+        counter = counter + 1 if risk > prev else 0
+        prev = risk
+    assert switch > 0, "the data should make the validation risk turn up"
+    assert full.switch_iter == switch
 
 def test_binomial_fit_decreases_risk():
     rng = np.random.default_rng(18)
