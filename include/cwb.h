@@ -141,7 +141,7 @@ typedef struct {
  *               during this call.
  *   out         receives the new model (NULL on failure)
  *
- * Errors: CWB_EINVAL for bad sizes, a constant feature (max == min), n* outside
+ * Errors: CWB_EINVAL for bad sizes, non-finite features or targets, a constant feature (max == min), n* outside
  * [2, 65535], d > CWB_MAX_D, binomial targets outside {0, 1}, a categorical feature
  * holding a value that is not a class code 0..c-1, or HCWB without a validation mask
  * holding at least one training and one validation row;
@@ -163,7 +163,11 @@ cwb_status cwb_create(const cwb_config* cfg, const void* X, int32_t x_dtype, int
  * (as CUDA graphs).  The update of the last iteration is folded into the next
  * iteration's row pass; calls that read the fitted values, the trace or the
  * coefficients apply it first.  A device-side wait that ran out is reported by
- * the next call that synchronises, as CWB_ETIMEOUT.
+ * the next call that synchronises, as CWB_ETIMEOUT (the kernel that waited has
+ * returned; the model's state is then undefined, other models are unaffected);
+ * a non-finite residual or criterion (a diverging fit) as CWB_ENUMERIC.  The
+ * limit of the waits is about two seconds; the environment variable
+ * CWB_WAIT_CYCLES, read when a model is created, sets it in SM clock cycles.
  */
 cwb_status cwb_fit(cwb_model* m, int32_t iterations);
 
@@ -265,10 +269,20 @@ cwb_status cwb_get_residuals(const cwb_model* m, int32_t channel, float* out);
  * binnings per warp (lane-private columns), binnings per group, groups, bin ranges,
  * bins per CTA, cluster size, clusters, pipeline stages, threads per CTA,
  * dynamic shared memory bytes, 1 if histograms use exact int32 fixed point,
- * then the scatter CTAs that can be resident at cluster sizes 1, 2, 4 and 8.
+ * then the scatter CTAs that can be resident at cluster sizes 1, 2, 4 and 8,
+ * then 1 if cwb_fit runs the model's iterations as one persistent kernel (see
+ * CWB_ITER_MODE below), that kernel's ring stages, CTAs and shared memory bytes.
  * The cluster size is the largest that keeps nearly every SM busy; the
  * environment variable CWB_CLUSTER_SIZE (1, 2, 4, 8 or 16), read when a model is
  * created, overrides it when that size can be resident.
+ *
+ * CWB_ITER_MODE, read when a model is created: unset or "kernels" runs every
+ * iteration as three kernels (pseudo residuals, binMatVec scatter, solve with the
+ * argmin) launched from CUDA graphs; "persistent" runs plain CWB models (one
+ * residual channel, histograms that fit one CTA) as one cooperative kernel per
+ * cwb_fit call with grid-wide barriers between the phases of an iteration
+ * (cwb_create fails with CWB_EINVAL for a model that does not qualify).  Both
+ * compute the same iteration; results agree within the oracle tolerances.
  */
 cwb_status cwb_get_scatter_plan(const cwb_model* m, int32_t* values, int32_t cap);
 

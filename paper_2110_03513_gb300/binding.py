@@ -215,7 +215,8 @@ def cwb_get_residuals(model, channel: int, out: np.ndarray):
 
 _PLAN_KEYS = ("f_lane", "binnings_per_group", "groups", "bin_ranges", "bins_per_cta", "cluster_size", "clusters",
               "stages", "threads", "smem_bytes", "int_fixed_point", "resident_ctas_cs1", "resident_ctas_cs2",
-              "resident_ctas_cs4", "resident_ctas_cs8")
+              "resident_ctas_cs4", "resident_ctas_cs8", "persistent", "persistent_stages", "persistent_ctas",
+              "persistent_smem_bytes")
 
 
 def cwb_get_scatter_plan(model) -> dict:

@@ -4,6 +4,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -150,7 +151,8 @@ void free_model(cwb_model* m)
     void* bufs[] = {m->ind, m->y, m->y_lo, m->w, m->f, m->h, m->c, m->rw, m->perm, m->zb, m->zb64, m->zcol, m->crange, m->toff, m->ztab, m->G,
                     m->P, m->Acrit, m->Pdf, m->Adf, m->lambda, m->l_bin, m->l_d, m->l_nstar, m->l_type, m->l_xmin, m->l_xmax, m->l_degree,
                     m->l_nknots, m->l_feat, m->part, m->cluster_slot, m->slot_c0, m->theta_it, m->q_it, m->v, m->state, m->risk_part, m->tr_k,
-                    m->tr_mode, m->tr_theta, m->tr_q, m->forced, m->coef};
+                    m->tr_mode, m->tr_theta, m->tr_q, m->forced, m->coef, m->f2, m->uacc, m->gbar, m->ptime, m->ztab_lo,
+                    m->vmax};
     for (void* p : bufs) dev_free(p);
     profile_release(m);
     release_graphs(m);
@@ -194,7 +196,8 @@ cwb_status validate_learner(const cwb_learner& b, int32_t p, int k)
 }
 
 cwb_status create_impl(const cwb_config* cfg, const void* X, int32_t x_dtype, int64_t n, int32_t p, const void* y,
-                       const double* w, const cwb_learner* bl, int32_t K, int32_t device_ptrs, cwb_model** out)
+                       const double* w, const cwb_learner* bl, int32_t K, int32_t device_ptrs, cwb_model** out,
+                       int iter_mode)
 {
     if (!out) { set_error("out is NULL"); return CWB_EINVAL; }
     *out = nullptr;
@@ -230,6 +233,24 @@ cwb_status create_impl(const cwb_config* cfg, const void* X, int32_t x_dtype, in
     m->K = K;
     m->hybrid = cfg->opt == CWB_OPT_HCWB;
     m->accel = cfg->opt != CWB_OPT_CWB;
+    m->iter_mode = iter_mode;
+    if (const char* wc = std::getenv("CWB_WAIT_CYCLES")) {
+        // limit of the device-side ring waits in SM clocks (default ~2 s); a short limit makes a
+        // wait run out on purpose (failure-path tests)
+        const long long v = std::atoll(wc);
+        if (v > 0) m->wait_cycles = v;
+    }
+    if (const char* wt = std::getenv("CWB_WITHHOLD_TILE")) {
+        // failure-path test hook: the first scatter CTA arms this tile's ring stage but never issues its
+        // copies, so the waits on it run out and the kernel returns CWB_ETIMEOUT
+        m->withhold_tile = std::atoi(wt);
+    }
+    if (const char* mode = std::getenv("CWB_ITER_MODE")) {
+        // "kernels" or unset: three kernels per iteration (rows, scatter, solve) launched from CUDA
+        // graphs; "persistent": one persistent cooperative kernel for plain CWB models that qualify
+        if (iter_mode == kIterAuto && std::strcmp(mode, "kernels") == 0) m->iter_mode = kIterKernels;
+        else if (iter_mode == kIterAuto && std::strcmp(mode, "persistent") == 0) m->iter_mode = kIterPersistent;
+    }
     if (cfg->stream) {
         m->stream = static_cast<cudaStream_t>(cfg->stream);
     } else {
@@ -293,6 +314,7 @@ cwb_status create_impl(const cwb_config* cfg, const void* X, int32_t x_dtype, in
         if (st == CWB_OK) st = dev_alloc((void**)&m->v, sizeof(float) * 2 * (size_t)K * S, m->stream);
         if (st == CWB_OK) st = dev_alloc((void**)&m->state, sizeof(DevState), m->stream);
         if (st == CWB_OK) st = dev_alloc((void**)&m->coef, sizeof(double) * 2 * K * D, m->stream);
+        if (st == CWB_OK) st = dev_alloc((void**)&m->vmax, sizeof(float) * K, m->stream);
         if (st == CWB_OK) st = dev_alloc((void**)&l_feat, sizeof(int32_t) * K, m->stream);
         if (st == CWB_OK) {
             m->risk_blocks = 0;
@@ -316,9 +338,15 @@ cwb_status create_impl(const cwb_config* cfg, const void* X, int32_t x_dtype, in
             cudaError_t e = cudaMemcpyAsync(m->state, &s0, sizeof(s0), cudaMemcpyHostToDevice, m->stream);
             if (e == cudaSuccess) e = cudaMemsetAsync(m->v, 0, sizeof(float) * 2 * (size_t)K * S, m->stream);
             if (e == cudaSuccess) e = cudaMemsetAsync(m->coef, 0, sizeof(double) * 2 * K * D, m->stream);
+            if (e == cudaSuccess) e = cudaMemsetAsync(m->vmax, 0, sizeof(float) * K, m->stream);
             if (e != cudaSuccess) st = cuda_status(e, "state init");
         }
         if (st == CWB_OK) st = scatter_count_pass(m);
+        if (st == CWB_OK) st = plan_persistent(m);
+        if (st == CWB_OK && m->iter_mode == kIterPersistent && !m->persist_ok) {
+            set_error("CWB_ITER_MODE=persistent: this model does not qualify for the persistent iteration kernel");
+            st = CWB_EINVAL;
+        }
         if (st == CWB_OK) st = ensure_trace(m, std::max(cfg->iterations, 1));
         if (st == CWB_OK) st = launch_initial_rows(m);
         if (st == CWB_OK) {
@@ -338,6 +366,19 @@ cwb_status create_impl(const cwb_config* cfg, const void* X, int32_t x_dtype, in
 }
 
 }  // namespace
+
+cwb_status create_model(const cwb_config* cfg, const void* X, int32_t x_dtype, int64_t n, int32_t p, const void* y,
+                        const double* w, const cwb_learner* bl, int32_t K, int32_t device_ptrs, cwb_model** out,
+                        int iter_mode)
+{
+    set_error("");
+    try {
+        return create_impl(cfg, X, x_dtype, n, p, y, w, bl, K, device_ptrs, out, iter_mode);
+    } catch (const std::exception& e) {
+        set_error(std::string("host exception: ") + e.what());
+        return CWB_ENOMEM;
+    }
+}
 
 cwb_status launch_predict(const cwb_model* m, const void* Xnew, int x_dtype, int64_t n_new, float* out_dev)
 {
@@ -363,13 +404,7 @@ extern "C" {
 cwb_status cwb_create(const cwb_config* cfg, const void* X, int32_t x_dtype, int64_t n, int32_t p, const void* y,
                       const double* w, const cwb_learner* bl, int32_t K, int32_t device_ptrs, cwb_model** out)
 {
-    set_error("");
-    try {
-        return create_impl(cfg, X, x_dtype, n, p, y, w, bl, K, device_ptrs, out);
-    } catch (const std::exception& e) {
-        set_error(std::string("host exception: ") + e.what());
-        return CWB_ENOMEM;
-    }
+    return create_model(cfg, X, x_dtype, n, p, y, w, bl, K, device_ptrs, out, kIterAuto);
 }
 
 cwb_status cwb_fit(cwb_model* m, int32_t iterations)
@@ -586,8 +621,22 @@ cwb_status cwb_get_residuals(const cwb_model* m, int32_t channel, float* out)
     DeviceGuard guard(m->device);
     std::vector<float> raw(m->n);
     std::vector<int32_t> perm;
-    CWB_CUDA_TRY(cudaMemcpyAsync(raw.data(), m->rw + (int64_t)channel * m->n_pad, sizeof(float) * m->n,
-                                 cudaMemcpyDeviceToHost, m->stream));
+    DevState st;
+    CWB_CUDA_TRY(cudaMemcpyAsync(&st, m->state, sizeof(st), cudaMemcpyDeviceToHost, m->stream));
+    CWB_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    if (st.resid_path == 1) {
+        // the persistent path forms w r inside its scatter: recompute it at the model's current f
+        // (channel 1 is not used by plain CWB)
+        if (channel == 1) {
+            for (int64_t q = 0; q < m->n; ++q) out[q] = 0.0f;
+            return CWB_OK;
+        }
+        CWB_TRY(persistent_residuals(const_cast<cwb_model*>(m), m->rw));
+        CWB_CUDA_TRY(cudaMemcpyAsync(raw.data(), m->rw, sizeof(float) * m->n, cudaMemcpyDeviceToHost, m->stream));
+    } else {
+        CWB_CUDA_TRY(cudaMemcpyAsync(raw.data(), m->rw + (int64_t)channel * m->n_pad, sizeof(float) * m->n,
+                                     cudaMemcpyDeviceToHost, m->stream));
+    }
     if (m->perm) {
         perm.resize(m->n);
         CWB_CUDA_TRY(cudaMemcpyAsync(perm.data(), m->perm, sizeof(int32_t) * m->n, cudaMemcpyDeviceToHost, m->stream));
@@ -625,6 +674,11 @@ cwb_status cwb_profile(cwb_model* m, int32_t enable)
         m->prof_ms[i] = 0.0;
         m->prof_launches[i] = 0;
     }
+    if (m->persist_ok) {
+        double ms3[3];
+        int64_t its = 0;
+        CWB_TRY(persistent_profile(m, ms3, &its, true));
+    }
     const int mask = enable == CWB_PROF_ALL ? 0x7 : ((enable >> 4) & 0x7);
     if (mask != m->prof_mask && m->prof_exec) {
         cudaGraphExecDestroy(m->prof_exec);
@@ -644,6 +698,16 @@ cwb_status cwb_get_profile(cwb_model* m, double* ms, int64_t* launches, int32_t 
     if (!m || cap < 0) { set_error("bad argument"); return CWB_EINVAL; }
     DeviceGuard guard(m->device);
     CWB_TRY(profile_collect(m));
+    if (m->persist_ok) {
+        // phase times of the persistent kernel (rows, scatter, solve with the argmin), per iteration
+        double ms3[3];
+        int64_t its = 0;
+        CWB_TRY(persistent_profile(m, ms3, &its, true));
+        for (int i = 0; i < 3; ++i) {
+            m->prof_ms[i] += ms3[i];
+            m->prof_launches[i] += its;
+        }
+    }
     for (int i = 0; i < cap && i < 4; ++i) {
         if (ms) ms[i] = m->prof_ms[i];
         if (launches) launches[i] = m->prof_launches[i];
@@ -656,10 +720,12 @@ cwb_status cwb_get_scatter_plan(const cwb_model* m, int32_t* values, int32_t cap
     set_error("");
     if (!m || (cap > 0 && !values)) { set_error("bad argument"); return CWB_EINVAL; }
     const ScatterPlan& P = m->plan;
-    const int32_t v[15] = {P.f_lane, P.fe, P.groups, P.bin_ranges, P.nb_cta, P.cs, P.clusters, P.stages, P.threads,
+    const bool pers = m->persist_ok && m->iter_mode != kIterKernels;
+    const int32_t v[19] = {P.f_lane, P.fe, P.groups, P.bin_ranges, P.nb_cta, P.cs, P.clusters, P.stages, P.threads,
                            (int32_t)P.smem, P.int_acc ? 1 : 0, P.active_ctas[0], P.active_ctas[1], P.active_ctas[2],
-                           P.active_ctas[3]};
-    for (int i = 0; i < cap && i < 15; ++i) values[i] = v[i];
+                           P.active_ctas[3], pers ? 1 : 0, pers ? m->pplan.stages : 0, pers ? m->pplan.ctas : 0,
+                           pers ? (int32_t)m->pplan.smem : 0};
+    for (int i = 0; i < cap && i < 19; ++i) values[i] = v[i];
     return CWB_OK;
 }
 

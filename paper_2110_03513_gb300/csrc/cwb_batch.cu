@@ -376,8 +376,10 @@ cwb_status cwb_server_poll(cwb_server* s, int32_t wait, int64_t* done_ids, int32
             s->pending.pop_front();
             Active a;
             if (!r.val_mask.empty()) r.cfg.val_mask = r.val_mask.data();
-            cwb_status st = cwb_create(&r.cfg, r.X, r.x_dtype, r.n, r.p, r.y, r.w, r.bl.data(), (int32_t)r.bl.size(), 0,
-                                       &a.m);
+            // server fits interleave their iterations with other fits on the GPU: the three-kernel path
+            // (a persistent kernel would hold every SM for its whole slice)
+            cwb_status st = create_model(&r.cfg, r.X, r.x_dtype, r.n, r.p, r.y, r.w, r.bl.data(), (int32_t)r.bl.size(), 0,
+                                         &a.m, kIterKernels);
             if (st != CWB_OK) {
                 s->failed[r.id] = cwb_last_error();
                 s->completed += 1;

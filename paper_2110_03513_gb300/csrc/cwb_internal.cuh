@@ -66,7 +66,24 @@ struct DevState {
     uint32_t rmax_bits[2];  // max |w r| and max |w c| of the current iteration (FP32 bits): atomicMax by the
                             // row pass, reset to 0 by the solve's last block
     int32_t cnt_log2[2];    // ceil(log2(largest per-cluster bin count)): [0] all rows, [1] HCWB training rows
-    int32_t cnt_max[2];     // largest per-cluster bin count of the counting passes
+    int32_t cnt_max[2];     // largest per-cluster bin count of the counting passes ([1]: persistent plan)
+    uint32_t rprev_bits;    // max |w r| of the most recently computed residuals (FP32 bits)
+    int32_t cnt_log2p;      // ceil(log2(largest per-CTA bin count)) of the persistent plan
+    int32_t fix_exp;        // fixed-point exponent of the residuals the persistent path wrote last
+    int32_t resid_path;     // 0: the latest residuals are FP32 in rw, 1: fixed point in rq (persistent path)
+};
+
+// How cwb_fit runs iterations: auto picks the persistent kernel when the model qualifies.
+enum : int { kIterAuto = 0, kIterKernels = 1, kIterPersistent = 2 };
+
+// Decomposition of the persistent iteration kernel (cwb_persist.cu).
+struct PersistPlan {
+    int FE, G, per_group, stages, nb, ctas;
+    int64_t tiles;
+    uint32_t ring_off, stage_stride;                           // ring of stages
+    uint32_t f_off, y_off, sel_off, w_off, ylo_off, q_off;     // offsets within a stage (after the index box)
+    uint32_t hist_off, vtab_off;
+    size_t smem;
 };
 
 // Static description of the scatter decomposition (see k_scatter).
@@ -187,6 +204,21 @@ struct cwb_model {
     int graph_iters = 0;
     bool graph_valid_for_batch = false;   // set by a batch capture, cleared when buffers or plans change
     bool use_pdl = true;                  // launch the iteration kernels with programmatic dependencies
+    // persistent iteration kernel (plain CWB): plan, tensor map and buffers
+    int iter_mode = cwb::kIterAuto;
+    bool persist_ok = false;
+    cwb::PersistPlan pplan{};
+    CUtensorMap pmap;
+    float* f2 = nullptr;                  // [n_pad][2] second f buffer (the persistent kernel alternates)
+    long long* uacc = nullptr;            // [2][nb][B] exact histogram sums (bin-major)
+    bool uacc_clean = true;               // both parities of uacc are zero
+    unsigned* gbar = nullptr;             // barrier words, the two residual maxima, one arrival flag per CTA
+    long long* ptime = nullptr;           // [4] phase times and iteration count (profiling)
+    float* ztab_lo = nullptr;             // [K][4 S] low parts of the column-major design
+    float* vmax = nullptr;                // [K] max |v_k| of the latest update tables
+    double wmax = 1.0;                    // largest observation weight
+    long long wait_cycles = 4000000000LL; // limit of each device-side ring wait (SM clocks, ~2 s)
+    int withhold_tile = -1;               // test hook (CWB_WITHHOLD_TILE): a scatter tile whose copies are never issued
 };
 
 namespace cwb {
@@ -245,6 +277,17 @@ cwb_status launch_aggregate(cwb_model* m);
 cwb_status read_device_error(cwb_model* m);
 cwb_status profile_collect(cwb_model* m);
 void profile_release(cwb_model* m);
+
+// Persistent iteration kernel (cwb_persist.cu)
+cwb_status plan_persistent(cwb_model* m);
+cwb_status launch_persistent(cwb_model* m, int32_t iters);
+cwb_status persistent_profile(cwb_model* m, double ms[3], int64_t* iters, bool reset);
+cwb_status persistent_residuals(cwb_model* m, float* out_dev);
+
+// Model creation with an explicit iteration mode (kIterAuto, kIterKernels, kIterPersistent)
+cwb_status create_model(const cwb_config* cfg, const void* X, int32_t x_dtype, int64_t n, int32_t p, const void* y,
+                        const double* w, const cwb_learner* bl, int32_t K, int32_t device_ptrs, cwb_model** out,
+                        int iter_mode);
 
 // Predict / fitted (cwb_api.cu)
 cwb_status launch_predict(const cwb_model* m, const void* Xnew, int x_dtype, int64_t n_new, float* out_dev);

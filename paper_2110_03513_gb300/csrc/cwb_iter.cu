@@ -23,6 +23,7 @@
 #include <cuda.h>
 
 #include "cwb_internal.cuh"
+#include "cwb_device.cuh"
 
 namespace cwb {
 
@@ -36,15 +37,6 @@ constexpr int kGraphIters = 32;
 
 enum { kRowsFused = 0, kRowsUpdate = 1, kRowsResid = 2 };
 
-// Programmatic dependent launch: the iteration's kernels are launched so that each may start
-// while its predecessor drains.  grid_dep_wait() blocks until the predecessor grid has completed
-// and its memory is visible (a no-op without a programmatic dependency); grid_dep_launch() lets
-// the successor grid be scheduled.
-__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-// Release / acquire fence at GPU scope for the last-block tickets (the data behind a ticket is
-// read with L2 loads); cheaper than the sequentially consistent fence of __threadfence().
-__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
 struct RowArgs {
     DevState* state;
@@ -70,99 +62,6 @@ struct RowArgs {
     int patience;
     double* risk_part;
 };
-
-template <typename IndT>
-__device__ __forceinline__ void load_ind4(const IndT* p, int64_t i, int out[4]);
-
-template <>
-__device__ __forceinline__ void load_ind4<uint16_t>(const uint16_t* p, int64_t i, int out[4])
-{
-    uint2 u = *reinterpret_cast<const uint2*>(p + i);
-    out[0] = u.x & 0xffff;
-    out[1] = u.x >> 16;
-    out[2] = u.y & 0xffff;
-    out[3] = u.y >> 16;
-}
-
-template <>
-__device__ __forceinline__ void load_ind4<uint8_t>(const uint8_t* p, int64_t i, int out[4])
-{
-    uint32_t u = *reinterpret_cast<const uint32_t*>(p + i);
-    out[0] = u & 0xff;
-    out[1] = (u >> 8) & 0xff;
-    out[2] = (u >> 16) & 0xff;
-    out[3] = u >> 24;
-}
-
-// ---- compensated ("double-float") arithmetic: a value is hi + lo, two FP32 numbers.
-// The models f and h and the per-iteration coefficients (1 - theta_m, theta_m,
-// nu, eta_m, m/(m+1)) are carried this way so that the only FP32 rounding left
-// in a residual is its own final rounding.  Error-free transforms: TwoSum
-// (Knuth) and the FMA product error.
-struct DF {
-    float hi, lo;
-};
-
-__device__ __forceinline__ DF fast_two_sum(float a, float b)
-{
-    float s = a + b;
-    return {s, b - (s - a)};
-}
-
-__device__ __forceinline__ DF two_sum(float a, float b)
-{
-    float s = a + b;
-    float bb = s - a;
-    return {s, (a - (s - bb)) + (b - bb)};
-}
-
-__device__ __forceinline__ DF df_add(DF a, DF b)
-{
-    DF s = two_sum(a.hi, b.hi);
-    return fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
-}
-
-__device__ __forceinline__ DF df_mul(DF a, DF b)
-{
-    float p = a.hi * b.hi;
-    float e = fmaf(a.hi, b.hi, -p);
-    e = fmaf(a.hi, b.lo, e);
-    e = fmaf(a.lo, b.hi, e);
-    return fast_two_sum(p, e);
-}
-
-__device__ __forceinline__ DF df_mul_f(DF a, float b)
-{
-    float p = a.hi * b;
-    float e = fmaf(a.hi, b, -p);
-    e = fmaf(a.lo, b, e);
-    return fast_two_sum(p, e);
-}
-
-__device__ __forceinline__ DF df_of(double x)
-{
-    float hi = (float)x;
-    return {hi, (float)(x - (double)hi)};
-}
-
-// r = -dL/df at f = g (L2: y - g; binomial: y - sigmoid(g), first order in g.lo).
-__device__ __forceinline__ float neg_gradient(int loss, float y, float ylo, DF g)
-{
-    if (loss == CWB_LOSS_L2) return ((y - g.hi) + ylo) - g.lo;
-    float sg = 1.0f / (1.0f + expf(-g.hi));
-    return (y - sg) - sg * (1.0f - sg) * g.lo;
-}
-
-__device__ __forceinline__ float loss_value(int loss, float y, float ylo, DF f)
-{
-    if (loss == CWB_LOSS_L2) {
-        float e = ((y - f.hi) + ylo) - f.lo;
-        return 0.5f * e * e;
-    }
-    float lse = f.hi > 0.0f ? f.hi + log1pf(expf(-f.hi)) : log1pf(expf(f.hi));
-    float sg = 1.0f / (1.0f + expf(-f.hi));
-    return (lse - y * f.hi) + (sg - y) * f.lo;
-}
 
 __device__ __forceinline__ float get4(const float4& v, int t)
 {
@@ -525,105 +424,11 @@ struct ScatterArgs {
     int stage_cb;                  // bins per chunk of the epilogue's transposing stage
     uint32_t* err;
     int64_t count_rows;            // >= 0: counting pass over this many rows (every row adds 1)
+    long long wait_cycles;         // limit of each ring wait (SM clocks); copies in flight are drained with kWaitCycles
+    int withhold;                  // test hook: >= 0 makes CTA 0 arm, but never fill, its tile min(withhold, ntiles - 1)
 };
 
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait for the phase with the given parity; false once the deadline (SM clock) passed.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long deadline)
-{
-    while (!mbar_try_wait(bar, parity))
-        if (clock64() > deadline) return false;
-    return true;
-}
-
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-        ::"r"(smem_addr(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 ::"r"(smem_addr(dst)), "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_addr(bar))
-                 : "memory");
-}
-
-constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz: a stuck pipeline reports an error
 constexpr int kEpiVec = 4;                         // 16-byte vectors per thread and pass of the cluster epilogue
-
-template <typename IndT>
-__device__ __forceinline__ void unpack16(uint4 raw, int out[16 / sizeof(IndT)]);
-
-template <>
-__device__ __forceinline__ void unpack16<uint16_t>(uint4 raw, int out[8])
-{
-    uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-        out[2 * t] = w[t] & 0xffff;
-        out[2 * t + 1] = w[t] >> 16;
-    }
-}
-
-template <>
-__device__ __forceinline__ void unpack16<uint8_t>(uint4 raw, int out[16])
-{
-    uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-        out[4 * t] = w[t] & 0xff;
-        out[4 * t + 1] = (w[t] >> 8) & 0xff;
-        out[4 * t + 2] = (w[t] >> 16) & 0xff;
-        out[4 * t + 3] = w[t] >> 24;
-    }
-}
-
-// Fixed-point exponent of a histogram channel: values are w r * 2^s rounded to
-// int32.  With max|w r| < 2^e and at most 2^c rows of one cluster in one bin,
-// s = 30 - c - e keeps every cluster sum below 2^30 in magnitude.
-__device__ __forceinline__ int fixed_scale(uint32_t rmax_bits, int cnt_log2)
-{
-    if (rmax_bits == 0) return 100;
-    const int E = (int)((rmax_bits >> 23) & 0xff);
-    const int e = (E == 0) ? -126 : E - 126;
-    return max(-120, min(100, 30 - cnt_log2 - e));
-}
-
-// 2^e as an FP32 value for -126 <= e <= 127 (fixed_scale keeps every exponent used here in range).
-__device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }
 
 // FL2 >= 0: the lanes per channel F = 2^FL2 is a compile-time constant (the common plans), -1: read at run time.
 template <typename IndT, int CMAX, bool INT_ACC, bool RANGED, int FL2>
@@ -684,7 +489,7 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
     const int64_t pieces = (int64_t)ncl * a.cs, piece = (int64_t)cin * a.cs + rank;
     const int64_t t_lo = tiles * piece / pieces, t_hi = tiles * (piece + 1) / pieces;
     const int ntiles = (int)(t_hi - t_lo);
-    const long long deadline = clock64() + kWaitCycles;
+    const long long deadline = clock64() + a.wait_cycles;
 
     if (warp == W) {
         // loader: one 3D TMA box (the tile's rows x FE binnings) and C residual rows per tile
@@ -692,12 +497,16 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
             const uint32_t bytes = (uint32_t)(FE * row_bytes + C * kStageRows * 4);   // box bytes + residual rows
             int issued = 0;
             bool ok = true;
+            // a withheld tile's stage is armed but no copy is issued, so its barrier never completes and
+            // the waits on it run out (the failure-path test); the drain below skips it
+            const int wh = (a.withhold >= 0 && blockIdx.x == 0 && ntiles > 0) ? min(a.withhold, ntiles - 1) : -1;
             // the first ring's index boxes before the wait (their barriers expect the residual
             // bytes too, which follow once the row pass is complete)
             const int early = fixed_mode ? min(a.stages, ntiles) : 0;
             for (int it = 0; it < early; ++it) {
                 const int64_t row0 = (t_lo + it) * kStageRows;
                 mbar_arrive_expect_tx(&full[it], bytes);
+                if (it == wh) continue;
                 tma_load_3d(smem + a.ind_off + (size_t)it * a.stage_ind_bytes, &tmap, 0, g * FE,
                             (int)(row0 / (128 / (int)sizeof(IndT))), &full[it]);
             }
@@ -705,6 +514,10 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
             for (int it = 0; it < early; ++it) {
                 const int64_t row0 = (t_lo + it) * kStageRows;
                 float* r_dst = reinterpret_cast<float*>(smem + a.r_off + (size_t)it * a.stage_r_bytes);
+                if (it == wh) {
+                    ++issued;
+                    continue;
+                }
                 for (int ch = 0; ch < C; ++ch)
                     bulk_load(r_dst + ch * kStageRows, a.rw + ch * a.n_pad + row0, (uint32_t)kStageRows * 4,
                               &full[it]);
@@ -724,6 +537,10 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
                 }
                 const int64_t row0 = (t_lo + it) * kStageRows;
                 mbar_arrive_expect_tx(&full[s], bytes);
+                if (it == wh) {
+                    ++issued;
+                    continue;
+                }
                 tma_load_3d(smem + a.ind_off + (size_t)s * a.stage_ind_bytes, &tmap, 0, g * FE,
                             (int)(row0 / (128 / (int)sizeof(IndT))), &full[s]);
                 float* r_dst = reinterpret_cast<float*>(smem + a.r_off + (size_t)s * a.stage_r_bytes);
@@ -732,12 +549,12 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
                               &full[s]);
                 ++issued;
             }
-            if (!ok) {
-                atomicOr(a.err, kErrTimeout);
-                // let copies already in flight land before the CTA retires
+            if (!ok || wh >= 0) {
+                if (!ok) atomicOr(a.err, kErrTimeout);
+                // let copies already in flight land before the CTA retires (a withheld tile has none)
                 const long long d2 = clock64() + kWaitCycles;
                 for (int it = (issued > a.stages ? issued - a.stages : 0); it < issued; ++it)
-                    mbar_wait(&full[it % a.stages], (it / a.stages) & 1, d2);
+                    if (it != wh) mbar_wait(&full[it % a.stages], (it / a.stages) & 1, d2);
             }
         }
     } else if (warp == W + 1) {
@@ -991,6 +808,7 @@ struct SolveArgs {
     const int32_t* crange;    // [K][D][2]
     const int32_t* toff;      // [K][D]
     const float* ztab;        // [K][4 S]
+    const float* ztab_lo;     // [K][4 S] low parts (float-float design)
     const int32_t* l_bin;
     const int32_t* l_d;
     const int32_t* l_nstar;
@@ -1004,48 +822,8 @@ struct SolveArgs {
     double* tr_q;             // [cap][2]
     const int32_t* forced;    // [cap]
     int trace_cap;
+    float* vmax;              // [K] max |v_k| of channel 0 (the bound of the persistent path's fixed point)
 };
-
-// Criteria are compared as integers: an FP64 value maps to a signed 64-bit key with the
-// same order (negative values have their magnitude bits flipped); the map is its own
-// inverse.  Integer compares keep the argmin off the (slow) FP64 pipe.
-__device__ __forceinline__ long long order_key(double q)
-{
-    const long long b = __double_as_longlong(q);
-    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
-}
-__device__ __forceinline__ double key_value(long long k) { return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffLL)); }
-
-// (best key, index of best, second best key); ties go to the lowest index.
-struct Best2 {
-    long long q1, q2;
-    int k1;
-};
-
-__device__ __forceinline__ Best2 best2_merge(Best2 a, Best2 b)
-{
-    const bool take_b = b.k1 >= 0 && (a.k1 < 0 || b.q1 < a.q1 || (b.q1 == a.q1 && b.k1 < a.k1));
-    Best2 r;
-    if (take_b) {
-        r.q1 = b.q1;
-        r.k1 = b.k1;
-        r.q2 = min(a.q1, min(a.q2, b.q2));
-    } else {
-        r.q1 = a.q1;
-        r.k1 = a.k1;
-        r.q2 = min(a.q2, min(b.q1, b.q2));
-    }
-    return r;
-}
-
-__device__ __forceinline__ Best2 best2_shfl(Best2 x, int o)
-{
-    Best2 y;
-    y.q1 = __shfl_xor_sync(0xffffffffu, x.q1, o);
-    y.q2 = __shfl_xor_sync(0xffffffffu, x.q2, o);
-    y.k1 = __shfl_xor_sync(0xffffffffu, x.k1, o);
-    return y;
-}
 
 __device__ __forceinline__ void cp_async4(void* dst, const void* src)
 {
@@ -1077,12 +855,13 @@ __global__ void __launch_bounds__(kSolveThreads, 512 / kSolveThreads) k_solve(So
     extern __shared__ __align__(16) double dsm[];
     float2* Ps = reinterpret_cast<float2*>(dsm);            // float-float pairs (hi, lo)
     float2* As = Ps + (size_t)D * D;
-    float* u_s = reinterpret_cast<float*>(As + (size_t)D * D);                    // [2][kSolveChunk]
+    DF* u_s = reinterpret_cast<DF*>(As + (size_t)D * D);                          // [2][kSolveChunk] float-float
     long long* pb = reinterpret_cast<long long*>(u_s + 2 * kSolveChunk);          // [2][kSolveChunk]
     float4* zb_s = reinterpret_cast<float4*>(pb + 2 * kSolveChunk);              // [nst] when staged
     int* zc_s = reinterpret_cast<int*>(zb_s + (a.stage_v ? S : 0));
     float* zt_s = reinterpret_cast<float*>(zc_s + (a.stage_v ? ((S + 3) & ~3) : 0));   // [4 nst] when staged
-    __shared__ float s_s[2][kMaxD];
+    float* zl_s = zt_s + (a.stage_z ? kMaxNnz * S : 0);                                 // low parts, [4 nst]
+    __shared__ DF s_s[2][kMaxD];
     __shared__ double th_s[2][kMaxD];
     __shared__ DF term[2][kMaxD];
     __shared__ bool is_last;
@@ -1102,7 +881,11 @@ __global__ void __launch_bounds__(kSolveThreads, 512 / kSolveThreads) k_solve(So
         }
         if (a.stage_z) {
             const float4* zt4 = reinterpret_cast<const float4*>(a.ztab + (int64_t)k * kMaxNnz * S);
-            for (int e = tid; e < nst; e += blockDim.x) cp_async16(reinterpret_cast<float4*>(zt_s) + e, zt4 + e);
+            const float4* zl4 = reinterpret_cast<const float4*>(a.ztab_lo + (int64_t)k * kMaxNnz * S);
+            for (int e = tid; e < nst; e += blockDim.x) {
+                cp_async16(reinterpret_cast<float4*>(zt_s) + e, zt4 + e);
+                cp_async16(reinterpret_cast<float4*>(zl_s) + e, zl4 + e);
+            }
         }
     }
     auto stage_pa = [&](int ph) {          // P and A of the cache `ph`
@@ -1115,6 +898,7 @@ __global__ void __launch_bounds__(kSolveThreads, 512 / kSolveThreads) k_solve(So
     };
     if (!a.hybrid) stage_pa(0);
     const float* zt = a.stage_z ? zt_s : a.ztab + (int64_t)k * kMaxNnz * S;
+    const float* ztl = a.stage_z ? zl_s : a.ztab_lo + (int64_t)k * kMaxNnz * S;
     const float4* zbp = a.stage_v ? zb_s : reinterpret_cast<const float4*>(a.zb) + (int64_t)k * S;
     const int* zcp = a.stage_v ? zc_s : a.zcol + (int64_t)k * S;
     int c_lo[kColsPerWarp], c_len[kColsPerWarp], c_off[kColsPerWarp];
@@ -1132,7 +916,7 @@ __global__ void __launch_bounds__(kSolveThreads, 512 / kSolveThreads) k_solve(So
     }
     if (tid < 2 * kMaxD) {
         th_s[tid / kMaxD][tid % kMaxD] = 0.0;
-        s_s[tid / kMaxD][tid % kMaxD] = 0.0f;
+        s_s[tid / kMaxD][tid % kMaxD] = DF{0.0f, 0.0f};
     }
     // Thread (i, half) sums bins 4i..4i+3 of a chunk over the clusters of parity `half`; the
     // clusters holding a bin are those of its slot (binning group x bin range)
@@ -1162,9 +946,9 @@ __global__ void __launch_bounds__(kSolveThreads, 512 / kSolveThreads) k_solve(So
 
     // ---- u = sum of the slot's partial histograms, then s = Z^b^T u, in chunks of bins
     const int64_t cl_stride = (int64_t)a.cmax * a.F * a.nb_cta;
-    float acc0[kColsPerWarp], acc1[kColsPerWarp];
+    DF acc0[kColsPerWarp], acc1[kColsPerWarp];
 #pragma unroll
-    for (int c = 0; c < kColsPerWarp; ++c) acc0[c] = acc1[c] = 0.0f;
+    for (int c = 0; c < kColsPerWarp; ++c) acc0[c] = acc1[c] = DF{0.0f, 0.0f};
     for (int L0 = 0; L0 < nst; L0 += kSolveChunk) {
         const int L1 = min(nst, L0 + kSolveChunk);
         const bool mine = 4 * gi < L1 - L0;
@@ -1226,17 +1010,20 @@ __global__ void __launch_bounds__(kSolveThreads, 512 / kSolveThreads) k_solve(So
 #pragma unroll
             for (int ch = 0; ch < 2; ++ch) {
                 if (ch >= C) continue;
-                float o[4];
+                DF o[4];
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
                     if (INT_ACC) {
+                        // the exact integer sum as a float-float pair (48 bits), power-of-two scale
                         const long long tot = it0[ch][t] + pb[ch * kSolveChunk + 4 * gi + t];
-                        o[t] = (float)tot * (ch ? scl1 : scl0);     // exact sum, one rounding, power-of-two scale
+                        o[t] = df_scale(df_of_ll(tot), ch ? scl1 : scl0);
                     } else {
-                        o[t] = (ft[ch][t] - fc[ch][t]) + reinterpret_cast<float*>(pb)[ch * kSolveChunk + 4 * gi + t];
+                        o[t] = df_add(DF{ft[ch][t], -fc[ch][t]},
+                                      DF{reinterpret_cast<float*>(pb)[ch * kSolveChunk + 4 * gi + t], 0.0f});
                     }
                 }
-                *reinterpret_cast<float4*>(u_s + ch * kSolveChunk + 4 * gi) = make_float4(o[0], o[1], o[2], o[3]);
+                *reinterpret_cast<float4*>(u_s + ch * kSolveChunk + 4 * gi) = make_float4(o[0].hi, o[0].lo, o[1].hi, o[1].lo);
+                *reinterpret_cast<float4*>(u_s + ch * kSolveChunk + 4 * gi + 2) = make_float4(o[2].hi, o[2].lo, o[3].hi, o[3].lo);
             }
         }
         if (L0 == 0) cp_async_wait_all();              // the design must be in shared memory before s
@@ -1245,10 +1032,12 @@ __global__ void __launch_bounds__(kSolveThreads, 512 / kSolveThreads) k_solve(So
         for (int c = 0; c < kColsPerWarp; ++c) {
             const int from = max(c_lo[c], L0), to = min(c_lo[c] + c_len[c], L1);
             const float* zc = zt + c_off[c] - c_lo[c];
+            const float* zcl = ztl + c_off[c] - c_lo[c];
             for (int t = from + lane; t < to; t += 32) {
-                const float z = zc[t];
-                acc0[c] = fmaf(z, u_s[t - L0], acc0[c]);
-                if (C == 2) acc1[c] = fmaf(z, u_s[kSolveChunk + t - L0], acc1[c]);
+                // s in float-float: the design as (hi, lo) pairs times the float-float sums
+                const DF z = {zc[t], zcl[t]};
+                acc0[c] = df_add(acc0[c], df_mul(z, u_s[t - L0]));
+                if (C == 2) acc1[c] = df_add(acc1[c], df_mul(z, u_s[kSolveChunk + t - L0]));
             }
         }
         __syncthreads();
@@ -1257,9 +1046,9 @@ __global__ void __launch_bounds__(kSolveThreads, 512 / kSolveThreads) k_solve(So
     for (int c = 0; c < kColsPerWarp; ++c) {
         const int j = warp + c * NW;
         if (j >= d) break;                    // warp-uniform
-        for (int o = 16; o > 0; o >>= 1) acc0[c] += __shfl_xor_sync(0xffffffffu, acc0[c], o);
+        for (int o = 16; o > 0; o >>= 1) acc0[c] = df_add(acc0[c], df_shfl_xor(acc0[c], o));
         if (C == 2)
-            for (int o = 16; o > 0; o >>= 1) acc1[c] += __shfl_xor_sync(0xffffffffu, acc1[c], o);
+            for (int o = 16; o > 0; o >>= 1) acc1[c] = df_add(acc1[c], df_shfl_xor(acc1[c], o));
         if (lane == 0) {
             s_s[0][j] = acc0[c];
             s_s[1][j] = acc1[c];
@@ -1285,7 +1074,7 @@ __global__ void __launch_bounds__(kSolveThreads, 512 / kSolveThreads) k_solve(So
         if (valid)
             for (int j = q; j < d; j += 8) {
                 const float2 mij = Mx[i * D + j];
-                p = df_add(p, df_mul_f(DF{mij.x, mij.y}, s_s[ch][j]));
+                p = df_add(p, df_mul(DF{mij.x, mij.y}, s_s[ch][j]));
             }
 #pragma unroll 1
         for (int o = 1; o < 8; o <<= 1) {
@@ -1293,7 +1082,7 @@ __global__ void __launch_bounds__(kSolveThreads, 512 / kSolveThreads) k_solve(So
             p = df_add(p, other);
         }
         if (valid && q == 0) {
-            if (mat) term[ch][i] = df_mul_f(p, s_s[ch][i]);
+            if (mat) term[ch][i] = df_mul(p, s_s[ch][i]);
             else th_s[ch][i] = (double)p.hi + (double)p.lo;
         }
     }
@@ -1328,7 +1117,8 @@ __global__ void __launch_bounds__(kSolveThreads, 512 / kSolveThreads) k_solve(So
         const int ch = e / D, i = e - (e / D) * D;
         a.theta_it[((int64_t)ch * a.K + k) * D + i] = th_s[ch][i];
     }
-    // ---- update table of this learner, v_k = Z^b theta (FP32)
+    // ---- update table of this learner, v_k = Z^b theta (FP32), and max |v_k| of channel 0
+    float vm = 0.0f;
     for (int e = tid; e < C * nst; e += blockDim.x) {
         const int ch = e >= nst ? 1 : 0, l = e - ch * nst;
         const int c0 = zcp[l];
@@ -1339,6 +1129,16 @@ __global__ void __launch_bounds__(kSolveThreads, 512 / kSolveThreads) k_solve(So
         if (c0 + 2 < D) acc = fmaf(z.z, (float)th_s[ch][c0 + 2], acc);
         if (c0 + 3 < D) acc = fmaf(z.w, (float)th_s[ch][c0 + 3], acc);
         a.v[((int64_t)ch * a.K + k) * S + l] = acc;
+        if (ch == 0) vm = fmaxf(vm, fabsf(acc));
+    }
+    for (int o = 16; o > 0; o >>= 1) vm = fmaxf(vm, __shfl_xor_sync(0xffffffffu, vm, o));
+    __shared__ float vm_w[NW];
+    if (lane == 0) vm_w[warp] = vm;
+    __syncthreads();
+    if (tid == 0) {
+        float mx = 0.0f;
+        for (int w2 = 0; w2 < NW; ++w2) mx = fmaxf(mx, vm_w[w2]);
+        a.vmax[k] = mx;
     }
     // ---- last CTA: argmin per channel, trace, state -- one warp (no block barriers on the
     // iteration's critical path)
@@ -1416,6 +1216,8 @@ __global__ void __launch_bounds__(kSolveThreads, 512 / kSolveThreads) k_solve(So
         S_->k_cor = (C == 2) ? best_k[1] : -1;
         S_->pend_mode = mode;
         S_->m = st.m + 1;
+        S_->rprev_bits = S_->rmax_bits[0];   // max |w r| of this iteration (input of the persistent path's bound)
+        S_->resid_path = 0;
         S_->rmax_bits[0] = 0u;           // the next row pass takes its maxima with atomicMax
         S_->rmax_bits[1] = 0u;
         S_->ticket_solve = 0;
@@ -1574,6 +1376,8 @@ ScatterArgs scatter_args(cwb_model* m)
     a.stage_cb = P.stage_cb;
     a.err = &m->state->err;
     a.count_rows = -1;
+    a.wait_cycles = m->wait_cycles;
+    a.withhold = m->withhold_tile;
     return a;
 }
 
@@ -1600,9 +1404,9 @@ size_t solve_smem(const cwb_model* m, bool stage_v, bool stage_z)
     const size_t S = m->nstar_max;
     const size_t chunk = solve_chunk(solve_threads(m));
     size_t b = sizeof(float2) * 2 * (size_t)m->d_max * m->d_max;        // P, A (float-float pairs)
-    b += sizeof(float) * 2 * chunk + sizeof(long long) * 2 * chunk;      // u chunk, half sums
+    b += sizeof(float2) * 2 * chunk + sizeof(long long) * 2 * chunk;     // u chunk (float-float), half sums
     if (stage_v) b += 16 * S + 4 * ((S + 3) & ~size_t(3));              // design rows, first columns
-    if (stage_z) b += sizeof(float) * kMaxNnz * S;                       // column-major design
+    if (stage_z) b += 2 * sizeof(float) * kMaxNnz * S;                   // column-major design (hi, lo)
     return b;
 }
 
@@ -1629,6 +1433,7 @@ void launch_solve(cwb_model* m, cudaStream_t s)
     a.crange = m->crange;
     a.toff = m->toff;
     a.ztab = m->ztab;
+    a.ztab_lo = m->ztab_lo;
     a.l_bin = m->l_bin;
     a.l_d = m->l_d;
     a.l_nstar = m->l_nstar;
@@ -1642,6 +1447,7 @@ void launch_solve(cwb_model* m, cudaStream_t s)
     a.tr_q = m->tr_q;
     a.forced = m->forced;
     a.trace_cap = m->trace_cap;
+    a.vmax = m->vmax;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(m->K, 1, 1);
     const int threads = solve_threads(m);
@@ -1958,6 +1764,8 @@ cwb_status scatter_count_pass(cwb_model* m)
     for (int idx = 0; idx < passes; ++idx) {
         ScatterArgs a = scatter_args(m);
         a.count_rows = idx == 1 ? m->n_tr : m->n;
+        a.wait_cycles = kWaitCycles;             // setup work: the default limit
+        a.withhold = -1;
         CWB_CUDA_TRY(launch_scatter_args(m, m->stream, a, true));
         const int64_t total = (int64_t)P.clusters * P.nb_cta * P.f_lane;
         const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(4 * num_sms(m->device), (total + 255) / 256));
@@ -2163,6 +1971,11 @@ cwb_status launch_iterations(cwb_model* m, int32_t iters)
 {
     if (iters <= 0) return CWB_OK;
     CWB_TRY(prepare_launch(m, iters));
+    if (m->persist_ok && m->iter_mode != kIterKernels) {
+        CWB_TRY(launch_persistent(m, iters));
+        note_iterations_queued(m, iters);
+        return CWB_OK;
+    }
     if (m->prof_on) {
         if (!m->prof_exec) CWB_TRY(capture_graph(m, 1, m->prof_mask, &m->prof_exec));
         for (int32_t i = 0; i < iters; ++i) {

@@ -72,6 +72,13 @@ __global__ void k_check_binary(const T* __restrict__ y, int64_t n, uint32_t* bad
 }
 
 template <typename T>
+__global__ void k_check_finite(const T* __restrict__ v, int64_t n, uint32_t* bad)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (!isfinite((double)v[i])) atomicOr(bad, 1u);
+}
+
+template <typename T>
 __global__ void k_check_weights(const T* __restrict__ w, int64_t n, uint32_t* bad)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -444,6 +451,25 @@ __global__ void k_build_ztab(int S, int D, const int32_t* __restrict__ l_d, cons
         for (int l = lo; l < hi; ++l) {
             const int t = j - zcol[(int64_t)k * S + l];
             out[l - lo] = (t >= 0 && t < kMaxNnz) ? zb[((int64_t)k * S + l) * kMaxNnz + t] : 0.0f;
+        }
+    }
+}
+
+// Low parts of the column-major design, ztab_lo = z - (float)z from the FP64 basis values: with
+// ztab they hold every design value as a float-float pair for the solve's s = Z^b^T u.
+__global__ void k_build_ztab_lo(int S, int D, const int32_t* __restrict__ l_d, const double* __restrict__ zb64,
+                                const int32_t* __restrict__ zcol, const int32_t* __restrict__ crange,
+                                const int32_t* __restrict__ toff, float* __restrict__ ztab_lo)
+{
+    const int k = blockIdx.x;
+    const int d = l_d[k];
+    for (int j = threadIdx.x; j < d; j += blockDim.x) {
+        const int lo = crange[((int64_t)k * D + j) * 2], hi = crange[((int64_t)k * D + j) * 2 + 1];
+        float* out = ztab_lo + (int64_t)k * kMaxNnz * S + toff[(int64_t)k * D + j];
+        for (int l = lo; l < hi; ++l) {
+            const int t = j - zcol[(int64_t)k * S + l];
+            const double z = (t >= 0 && t < kMaxNnz) ? zb64[((int64_t)k * S + l) * kMaxNnz + t] : 0.0;
+            out[l - lo] = (float)(z - (double)(float)z);
         }
     }
 }
@@ -925,6 +951,10 @@ cwb_status setup_model(cwb_model* m, const void* X_in, int x_dtype, const void* 
         if (x_dtype == CWB_F64) k_check_binary<<<g_rows, kThreads, 0, s>>>((const double*)yd, n, flags);
         else k_check_binary<<<g_rows, kThreads, 0, s>>>((const float*)yd, n, flags);
     }
+    {
+        if (x_dtype == CWB_F64) k_check_finite<<<g_rows, kThreads, 0, s>>>((const double*)yd, n, flags + 5);
+        else k_check_finite<<<g_rows, kThreads, 0, s>>>((const float*)yd, n, flags + 5);
+    }
     if (wd) k_check_weights<<<g_rows, kThreads, 0, s>>>(wd, n, flags + 1);
 
     // --- y, w in the fitting order (FP64 copies kept for the offset and the counts)
@@ -979,6 +1009,7 @@ cwb_status setup_model(cwb_model* m, const void* X_in, int x_dtype, const void* 
     if (flags_h[0]) { set_error("binomial loss needs targets in {0, 1}"); return CWB_EINVAL; }
     if (flags_h[1]) { set_error("observation weights must be finite and > 0"); return CWB_EINVAL; }
     if (flags_h[2]) { set_error("features must be finite"); return CWB_EINVAL; }
+    if (flags_h[5]) { set_error("targets must be finite"); return CWB_EINVAL; }
     if (flags_h[4]) { set_error("a categorical feature holds a value that is not a class code 0..c-1"); return CWB_EINVAL; }
     for (int b = 0; b < B; ++b) {
         if (!(xmax_h[b] > xmin_h[b])) {
@@ -1150,6 +1181,9 @@ cwb_status setup_model(cwb_model* m, const void* X_in, int x_dtype, const void* 
         CWB_TRY(dev_alloc((void**)&m->ztab, sizeof(float) * (size_t)K * kMaxNnz * S, s));
         CWB_CUDA_TRY(cudaMemsetAsync(m->ztab, 0, sizeof(float) * (size_t)K * kMaxNnz * S, s));
         k_build_ztab<<<K, 64, 0, s>>>(S, D, m->l_d, m->zb, m->zcol, m->crange, m->toff, m->ztab);
+        CWB_TRY(dev_alloc((void**)&m->ztab_lo, sizeof(float) * (size_t)K * kMaxNnz * S, s));
+        CWB_CUDA_TRY(cudaMemsetAsync(m->ztab_lo, 0, sizeof(float) * (size_t)K * kMaxNnz * S, s));
+        k_build_ztab_lo<<<K, 64, 0, s>>>(S, D, m->l_d, m->zb64, m->zcol, m->crange, m->toff, m->ztab_lo);
     }
 
     // --- weighted bin counts per phase: phase 0 = fitting rows of the first phase, phase 1 = all rows

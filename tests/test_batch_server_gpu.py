@@ -58,15 +58,27 @@ def test_autotuned_plan_keeps_parity(cwb):
         model.free()
 
 
-def test_batch_equals_individual_fits(cwb):
+def test_batch_equals_individual_fits(cwb, monkeypatch):
     M = 70                                  # two graph launches of 32 and six single iterations
     fits = _fit_specs()
-    alone = []
+    alone, alone_persistent = [], []
     for data, specs, nu in fits:
+        # the batch runs the three-kernel path: alone on the same path it must agree bit for bit;
+        # alone on the persistent path (opt-in for plain CWB) within the parity tolerance
         m = cwb.Model(data.X, data.y, _learners(cwb, specs), nu=nu, iterations=M, device=0)
         m.fit(M)
         alone.append(_state(m, M))
         m.free()
+        monkeypatch.setenv("CWB_ITER_MODE", "persistent")
+        m = cwb.Model(data.X, data.y, _learners(cwb, specs), nu=nu, iterations=M, device=0)
+        monkeypatch.delenv("CWB_ITER_MODE")
+        m.fit(M)
+        alone_persistent.append(_state(m, M))
+        m.free()
+    for (k_a, th_a, f_a), (k_p, th_p, f_p) in zip(alone, alone_persistent):
+        np.testing.assert_array_equal(k_a, k_p)
+        assert rel_err(th_p, th_a) <= REL_TOL
+        assert rel_err(f_p, f_a) <= REL_TOL
     models = [cwb.Model(data.X, data.y, _learners(cwb, specs), nu=nu, iterations=M, device=0) for data, specs, nu in fits]
     batch = cwb.Batch(models, iters_per_launch=32)
     batch.fit(M)

@@ -432,3 +432,83 @@ def test_full_size_hcwb_binomial_first_iterations(cwb):
     specs = [dict(feature=j, n_bins=1414) for j in range(200)]
     run_pair(cwb, data.X, data.y, specs, M=6, loss=1, opt=2, nu=0.1, gamma=0.001, patience=5,
              val_mask=data.val_mask, check_predict=False)
+
+
+def test_full_size_hcwb_switch_at_first_iteration(cwb):
+    """n = 2,000,000, p = 200, n* = 1414, binomial HCWB with patience 0: the switch to CWB on all rows
+    happens at iteration 1, so the CWB phase (all-row caches, one-channel plan) runs at full size."""
+    data = S.sim_binomial_hybrid(seed=2)
+    specs = [dict(feature=j, n_bins=1414) for j in range(200)]
+    model, ref = run_pair(cwb, data.X, data.y, specs, M=4, loss=1, opt=2, nu=0.1, gamma=0.001, patience=0,
+                          val_mask=data.val_mask, check_predict=False)
+    assert ref.switch_iter == 1
+    model.free()
+
+
+# ------------------------------------------------------------------ criterion precision at near ties
+
+def _near_tie_data(n, moved, seed):
+    """Feature 1 is a copy of feature 0 with `moved` rows shifted by one bin width (the grid and the
+    range stay the same), so the two learners' SSEs differ by a tiny relative amount while the
+    winner explains most of r^T r; feature 2 is noise."""
+    rng = np.random.default_rng(seed)
+    x0 = rng.random(n)
+    y = 2.0 * np.sin(2 * np.pi * x0) + rng.normal(size=n)
+    nstar = int(np.floor(np.sqrt(n)))
+    h = (x0.max() - x0.min()) / (nstar - 1)
+    x1 = x0.copy()
+    idx = rng.choice(np.flatnonzero((x0 > x0.min() + 2 * h) & (x0 < x0.max() - 2 * h)), size=moved, replace=False)
+    x1[idx] += h * np.where(rng.random(moved) < 0.5, -1.0, 1.0)
+    return np.stack([x0, x1, rng.random(n)]), y
+
+
+@pytest.mark.parametrize("moved,seed", [(1, 0), (1, 1), (1, 3), (2, 2), (4, 0), (8, 1)])
+def test_near_tie_picks_the_oracle_learner(cwb, moved, seed):
+    """The criterion separates learners whose first-iteration SSE gap, relative to the SSE, lies between
+    1e-9 and 1e-6 while the winner explains about twice r^T r minus its SSE (|Q| / SSE ~ 1.9): the
+    GPU's sequence must equal the oracle's with no teacher forcing."""
+    X, y = _near_tie_data(200_000, moved, seed)
+    specs = [dict(feature=j, n_bins=-1, df=5.0) for j in range(3)]
+    M = 6
+    ref = O.fit(X, y, specs, iterations=M)
+    gaps = (ref.sse_second - ref.sse_best) / ref.sse_best
+    r0 = y - ref.offset
+    assert 1e-9 < gaps[0] < 1e-6 and (r0 @ r0 - ref.sse_best[0]) / ref.sse_best[0] > 0.05
+    model = cwb.Model(np.ascontiguousarray(X.astype(np.float32)), y.astype(np.float32), _specs_to_gpu(cwb, specs),
+                      nu=0.1, iterations=M, device=0)
+    model.fit(M)
+    k_sel, _, _ = model.trace()
+    above = gaps > 1e-9
+    np.testing.assert_array_equal(k_sel[above], ref.k_sel[above])
+    model.free()
+
+
+# ------------------------------------------------------------------ the persistent iteration kernel (opt-in)
+
+@pytest.mark.parametrize("case", ["l2_uint16", "l2_weights_f64_uint8", "binomial", "two_groups"])
+def test_persistent_path_matches_oracle(cwb, monkeypatch, case):
+    """CWB_ITER_MODE=persistent runs plain CWB as one cooperative kernel (row pass folded into the
+    scatter, fixed-point scale from a bound, exact int64 sums, float-float solve); same oracle
+    tolerances as the kernel path."""
+    monkeypatch.setenv("CWB_ITER_MODE", "persistent")
+    w = None
+    if case == "l2_uint16":
+        data = S.additive_regression(150_001, 8, 5, seed=71, dtype=np.float32)
+        specs = [dict(feature=j, n_bins=-1) for j in range(8)]
+        kw = dict(M=50)
+    elif case == "l2_weights_f64_uint8":
+        data = S.additive_regression(40_000, 6, 4, seed=72, dtype=np.float64)
+        specs = [dict(feature=j, n_bins=200, df=4.0) for j in range(6)]
+        w = np.random.default_rng(3).uniform(0.5, 2.0, size=40_000)
+        kw = dict(M=40, nu=0.3)
+    elif case == "binomial":
+        data = S.sim_binomial_hybrid(seed=73, n=120_000, p=7, n_informative=4)
+        specs = [dict(feature=j, n_bins=-1) for j in range(7)]
+        kw = dict(M=40, loss=1)
+    else:
+        data = S.additive_regression(90_000, 40, 6, seed=74, dtype=np.float32)
+        specs = [dict(feature=j, n_bins=-1) for j in range(40)]
+        kw = dict(M=30)
+    model, ref = run_pair(cwb, data.X, data.y, specs, w=w, **kw)
+    assert model.scatter_plan()["persistent"] == 1
+    model.free()
