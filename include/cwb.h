@@ -380,6 +380,44 @@ cwb_status cwb_server_take(cwb_server* s, int64_t id, cwb_model** out);
 cwb_status cwb_server_stats(const cwb_server* s, int64_t* values, int32_t cap);
 void cwb_server_free(cwb_server* s);
 
+/*
+ * Row shards -- the rows of one fit split over several GPUs (one process and one model per GPU).
+ * binMatVec sums over rows (Algorithm 2), so every shard scatters its own rows and the
+ * histograms are added across shards; every shard then runs the same solve and argmin on the
+ * same totals and keeps its rows' f in step.  The caller moves the data between shards (an
+ * all-reduce of its communication library, or a plain sum when the shards share a process):
+ *
+ *   setup      cwb_shard_create on each shard's rows with the feature ranges and the row count of
+ *              all shards (n* = floor(sqrt(n_global)) for CWB_BINS_SQRT), then cwb_shard_stats
+ *              (bin counts [B][S] and {sum of y, rows}: SUM over shards; the bin-count bound of
+ *              the scatter: MAX) and cwb_shard_finish with the totals: Z^T Z, lambda and the
+ *              cached inverse from the counts of all rows, the offset from all rows.
+ *   iteration  cwb_shard_rows (pending update, pseudo residuals of the shard's rows, their
+ *              max |r|: MAX over shards), cwb_shard_scatter with that maximum (the common
+ *              fixed-point scale; u = the shard's exact histogram sums, int64 [B][S]: SUM over
+ *              shards; integer sums, so the total does not depend on the order of the
+ *              additions), cwb_shard_solve with the total.
+ *
+ * Plain CWB, unweighted rows, equidistant (or categorical) binnings.  B and S come from
+ * cwb_shard_sizes.  Buffers follow device_ptrs (device buffers on the shard's device let
+ * the exchange run without host copies).  cwb_fit is not available on a shard; the getters
+ * (trace, coefficients, fitted values of the shard's rows, prediction) are.
+ */
+typedef struct {
+    int64_t n_global;     /* rows of all shards together */
+    const double* xmin;   /* p per-feature minima over all shards' rows (host memory) */
+    const double* xmax;   /* p per-feature maxima over all shards' rows (host memory) */
+} cwb_shard_config;
+cwb_status cwb_shard_create(const cwb_config* cfg, const void* X, int32_t x_dtype, int64_t n, int32_t p, const void* y,
+                            const cwb_learner* bl, int32_t K, int32_t device_ptrs, const cwb_shard_config* sc,
+                            cwb_model** out);
+cwb_status cwb_shard_sizes(const cwb_model* m, int32_t* B, int32_t* S);
+cwb_status cwb_shard_stats(cwb_model* m, double* counts, double* sums, int32_t* cnt_log2);
+cwb_status cwb_shard_finish(cwb_model* m, const double* counts, const double* sums, int32_t cnt_log2);
+cwb_status cwb_shard_rows(cwb_model* m, float* rmax, int32_t device_ptrs);
+cwb_status cwb_shard_scatter(cwb_model* m, const float* rmax, int64_t* u, int32_t device_ptrs);
+cwb_status cwb_shard_solve(cwb_model* m, const int64_t* u, int32_t device_ptrs);
+
 /* cwb_synchronize -- wait for the model's queued work; reports device-side errors. */
 cwb_status cwb_synchronize(cwb_model* m);
 

@@ -49,6 +49,10 @@ class cwb_server_config(C.Structure):
                 ("slice_iterations", C.c_int32)]
 
 
+class cwb_shard_config(C.Structure):
+    _fields_ = [("n_global", C.c_int64), ("xmin", C.c_void_p), ("xmax", C.c_void_p)]
+
+
 class cwb_learner_info(C.Structure):
     _fields_ = [("d", C.c_int32), ("nstar", C.c_int32), ("binning", C.c_int32), ("reserved", C.c_int32),
                 ("xmin", C.c_double), ("xmax", C.c_double), ("lam", C.c_double), ("lam_full", C.c_double)]
@@ -87,6 +91,15 @@ _SIGS = {
     "cwb_server_take": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_void_p)]),
     "cwb_server_stats": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
     "cwb_server_free": (None, [C.c_void_p]),
+    "cwb_shard_create": (C.c_int, [C.POINTER(cwb_config), C.c_void_p, C.c_int32, C.c_int64, C.c_int32, C.c_void_p,
+                                   C.POINTER(cwb_learner), C.c_int32, C.c_int32, C.POINTER(cwb_shard_config),
+                                   C.POINTER(C.c_void_p)]),
+    "cwb_shard_sizes": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "cwb_shard_stats": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "cwb_shard_finish": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
+    "cwb_shard_rows": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
+    "cwb_shard_scatter": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
+    "cwb_shard_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
     "cwb_last_error": (C.c_char_p, []),
     "cwb_free": (None, [C.c_void_p]),
 }
@@ -207,6 +220,47 @@ def cwb_get_bin_index(model, k: int, ind: np.ndarray):
 
 def cwb_force_selection(model, k_forced: np.ndarray):
     _check(load_library().cwb_force_selection(model, _ptr(k_forced), k_forced.size), "cwb_force_selection")
+
+
+def cwb_shard_create(cfg: cwb_config, X, x_dtype: int, n: int, p: int, y, learners, device_ptrs: int,
+                     n_global: int, xmin: np.ndarray, xmax: np.ndarray) -> C.c_void_p:
+    arr = (cwb_learner * len(learners))(*learners)
+    xmin = np.ascontiguousarray(xmin, dtype=np.float64)
+    xmax = np.ascontiguousarray(xmax, dtype=np.float64)
+    sc = cwb_shard_config(n_global=n_global, xmin=_ptr(xmin).value, xmax=_ptr(xmax).value)
+    out = C.c_void_p()
+    st = load_library().cwb_shard_create(C.byref(cfg), _ptr(X), x_dtype, n, p, _ptr(y), arr, len(learners), device_ptrs,
+                                         C.byref(sc), C.byref(out))
+    _check(st, "cwb_shard_create")
+    return out
+
+
+def cwb_shard_sizes(model) -> tuple[int, int]:
+    b, s = C.c_int32(0), C.c_int32(0)
+    _check(load_library().cwb_shard_sizes(model, C.byref(b), C.byref(s)), "cwb_shard_sizes")
+    return b.value, s.value
+
+
+def cwb_shard_stats(model, counts: np.ndarray, sums: np.ndarray) -> int:
+    c = C.c_int32(0)
+    _check(load_library().cwb_shard_stats(model, _ptr(counts), _ptr(sums), C.byref(c)), "cwb_shard_stats")
+    return c.value
+
+
+def cwb_shard_finish(model, counts: np.ndarray, sums: np.ndarray, cnt_log2: int):
+    _check(load_library().cwb_shard_finish(model, _ptr(counts), _ptr(sums), cnt_log2), "cwb_shard_finish")
+
+
+def cwb_shard_rows(model, rmax, device_ptrs: int = 0):
+    _check(load_library().cwb_shard_rows(model, _ptr(rmax), device_ptrs), "cwb_shard_rows")
+
+
+def cwb_shard_scatter(model, rmax, u, device_ptrs: int = 0):
+    _check(load_library().cwb_shard_scatter(model, _ptr(rmax), _ptr(u), device_ptrs), "cwb_shard_scatter")
+
+
+def cwb_shard_solve(model, u, device_ptrs: int = 0):
+    _check(load_library().cwb_shard_solve(model, _ptr(u), device_ptrs), "cwb_shard_solve")
 
 
 def cwb_get_residuals(model, channel: int, out: np.ndarray):

@@ -152,7 +152,7 @@ void free_model(cwb_model* m)
                     m->P, m->Acrit, m->Pdf, m->Adf, m->lambda, m->l_bin, m->l_d, m->l_nstar, m->l_type, m->l_xmin, m->l_xmax, m->l_degree,
                     m->l_nknots, m->l_feat, m->part, m->cluster_slot, m->slot_c0, m->theta_it, m->q_it, m->v, m->state, m->risk_part, m->tr_k,
                     m->tr_mode, m->tr_theta, m->tr_q, m->forced, m->coef, m->f2, m->uacc, m->gbar, m->ptime, m->ztab_lo,
-                    m->vmax};
+                    m->vmax, m->u_shard};
     for (void* p : bufs) dev_free(p);
     profile_release(m);
     release_graphs(m);
@@ -197,7 +197,7 @@ cwb_status validate_learner(const cwb_learner& b, int32_t p, int k)
 
 cwb_status create_impl(const cwb_config* cfg, const void* X, int32_t x_dtype, int64_t n, int32_t p, const void* y,
                        const double* w, const cwb_learner* bl, int32_t K, int32_t device_ptrs, cwb_model** out,
-                       int iter_mode)
+                       int iter_mode, const cwb_shard_config* sc = nullptr)
 {
     if (!out) { set_error("out is NULL"); return CWB_EINVAL; }
     *out = nullptr;
@@ -212,6 +212,17 @@ cwb_status create_impl(const cwb_config* cfg, const void* X, int32_t x_dtype, in
     if (cfg->iterations < 0 || cfg->patience < 0) { set_error("iterations and patience must be >= 0"); return CWB_EINVAL; }
     if (cfg->opt == CWB_OPT_HCWB && !cfg->val_mask) { set_error("HCWB needs a validation mask"); return CWB_EINVAL; }
     for (int k = 0; k < K; ++k) CWB_TRY(validate_learner(bl[k], p, k));
+    if (sc) {
+        if (cfg->opt != CWB_OPT_CWB) { set_error("row shards run plain CWB"); return CWB_EINVAL; }
+        if (w) { set_error("row shards take unweighted rows"); return CWB_EINVAL; }
+        if (!sc->xmin || !sc->xmax || sc->n_global < n) { set_error("bad shard configuration"); return CWB_EINVAL; }
+        for (int k = 0; k < K; ++k)
+            if (bl[k].n_bins == CWB_BINS_EXACT && bl[k].type != CWB_BL_CATEGORICAL &&
+                bl[k].type != CWB_BL_CATEGORICAL_BINARY) {
+                set_error("row shards need equidistant binnings (the unique values differ per shard)");
+                return CWB_EINVAL;
+            }
+    }
 
     cwb_model* m = new cwb_model();
     int dev = cfg->device;
@@ -233,7 +244,13 @@ cwb_status create_impl(const cwb_config* cfg, const void* X, int32_t x_dtype, in
     m->K = K;
     m->hybrid = cfg->opt == CWB_OPT_HCWB;
     m->accel = cfg->opt != CWB_OPT_CWB;
-    m->iter_mode = iter_mode;
+    m->iter_mode = sc ? kIterKernels : iter_mode;
+    if (sc) {
+        m->shard = true;
+        m->shard_n_global = sc->n_global;
+        m->shard_xmin.assign(sc->xmin, sc->xmin + p);
+        m->shard_xmax.assign(sc->xmax, sc->xmax + p);
+    }
     if (const char* wc = std::getenv("CWB_WAIT_CYCLES")) {
         // limit of the device-side ring waits in SM clocks (default ~2 s); a short limit makes a
         // wait run out on purpose (failure-path tests)
@@ -315,6 +332,8 @@ cwb_status create_impl(const cwb_config* cfg, const void* X, int32_t x_dtype, in
         if (st == CWB_OK) st = dev_alloc((void**)&m->state, sizeof(DevState), m->stream);
         if (st == CWB_OK) st = dev_alloc((void**)&m->coef, sizeof(double) * 2 * K * D, m->stream);
         if (st == CWB_OK) st = dev_alloc((void**)&m->vmax, sizeof(float) * K, m->stream);
+        if (st == CWB_OK && m->shard)
+            st = dev_alloc((void**)&m->u_shard, sizeof(long long) * (size_t)m->B * m->nstar_max, m->stream);
         if (st == CWB_OK) st = dev_alloc((void**)&l_feat, sizeof(int32_t) * K, m->stream);
         if (st == CWB_OK) {
             m->risk_blocks = 0;
@@ -414,6 +433,10 @@ cwb_status cwb_fit(cwb_model* m, int32_t iterations)
     DeviceGuard guard(m->device);
     int32_t it = iterations > 0 ? iterations : m->cfg.iterations;
     if (it <= 0) return CWB_OK;
+    if (m->shard) {
+        set_error("a row shard runs its iterations through cwb_shard_rows / cwb_shard_scatter / cwb_shard_solve");
+        return CWB_ESTATE;
+    }
     try {
         CWB_TRY(launch_iterations(m, it));   // the last update is applied when f is next read
     } catch (const std::exception& e) {
@@ -785,6 +808,74 @@ cwb_status cwb_predict_noalloc(const cwb_model* mc, const void* Xnew, int32_t x_
     CWB_CUDA_TRY(cudaMemcpyAsync(out, out_dev, sizeof(float) * (size_t)n_new, cudaMemcpyDeviceToHost, m->stream));
     CWB_CUDA_TRY(cudaStreamSynchronize(m->stream));
     return read_device_error(m);
+}
+
+cwb_status cwb_shard_create(const cwb_config* cfg, const void* X, int32_t x_dtype, int64_t n, int32_t p, const void* y,
+                            const cwb_learner* bl, int32_t K, int32_t device_ptrs, const cwb_shard_config* sc,
+                            cwb_model** out)
+{
+    set_error("");
+    if (!sc) {
+        if (out) *out = nullptr;
+        set_error("shard configuration is NULL");
+        return CWB_EINVAL;
+    }
+    try {
+        return create_impl(cfg, X, x_dtype, n, p, y, nullptr, bl, K, device_ptrs, out, kIterKernels, sc);
+    } catch (const std::exception& e) {
+        set_error(std::string("host exception: ") + e.what());
+        return CWB_ENOMEM;
+    }
+}
+
+cwb_status cwb_shard_sizes(const cwb_model* m, int32_t* B, int32_t* S)
+{
+    set_error("");
+    if (!m || !m->shard) { set_error("not a row shard"); return CWB_EINVAL; }
+    if (B) *B = m->B;
+    if (S) *S = m->nstar_max;
+    return CWB_OK;
+}
+
+cwb_status cwb_shard_stats(cwb_model* m, double* counts, double* sums, int32_t* cnt_log2)
+{
+    set_error("");
+    if (!m || !m->shard || !counts || !sums || !cnt_log2) { set_error("bad argument"); return CWB_EINVAL; }
+    DeviceGuard guard(m->device);
+    return shard_stats(m, counts, sums, cnt_log2);
+}
+
+cwb_status cwb_shard_finish(cwb_model* m, const double* counts, const double* sums, int32_t cnt_log2)
+{
+    set_error("");
+    if (!m || !m->shard || !counts || !sums) { set_error("bad argument"); return CWB_EINVAL; }
+    if (m->done > 0) { set_error("cwb_shard_finish comes before the first iteration"); return CWB_ESTATE; }
+    DeviceGuard guard(m->device);
+    return shard_finish(m, counts, sums, cnt_log2);
+}
+
+cwb_status cwb_shard_rows(cwb_model* m, float* rmax, int32_t device_ptrs)
+{
+    set_error("");
+    if (!m || !m->shard || !rmax) { set_error("bad argument"); return CWB_EINVAL; }
+    DeviceGuard guard(m->device);
+    return shard_rows(m, rmax, device_ptrs);
+}
+
+cwb_status cwb_shard_scatter(cwb_model* m, const float* rmax, int64_t* u, int32_t device_ptrs)
+{
+    set_error("");
+    if (!m || !m->shard || !rmax || !u) { set_error("bad argument"); return CWB_EINVAL; }
+    DeviceGuard guard(m->device);
+    return shard_scatter(m, rmax, device_ptrs, reinterpret_cast<long long*>(u), device_ptrs);
+}
+
+cwb_status cwb_shard_solve(cwb_model* m, const int64_t* u, int32_t device_ptrs)
+{
+    set_error("");
+    if (!m || !m->shard || !u) { set_error("bad argument"); return CWB_EINVAL; }
+    DeviceGuard guard(m->device);
+    return shard_solve(m, reinterpret_cast<const long long*>(u), device_ptrs);
 }
 
 const char* cwb_last_error(void) { return g_last_error.c_str(); }

@@ -219,6 +219,12 @@ struct cwb_model {
     double wmax = 1.0;                    // largest observation weight
     long long wait_cycles = 4000000000LL; // limit of each device-side ring wait (SM clocks, ~2 s)
     int withhold_tile = -1;               // test hook (CWB_WITHHOLD_TILE): a scatter tile whose copies are never issued
+    // row shards (cwb_shard_*): global binning ranges and row count, exchanged histogram sums
+    bool shard = false;
+    int64_t shard_n_global = 0;
+    std::vector<double> shard_xmin, shard_xmax;   // per feature
+    long long* u_shard = nullptr;         // [B][S] exact histogram sums (local, then the exchanged total)
+    const long long* solve_u64 = nullptr; // set while a shard's solve is queued
 };
 
 namespace cwb {
@@ -277,6 +283,14 @@ cwb_status launch_aggregate(cwb_model* m);
 cwb_status read_device_error(cwb_model* m);
 cwb_status profile_collect(cwb_model* m);
 void profile_release(cwb_model* m);
+
+// Row shards (cwb_setup.cu, cwb_iter.cu)
+cwb_status build_caches(cwb_model* m, const double* cnt, int phases);
+cwb_status shard_stats(cwb_model* m, double* counts_h, double sums_h[2], int32_t* cnt_log2);
+cwb_status shard_finish(cwb_model* m, const double* counts_h, const double sums_h[2], int32_t cnt_log2);
+cwb_status shard_rows(cwb_model* m, float* rmax, int device_ptrs);
+cwb_status shard_scatter(cwb_model* m, const float* rmax, int rmax_device, long long* u, int u_device);
+cwb_status shard_solve(cwb_model* m, const long long* u, int device_ptrs);
 
 // Persistent iteration kernel (cwb_persist.cu)
 cwb_status plan_persistent(cwb_model* m);

@@ -776,6 +776,23 @@ __global__ void k_count_log2(DevState* state, int idx)
     state->cnt_log2[idx] = l;
 }
 
+// Exact int64 sums of the per-cluster fixed-point partials of channel 0, u[b][l] (row shards
+// exchange these).  One thread per (binning, bin); the clusters of a bin are those of its slot.
+__global__ void k_partials_to_u(const int* __restrict__ part, const int32_t* __restrict__ slot_c0, int B, int S, int FE,
+                                int F, int nb_cta, int bin_ranges, int cmax, long long* __restrict__ u)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)B * S; e += (int64_t)gridDim.x * blockDim.x) {
+        const int b = (int)(e / S), l = (int)(e - (int64_t)b * S);
+        const int g = b / FE, f = b - g * FE;
+        const int br = l / nb_cta, lb = l - br * nb_cta;
+        const int slot = g * bin_ranges + br;
+        long long acc = 0;
+        for (int c = slot_c0[slot]; c < slot_c0[slot + 1]; ++c)
+            acc += __ldcg(part + (((int64_t)c * cmax) * F + f) * nb_cta + lb);
+        u[e] = acc;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Per-learner fit, criterion and argmin.
 //
@@ -823,6 +840,7 @@ struct SolveArgs {
     const int32_t* forced;    // [cap]
     int trace_cap;
     float* vmax;              // [K] max |v_k| of channel 0 (the bound of the persistent path's fixed point)
+    const long long* u64;     // row shards: exact histogram sums [B][S] of all shards (replaces the partials)
 };
 
 __device__ __forceinline__ void cp_async4(void* dst, const void* src)
@@ -955,6 +973,15 @@ __global__ void __launch_bounds__(kSolveThreads, 512 / kSolveThreads) k_solve(So
         int c0 = c0n, c1 = c1n, lb = lbn;
         if (L0 > 0) chunk_clusters(L0, L1, c0, c1, lb);
         long long it0[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+        if (a.u64) {
+            // row shards: the exchanged exact sums of every shard's histograms stand for the partials
+            c0 = c1 = 0;
+            if (half == 0 && mine)
+                for (int t = 0; t < 4; ++t) {
+                    const int l = L0 + 4 * gi + t;
+                    it0[0][t] = l < nst ? __ldcg(a.u64 + (int64_t)b * S + l) : 0;
+                }
+        }
         float ft[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
         float fc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
         for (int cc = c0 + half; cc < c1; cc += 2 * kSolveBatch) {
@@ -1448,6 +1475,7 @@ void launch_solve(cwb_model* m, cudaStream_t s)
     a.forced = m->forced;
     a.trace_cap = m->trace_cap;
     a.vmax = m->vmax;
+    a.u64 = m->solve_u64;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(m->K, 1, 1);
     const int threads = solve_threads(m);
@@ -2065,6 +2093,54 @@ void profile_release(cwb_model* m)
     m->prof_pending.clear();
     for (cudaEvent_t e : m->prof_pool) cudaEventDestroy(e);
     m->prof_pool.clear();
+}
+
+// ---- row shards: one iteration split at its two exchange points (see cwb_shard_* in cwb.h)
+cwb_status shard_rows(cwb_model* m, float* rmax, int device_ptrs)
+{
+    CWB_TRY(prepare_launch(m, 1));
+    launch_rows<kRowsFused>(m, m->stream);
+    CWB_CUDA_TRY(cudaGetLastError());
+    CWB_CUDA_TRY(cudaMemcpyAsync(rmax, &m->state->rmax_bits[0], sizeof(float),
+                                 device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, m->stream));
+    if (!device_ptrs) CWB_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    return CWB_OK;
+}
+
+cwb_status shard_scatter(cwb_model* m, const float* rmax, int rmax_device, long long* u, int u_device)
+{
+    const ScatterPlan& P = m->plan;
+    if (!P.int_acc) {
+        set_error("row shards need the exact fixed-point histograms");
+        return CWB_ESTATE;
+    }
+    CWB_CUDA_TRY(cudaMemcpyAsync(&m->state->rmax_bits[0], rmax, sizeof(float),
+                                 rmax_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, m->stream));
+    launch_scatter(m, m->stream);
+    const int64_t total = (int64_t)m->B * m->nstar_max;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(4 * num_sms(m->device), (total + 255) / 256));
+    k_partials_to_u<<<blocks, 256, 0, m->stream>>>(reinterpret_cast<const int*>(m->part), m->slot_c0, m->B, m->nstar_max,
+                                                   P.fe, P.f_lane, P.nb_cta, P.bin_ranges, P.cmax, m->u_shard);
+    CWB_CUDA_TRY(cudaGetLastError());
+    if (u != m->u_shard)
+        CWB_CUDA_TRY(cudaMemcpyAsync(u, m->u_shard, sizeof(long long) * total,
+                                     u_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, m->stream));
+    if (!u_device) CWB_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    return CWB_OK;
+}
+
+cwb_status shard_solve(cwb_model* m, const long long* u, int device_ptrs)
+{
+    const int64_t total = (int64_t)m->B * m->nstar_max;
+    if (u != m->u_shard)
+        CWB_CUDA_TRY(cudaMemcpyAsync(m->u_shard, u, sizeof(long long) * total,
+                                     device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, m->stream));
+    m->solve_u64 = m->u_shard;
+    launch_solve(m, m->stream);
+    m->solve_u64 = nullptr;
+    CWB_CUDA_TRY(cudaGetLastError());
+    note_iterations_queued(m, 1);
+    return CWB_OK;
 }
 
 cwb_status read_device_error(cwb_model* m)

@@ -62,6 +62,13 @@ __global__ void k_split_f64(const double* __restrict__ src, int64_t n, int64_t n
     }
 }
 
+// FP64 values from FP32 high parts and optional low parts (the split of FP64 targets).
+__global__ void k_join_f64(const float* __restrict__ hi, const float* __restrict__ lo, int64_t n, double* __restrict__ out)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+        out[q] = (double)hi[q] + (lo ? (double)lo[q] : 0.0);
+}
+
 template <typename T>
 __global__ void k_check_binary(const T* __restrict__ y, int64_t n, uint32_t* bad)
 {
@@ -884,6 +891,155 @@ int grid_for(int64_t work, int device)
 
 }  // namespace
 
+// Z^T W Z = Z^b^T diag(cnt) Z^b from the bin counts cnt [2 phases][B][S] (device), lambda from df and
+// the cached P = (G + lambda K)^-1 with the criterion matrix, for `phases` caches (with one phase
+// the second cache is a copy of the first).  Allocates the cache arrays on first use.
+cwb_status build_caches(cwb_model* m, const double* cnt, int phases)
+{
+    cudaStream_t s = m->stream;
+    const int K = m->K, D = m->d_max, S = m->nstar_max, B = m->B;
+    const size_t dd = (size_t)D * D;
+    TempBuf tmp;
+    std::vector<int32_t> lnnz(K), ldiff(K);
+    std::vector<double> ldf(K), llam(K);
+    for (int k = 0; k < K; ++k) {
+        lnnz[k] = m->lrn[k].nnz;
+        ldiff[k] = m->lrn[k].spec.diff_order;
+        ldf[k] = m->lrn[k].spec.df;
+        llam[k] = m->lrn[k].spec.lambda;
+    }
+    int32_t *nnz_d = nullptr, *ldiff_d = nullptr, *lstat = nullptr;
+    double *ldf_d = nullptr, *llam_d = nullptr;
+    CWB_TRY(tmp.get(&nnz_d, (size_t)K, s));
+    CWB_TRY(tmp.get(&ldiff_d, (size_t)K, s));
+    CWB_TRY(tmp.get(&ldf_d, (size_t)K, s));
+    CWB_TRY(tmp.get(&llam_d, (size_t)K, s));
+    CWB_TRY(tmp.get(&lstat, (size_t)2 * K, s));
+    CWB_CUDA_TRY(cudaMemcpyAsync(nnz_d, lnnz.data(), sizeof(int32_t) * K, cudaMemcpyHostToDevice, s));
+    CWB_CUDA_TRY(cudaMemcpyAsync(ldiff_d, ldiff.data(), sizeof(int32_t) * K, cudaMemcpyHostToDevice, s));
+    CWB_CUDA_TRY(cudaMemcpyAsync(ldf_d, ldf.data(), sizeof(double) * K, cudaMemcpyHostToDevice, s));
+    CWB_CUDA_TRY(cudaMemcpyAsync(llam_d, llam.data(), sizeof(double) * K, cudaMemcpyHostToDevice, s));
+    if (!m->G) {
+        CWB_TRY(dev_alloc((void**)&m->G, sizeof(double) * 2 * K * dd, s));
+        CWB_TRY(dev_alloc((void**)&m->P, sizeof(double) * 2 * K * dd, s));
+        CWB_TRY(dev_alloc((void**)&m->Acrit, sizeof(double) * 2 * K * dd, s));
+        CWB_TRY(dev_alloc((void**)&m->Pdf, sizeof(float2) * 2 * K * dd, s));
+        CWB_TRY(dev_alloc((void**)&m->Adf, sizeof(float2) * 2 * K * dd, s));
+        CWB_TRY(dev_alloc((void**)&m->lambda, sizeof(double) * 2 * K, s));
+    }
+    k_gram<<<dim3(K, 2), kThreads, 0, s>>>(S, D, K, m->l_bin, m->l_d, nnz_d, m->zb64, m->zcol, m->crange, cnt, B, m->G);
+    {
+        LamArgs a{K, D, m->l_type, m->l_d, ldiff_d, ldf_d, llam_d, m->G, m->P, m->Acrit, m->lambda, lstat, phases};
+        size_t smem = sizeof(double) * (4 * dd + D);
+        CWB_CUDA_TRY(allow_max_dynamic_smem((const void*)k_lambda, m->device));
+        k_lambda<<<dim3(K, phases), kLamThreads, smem, s>>>(a);
+        if (phases == 1) {           // one cache serves both phases
+            CWB_CUDA_TRY(cudaMemcpyAsync(m->P + (size_t)K * dd, m->P, sizeof(double) * K * dd, cudaMemcpyDeviceToDevice, s));
+            CWB_CUDA_TRY(cudaMemcpyAsync(m->Acrit + (size_t)K * dd, m->Acrit, sizeof(double) * K * dd,
+                                         cudaMemcpyDeviceToDevice, s));
+            CWB_CUDA_TRY(cudaMemcpyAsync(m->lambda + K, m->lambda, sizeof(double) * K, cudaMemcpyDeviceToDevice, s));
+            CWB_CUDA_TRY(cudaMemsetAsync(lstat + K, 0, sizeof(int32_t) * K, s));
+        }
+        const int gs = (int)std::min<int64_t>(1024, ((int64_t)2 * K * dd + kThreads - 1) / kThreads);
+        k_split_df<<<gs, kThreads, 0, s>>>(m->P, (int64_t)2 * K * dd, m->Pdf);
+        k_split_df<<<gs, kThreads, 0, s>>>(m->Acrit, (int64_t)2 * K * dd, m->Adf);
+    }
+    CWB_CUDA_TRY(cudaGetLastError());
+    std::vector<int32_t> lstat_h(2 * K);
+    CWB_CUDA_TRY(cudaMemcpyAsync(lstat_h.data(), lstat, sizeof(int32_t) * 2 * K, cudaMemcpyDeviceToHost, s));
+    CWB_CUDA_TRY(cudaStreamSynchronize(s));
+    for (int ph = 0; ph < phases; ++ph)
+        for (int k = 0; k < K; ++k) {
+            int st = lstat_h[(size_t)ph * K + k];
+            if (st == 1) {
+                set_error("learner " + std::to_string(k) + ": Z^T W Z + lambda K is not positive definite");
+                return CWB_ENUMERIC;
+            }
+            if (st == 2) {
+                set_error("learner " + std::to_string(k) + ": df is not reachable (at or below the penalty null space)");
+                return CWB_ENUMERIC;
+            }
+        }
+    return CWB_OK;
+}
+
+// Local statistics of a row shard for the setup exchange: unweighted bin counts [B][S] (host),
+// sum of the targets and the row count, and the shard's bin-count bound of the scatter.
+cwb_status shard_stats(cwb_model* m, double* counts_h, double sums_h[2], int32_t* cnt_log2)
+{
+    cudaStream_t s = m->stream;
+    const int B = m->B, S = m->nstar_max;
+    TempBuf tmp;
+    double* cnt = nullptr;
+    CWB_TRY(tmp.get(&cnt, (size_t)B * S, s));
+    CWB_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(double) * (size_t)B * S, s));
+    if (S <= kCountSmemBins) {
+        dim3 grid(std::min<int>(grid_for(m->n, m->device), 16), B);
+        const size_t smem = sizeof(int) * (size_t)S;
+        if (m->ind_bytes == 1) k_counts_smem<<<grid, kThreads, smem, s>>>((const uint8_t*)m->ind, m->n_pad, m->n, S, S, cnt);
+        else k_counts_smem<<<grid, kThreads, smem, s>>>((const uint16_t*)m->ind, m->n_pad, m->n, S, S, cnt);
+    } else {
+        dim3 grid(std::min<int>(grid_for(m->n, m->device), 64), B);
+        if (m->ind_bytes == 1) k_counts<<<grid, kThreads, 0, s>>>((const uint8_t*)m->ind, m->n_pad, 0, m->n, nullptr, S, cnt);
+        else k_counts<<<grid, kThreads, 0, s>>>((const uint16_t*)m->ind, m->n_pad, 0, m->n, nullptr, S, cnt);
+    }
+    // sum of the targets: FP32 high parts and the low parts of FP64 targets, in FP64
+    double* part = nullptr;
+    CWB_TRY(tmp.get(&part, 2 * (size_t)kOffsetBlocks, s));
+    double* y64 = nullptr;
+    CWB_TRY(tmp.get(&y64, (size_t)m->n, s));
+    k_join_f64<<<grid_for(m->n, m->device), kThreads, 0, s>>>(m->y, m->y_lo, m->n, y64);
+    k_offset_partial<<<kOffsetBlocks, kThreads, 0, s>>>(y64, nullptr, m->n, part);
+    std::vector<double> part_h(2 * kOffsetBlocks);
+    CWB_CUDA_TRY(cudaGetLastError());
+    CWB_CUDA_TRY(cudaMemcpyAsync(counts_h, cnt, sizeof(double) * (size_t)B * S, cudaMemcpyDeviceToHost, s));
+    CWB_CUDA_TRY(cudaMemcpyAsync(part_h.data(), part, sizeof(double) * 2 * kOffsetBlocks, cudaMemcpyDeviceToHost, s));
+    DevState st;
+    CWB_CUDA_TRY(cudaMemcpyAsync(&st, m->state, sizeof(st), cudaMemcpyDeviceToHost, s));
+    CWB_CUDA_TRY(cudaStreamSynchronize(s));
+    double sy = 0.0, sn = 0.0;
+    for (int i = 0; i < kOffsetBlocks; ++i) {
+        sy += part_h[i];
+        sn += part_h[kOffsetBlocks + i];
+    }
+    sums_h[0] = sy;
+    sums_h[1] = sn;
+    *cnt_log2 = st.cnt_log2[0];
+    return CWB_OK;
+}
+
+// Completes a row shard's setup from the exchanged statistics: the caches from the global bin
+// counts, the offset from the global target sum and row count, and the common fixed-point bound.
+cwb_status shard_finish(cwb_model* m, const double* counts_h, const double sums_h[2], int32_t cnt_log2)
+{
+    cudaStream_t s = m->stream;
+    const int B = m->B, S = m->nstar_max;
+    if (cnt_log2 > 13) {
+        set_error("shards: more than 8192 rows of one scatter cluster share a bin (heavily skewed bins are not supported "
+                  "for row shards)");
+        return CWB_EINVAL;
+    }
+    TempBuf tmp;
+    double* cnt = nullptr;
+    CWB_TRY(tmp.get(&cnt, (size_t)2 * B * S, s));
+    CWB_CUDA_TRY(cudaMemcpyAsync(cnt, counts_h, sizeof(double) * (size_t)B * S, cudaMemcpyHostToDevice, s));
+    CWB_CUDA_TRY(cudaMemcpyAsync(cnt + (size_t)B * S, counts_h, sizeof(double) * (size_t)B * S, cudaMemcpyHostToDevice, s));
+    CWB_TRY(build_caches(m, cnt, 1));
+    const double mean = sums_h[0] / sums_h[1];
+    if (m->cfg.loss == CWB_LOSS_BINOMIAL && !(mean > 0.0 && mean < 1.0)) {
+        set_error("binomial loss needs both classes among the rows of all shards");
+        return CWB_EINVAL;
+    }
+    m->offset = m->cfg.loss == CWB_LOSS_L2 ? mean : log(mean / (1.0 - mean));
+    const float off_hi = (float)m->offset;
+    const float off_lo = (float)(m->offset - (double)off_hi);
+    k_init_rows<<<grid_for(m->n_pad, m->device), kThreads, 0, s>>>(m->n_pad, off_hi, off_lo, m->f, m->h, m->c, m->rw);
+    CWB_CUDA_TRY(cudaMemcpyAsync(&m->state->cnt_log2[0], &cnt_log2, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    CWB_CUDA_TRY(cudaGetLastError());
+    CWB_CUDA_TRY(cudaStreamSynchronize(s));
+    return CWB_OK;
+}
+
 cwb_status setup_model(cwb_model* m, const void* X_in, int x_dtype, const void* y_in, const double* w_in,
                        const uint8_t* val_mask, int device_ptrs)
 {
@@ -1011,6 +1167,21 @@ cwb_status setup_model(cwb_model* m, const void* X_in, int x_dtype, const void* 
     if (flags_h[2]) { set_error("features must be finite"); return CWB_EINVAL; }
     if (flags_h[5]) { set_error("targets must be finite"); return CWB_EINVAL; }
     if (flags_h[4]) { set_error("a categorical feature holds a value that is not a class code 0..c-1"); return CWB_EINVAL; }
+    if (m->shard) {
+        // a row shard bins on the ranges of all shards' rows (equidistant design points are then
+        // the same on every shard); the local rows must lie inside them
+        for (int b = 0; b < B; ++b) {
+            if (m->bins[b].categories) continue;
+            const int f = m->bins[b].feature;
+            const double gl = m->shard_xmin[f], gh = m->shard_xmax[f];
+            if (!(xmin_h[b] >= gl && xmax_h[b] <= gh)) {
+                set_error("shard rows of feature " + std::to_string(f) + " lie outside the given global range");
+                return CWB_EINVAL;
+            }
+            xmin_h[b] = gl;
+            xmax_h[b] = gh;
+        }
+    }
     for (int b = 0; b < B; ++b) {
         if (!(xmax_h[b] > xmin_h[b])) {
             set_error("feature " + std::to_string(m->bins[b].feature) + " is constant (max == min)");
@@ -1040,7 +1211,8 @@ cwb_status setup_model(cwb_model* m, const void* X_in, int x_dtype, const void* 
             any_exact = true;
         } else {
             hb.exact = 0;
-            hb.nstar = hb.nbins_spec == CWB_BINS_SQRT ? (int)std::min<int64_t>(isqrt64(n), 1 << 30) : hb.nbins_spec;
+            const int64_t n_sqrt = m->shard ? m->shard_n_global : n;      // a shard uses the global row count
+            hb.nstar = hb.nbins_spec == CWB_BINS_SQRT ? (int)std::min<int64_t>(isqrt64(n_sqrt), 1 << 30) : hb.nbins_spec;
         }
     }
     double* keys = nullptr;
@@ -1210,50 +1382,10 @@ cwb_status setup_model(cwb_model* m, const void* X_in, int x_dtype, const void* 
         CWB_CUDA_TRY(cudaMemcpyAsync(cnt + (int64_t)B * S, cnt, sizeof(double) * (size_t)B * S, cudaMemcpyDeviceToDevice, s));
 
     // --- G, lambda, P per learner and phase
-    const size_t dd = (size_t)D * D;
-    CWB_TRY(dev_alloc((void**)&m->G, sizeof(double) * 2 * K * dd, s));
-    CWB_TRY(dev_alloc((void**)&m->P, sizeof(double) * 2 * K * dd, s));
-    CWB_TRY(dev_alloc((void**)&m->Acrit, sizeof(double) * 2 * K * dd, s));
-    CWB_TRY(dev_alloc((void**)&m->Pdf, sizeof(float2) * 2 * K * dd, s));
-    CWB_TRY(dev_alloc((void**)&m->Adf, sizeof(float2) * 2 * K * dd, s));
-    CWB_TRY(dev_alloc((void**)&m->lambda, sizeof(double) * 2 * K, s));
-    int32_t* lstat = nullptr;
-    CWB_TRY(tmp.get(&lstat, (size_t)2 * K, s));
-    k_gram<<<dim3(K, 2), kThreads, 0, s>>>(S, D, K, m->l_bin, m->l_d, nnz_d, m->zb64, m->zcol, m->crange, cnt, B, m->G);
-    {
-        LamArgs a{K, D, m->l_type, m->l_d, ldiff_d, ldf_d, llam_d, m->G, m->P, m->Acrit, m->lambda, lstat, phases};
-        size_t smem = sizeof(double) * (4 * dd + D);
-        CWB_CUDA_TRY(allow_max_dynamic_smem((const void*)k_lambda, m->device));
-        k_lambda<<<dim3(K, phases), kLamThreads, smem, s>>>(a);
-        if (phases == 1) {           // one cache serves both phases
-            CWB_CUDA_TRY(cudaMemcpyAsync(m->P + (size_t)K * dd, m->P, sizeof(double) * K * dd, cudaMemcpyDeviceToDevice, s));
-            CWB_CUDA_TRY(cudaMemcpyAsync(m->Acrit + (size_t)K * dd, m->Acrit, sizeof(double) * K * dd,
-                                         cudaMemcpyDeviceToDevice, s));
-            CWB_CUDA_TRY(cudaMemcpyAsync(m->lambda + K, m->lambda, sizeof(double) * K, cudaMemcpyDeviceToDevice, s));
-            CWB_CUDA_TRY(cudaMemsetAsync(lstat + K, 0, sizeof(int32_t) * K, s));
-        }
-        const int gs = (int)std::min<int64_t>(1024, ((int64_t)2 * K * dd + kThreads - 1) / kThreads);
-        k_split_df<<<gs, kThreads, 0, s>>>(m->P, (int64_t)2 * K * dd, m->Pdf);
-        k_split_df<<<gs, kThreads, 0, s>>>(m->Acrit, (int64_t)2 * K * dd, m->Adf);
-    }
-    CWB_CUDA_TRY(cudaGetLastError());
-    std::vector<int32_t> lstat_h(2 * K);
-    CWB_CUDA_TRY(cudaMemcpyAsync(lstat_h.data(), lstat, sizeof(int32_t) * 2 * K, cudaMemcpyDeviceToHost, s));
     CWB_CUDA_TRY(cudaMemcpyAsync(flags_h, flags, sizeof(flags_h), cudaMemcpyDeviceToHost, s));
     CWB_CUDA_TRY(cudaStreamSynchronize(s));
     if (flags_h[3]) { set_error("internal: exact binning lookup failed"); return CWB_ENUMERIC; }
-    for (int ph = 0; ph < phases; ++ph)
-        for (int k = 0; k < K; ++k) {
-            int st = lstat_h[(size_t)ph * K + k];
-            if (st == 1) {
-                set_error("learner " + std::to_string(k) + ": Z^T W Z + lambda K is not positive definite");
-                return CWB_ENUMERIC;
-            }
-            if (st == 2) {
-                set_error("learner " + std::to_string(k) + ": df is not reachable (at or below the penalty null space)");
-                return CWB_ENUMERIC;
-            }
-        }
+    CWB_TRY(build_caches(m, cnt, phases));
 
     // --- offset and initial models
     double *off_d = nullptr, *off_part = nullptr;
