@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "cwb_internal.cuh"
+#include "cwb_bspline.cuh"
 #include "cwb_noalloc_size.h"
 
 namespace cwb {
@@ -51,14 +52,7 @@ void dev_free(void* p)
 
 namespace {
 
-// Evaluate g_k(x)^T theta for a P-spline (B-spline basis on the equidistant
-// extended knot vector, Sec. 2.2) or a linear learner (1, x).
-__device__ __forceinline__ double knot_at(double xmin, double delta, int i_minus_q)
-{
-    return __dadd_rn(xmin, __dmul_rn((double)i_minus_q, delta));
-}
-
-// Categorical learners (App. B.1) take the raw value: a valid class code selects its
+// g_k(x)^T theta of one learner at a raw value x.  Categorical learners (App. B.1) take the raw value: a valid class code selects its
 // coefficient, anything else contributes nothing.  Numeric learners clamp x to the
 // training range.  For a binary learner q holds the class it indicates.
 __device__ double learner_eval(double x, int type, int q, int nk, double xmin, double xmax, const double* theta)
@@ -71,28 +65,11 @@ __device__ double learner_eval(double x, int type, int q, int nk, double xmin, d
     }
     x = fmin(fmax(x, xmin), xmax);
     if (type == CWB_BL_LINEAR) return theta[0] + theta[1] * x;
-    const double delta = __ddiv_rn(__dsub_rn(xmax, xmin), (double)(nk + 1));
-    const int last = nk + q;
-    int mu = (int)floor(__ddiv_rn(__dsub_rn(x, xmin), delta)) + q;
-    if (mu < q) mu = q;
-    if (mu > last) mu = last;
-    while (mu > q && x < knot_at(xmin, delta, mu - q)) --mu;
-    while (mu < last && x >= knot_at(xmin, delta, mu + 1 - q)) ++mu;
-    double N[kMaxNnz], left[kMaxNnz], right[kMaxNnz];
-    N[0] = 1.0;
-    for (int j = 1; j <= q; ++j) {
-        left[j] = x - knot_at(xmin, delta, mu + 1 - j - q);
-        right[j] = knot_at(xmin, delta, mu + j - q) - x;
-        double saved = 0.0;
-        for (int r = 0; r < j; ++r) {
-            double tmp = N[r] / (right[r + 1] + left[j - r]);
-            N[r] = saved + right[r + 1] * tmp;
-            saved = left[j - r] * tmp;
-        }
-        N[j] = saved;
-    }
+    // P-spline: g_k(x)^T theta over the q + 1 non-zero B-splines at x
+    double N[kMaxNnz];
+    const int c0 = bspline_nonzero(x, xmin, xmax, q, nk, N);
     double acc = 0.0;
-    for (int t = 0; t <= q; ++t) acc += N[t] * theta[mu - q + t];
+    for (int t = 0; t <= q; ++t) acc += N[t] * theta[c0 + t];
     return acc;
 }
 
@@ -262,6 +239,7 @@ cwb_status create_impl(const cwb_config* cfg, const void* X, int32_t x_dtype, in
         // copies, so the waits on it run out and the kernel returns CWB_ETIMEOUT
         m->withhold_tile = std::atoi(wt);
     }
+    if (const char* lk = std::getenv("CWB_L2_KEEP")) m->l2_keep = std::atoi(lk) != 0;
     if (const char* mode = std::getenv("CWB_ITER_MODE")) {
         // "kernels" or unset: three kernels per iteration (rows, scatter, solve) launched from CUDA
         // graphs; "persistent": one persistent cooperative kernel for plain CWB models that qualify

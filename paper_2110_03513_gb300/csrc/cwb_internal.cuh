@@ -218,6 +218,7 @@ struct cwb_model {
     float* vmax = nullptr;                // [K] max |v_k| of the latest update tables
     double wmax = 1.0;                    // largest observation weight
     long long wait_cycles = 4000000000LL; // limit of each device-side ring wait (SM clocks, ~2 s)
+    int l2_keep = 0;                      // scatter copies with L2 hints: the index kept, the residual rows streamed
     int withhold_tile = -1;               // test hook (CWB_WITHHOLD_TILE): a scatter tile whose copies are never issued
     // row shards (cwb_shard_*): global binning ranges and row count, exchanged histogram sums
     bool shard = false;

@@ -426,6 +426,7 @@ struct ScatterArgs {
     int64_t count_rows;            // >= 0: counting pass over this many rows (every row adds 1)
     long long wait_cycles;         // limit of each ring wait (SM clocks); copies in flight are drained with kWaitCycles
     int withhold;                  // test hook: >= 0 makes CTA 0 arm, but never fill, its tile min(withhold, ntiles - 1)
+    int l2_keep;                   // 1: index boxes with the evict-last hint, residual rows with evict-first
 };
 
 constexpr int kEpiVec = 4;                         // 16-byte vectors per thread and pass of the cluster epilogue
@@ -503,12 +504,22 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
             // the first ring's index boxes before the wait (their barriers expect the residual
             // bytes too, which follow once the row pass is complete)
             const int early = fixed_mode ? min(a.stages, ntiles) : 0;
+            const uint64_t pol_keep = policy_evict_last(), pol_once = policy_evict_first();
+            auto load_ind = [&](int st, int64_t row0) {
+                void* dst = smem + a.ind_off + (size_t)st * a.stage_ind_bytes;
+                const int z = (int)(row0 / (128 / (int)sizeof(IndT)));
+                if (a.l2_keep) tma_load_3d_hint(dst, &tmap, 0, g * FE, z, &full[st], pol_keep);
+                else tma_load_3d(dst, &tmap, 0, g * FE, z, &full[st]);
+            };
+            auto load_r = [&](float* dst, const float* src, uint64_t* bar) {
+                if (a.l2_keep) bulk_load_hint(dst, src, (uint32_t)kStageRows * 4, bar, pol_once);
+                else bulk_load(dst, src, (uint32_t)kStageRows * 4, bar);
+            };
             for (int it = 0; it < early; ++it) {
                 const int64_t row0 = (t_lo + it) * kStageRows;
                 mbar_arrive_expect_tx(&full[it], bytes);
                 if (it == wh) continue;
-                tma_load_3d(smem + a.ind_off + (size_t)it * a.stage_ind_bytes, &tmap, 0, g * FE,
-                            (int)(row0 / (128 / (int)sizeof(IndT))), &full[it]);
+                load_ind(it, row0);
             }
             if (fixed_mode) grid_dep_wait();
             for (int it = 0; it < early; ++it) {
@@ -518,9 +529,7 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
                     ++issued;
                     continue;
                 }
-                for (int ch = 0; ch < C; ++ch)
-                    bulk_load(r_dst + ch * kStageRows, a.rw + ch * a.n_pad + row0, (uint32_t)kStageRows * 4,
-                              &full[it]);
+                for (int ch = 0; ch < C; ++ch) load_r(r_dst + ch * kStageRows, a.rw + ch * a.n_pad + row0, &full[it]);
                 ++issued;
             }
             // ring position kept incrementally (no division by the run-time stage count per tile)
@@ -541,12 +550,9 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
                     ++issued;
                     continue;
                 }
-                tma_load_3d(smem + a.ind_off + (size_t)s * a.stage_ind_bytes, &tmap, 0, g * FE,
-                            (int)(row0 / (128 / (int)sizeof(IndT))), &full[s]);
+                load_ind(s, row0);
                 float* r_dst = reinterpret_cast<float*>(smem + a.r_off + (size_t)s * a.stage_r_bytes);
-                for (int ch = 0; ch < C; ++ch)
-                    bulk_load(r_dst + ch * kStageRows, a.rw + ch * a.n_pad + row0, (uint32_t)kStageRows * 4,
-                              &full[s]);
+                for (int ch = 0; ch < C; ++ch) load_r(r_dst + ch * kStageRows, a.rw + ch * a.n_pad + row0, &full[s]);
                 ++issued;
             }
             if (!ok || wh >= 0) {
@@ -1405,6 +1411,7 @@ ScatterArgs scatter_args(cwb_model* m)
     a.count_rows = -1;
     a.wait_cycles = m->wait_cycles;
     a.withhold = m->withhold_tile;
+    a.l2_keep = m->l2_keep;
     return a;
 }
 

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "cwb_internal.cuh"
+#include "cwb_bspline.cuh"
 
 namespace cwb {
 
@@ -326,44 +327,6 @@ __global__ void k_counts(const IndT* __restrict__ ind, int64_t n_pad, int64_t r0
     double* c = cnt + (int64_t)b * stride;
     for (int64_t q = r0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < r1; q += (int64_t)gridDim.x * blockDim.x)
         atomicAdd(&c[row[q]], w ? w[q] : 1.0);
-}
-
-// ---------------------------------------------------------------------------
-// B-spline basis on an equidistant extended knot vector (Sec. 2.2, P-splines).
-// Knots t_i = xmin + (i - q) delta, delta = (xmax - xmin)/(n_knots + 1).  The
-// q+1 non-zero functions on the knot interval holding x come from the
-// triangular form of the Cox-de Boor recursion.  Returns the first non-zero
-// column.  Degrees 1..3.
-
-__device__ __forceinline__ double knot(double xmin, double delta, int i_minus_q)
-{
-    return __dadd_rn(xmin, __dmul_rn((double)i_minus_q, delta));
-}
-
-__device__ int bspline_nonzero(double x, double xmin, double xmax, int q, int nk, double* N /* q+1 */)
-{
-    const double delta = __ddiv_rn(__dsub_rn(xmax, xmin), (double)(nk + 1));
-    const int last = nk + q;                      // last interval with a full set of functions: [t_last, t_last+1]
-    int mu = (int)floor(__ddiv_rn(__dsub_rn(x, xmin), delta)) + q;
-    if (mu < q) mu = q;
-    if (mu > last) mu = last;
-    // agree with the half-open rule t_mu <= x < t_mu+1 on the rounded knot values
-    while (mu > q && x < knot(xmin, delta, mu - q)) --mu;
-    while (mu < last && x >= knot(xmin, delta, mu + 1 - q)) ++mu;
-    double left[kMaxNnz], right[kMaxNnz];
-    N[0] = 1.0;
-    for (int j = 1; j <= q; ++j) {
-        left[j] = x - knot(xmin, delta, mu + 1 - j - q);
-        right[j] = knot(xmin, delta, mu + j - q) - x;
-        double saved = 0.0;
-        for (int r = 0; r < j; ++r) {
-            double tmp = N[r] / (right[r + 1] + left[j - r]);
-            N[r] = saved + right[r + 1] * tmp;
-            saved = left[j - r] * tmp;
-        }
-        N[j] = saved;
-    }
-    return mu - q;
 }
 
 struct BasisArgs {
