@@ -51,7 +51,9 @@ WORKLOAD = ("binned CWB, L2 loss, n=1,000,000, p=50 U[0,1] FP32 features (10 inf
 
 # DRAM traffic of one scatter launch from the committed ncu capture, valid for the
 # scatter kernel source with this SHA-256 prefix (null once the kernel changes).
-SCATTER_TRAFFIC = {"sha256": "e70e46dabd72cf96", "bytes": 104052736 + 2966016}   # one ncu capture of this kernel
+SCATTER_TRAFFIC = {"sha256": "95844ce12c05fe67", "bytes": 104054528 + 3567616}   # one ncu capture of this kernel
+# the same kernel on the HCWB workload (ACWB phase: 200 binnings x 1.6M training rows, two channels)
+HCWB_SCATTER_TRAFFIC = {"sha256": "95844ce12c05fe67", "bytes": 663382272 + 3185152}
 
 
 def scatter_source_hash() -> str:
@@ -83,6 +85,8 @@ def parse_args():
     ap.add_argument("--skip-e2e", action="store_true", help="do not run the end-to-end fit")
     ap.add_argument("--skip-batched", action="store_true", help="do not run the batched-fits measurement")
     ap.add_argument("--skip-served", action="store_true", help="do not run the served-requests measurement")
+    ap.add_argument("--skip-hcwb", action="store_true", help="do not add the HCWB workload's figures")
+    ap.add_argument("--skip-small", action="store_true", help="do not add the small exact-binning fit's figures")
     ap.add_argument("--batched-fits", type=int, default=512,
                     help="fits in the batched measurement (the first of the 512 seeded specs)")
     ap.add_argument("--served-requests", type=int, default=96, help="requests in the served measurement")
@@ -172,15 +176,48 @@ def time_oracle(X, y, specs, iters: int):
     return max(t_all - t_setup, 1e-9) / iters, t_setup
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the platform string)."""
+    import platform
+    import subprocess
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
 def cpu_baseline_full(data, iters: int = 6):
+    """The FP64 oracle as it stands on one thread, and with its learner loop on every host core
+    (OpenMP; the per-learner sums keep their order, so the results are bit-identical)."""
     import numpy as np
+    from oracle import oracle as O
     specs = [dict(feature=j, n_bins=-1, df=5.0) for j in range(N_FEAT)]
     X = data.X.astype(np.float64)
     y = data.y.astype(np.float64)
+    O.set_threads(1)
     per_iter, t_setup = time_oracle(X, y, specs, iters)
+    nproc = os.cpu_count() or 1
+    threads = O.set_threads(nproc)
+    try:
+        per_iter_mt, _ = time_oracle(X, y, specs, iters)
+    finally:
+        O.set_threads(1)
     return {"value": 1.0 / per_iter, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"FP64 C oracle, single thread, {iters} iterations of the full n=1,000,000 p=50 workload "
-                      f"(setup {t_setup:.1f} s timed separately and excluded)"}
+                      f"(setup {t_setup:.1f} s timed separately and excluded)",
+            "cpu": cpu_model(), "nproc": nproc,
+            "openmp": {"value": 1.0 / per_iter_mt, "unit": UNIT, "cores": threads,
+                       "sample": f"the same {iters} iterations with the oracle's learner loop on {threads} threads"}}
 
 
 def run_reference(args):
@@ -355,10 +392,41 @@ def run_ours(args):
         if not args.skip_served:
             line["served"] = run_served(cwb, args)
     model.free()
+    if rank == 0 and world == 1 and not args.skip_hcwb:
+        h = measure_hcwb(cwb, min(args.steps, 40), 3, args.seed)
+        line["hcwb"] = {k: h[k] for k in ("metric", "value", "unit", "ms_per_step", "hbm_gbs", "roofline",
+                                          "scatter_us", "config", "clocks")}
+    if rank == 0 and world == 1 and not args.skip_small:
+        line["small_exact"] = measure_small(cwb)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def measure_small(cwb, M: int = 500):
+    """The small configuration: n = 10,000, p = 10 U[0,1] FP64 features, exact binning (n* = number of
+    unique values, about 10,000, uint16), cubic P-splines df = 5, nu = 0.1, M = 500 (L2).  One whole
+    fit of M iterations per step (its iteration graphs replayed), three steps after one warm-up fit;
+    at this size an iteration is bound by kernel latency, not by memory."""
+    import numpy as np
+    import synthetic_inputs as S
+    d = S.sim_small_exact()
+    learners = [cwb.learner(j, n_bins=cwb.BINS_EXACT, df=5.0) for j in range(d.p)]
+    times = []
+    for rep in range(4):
+        model = cwb.Model(d.X, d.y, learners, nu=NU, iterations=M, device=0)
+        model.synchronize()
+        t0 = time.perf_counter()
+        model.fit(M)
+        model.synchronize()
+        if rep:
+            times.append(time.perf_counter() - t0)
+        model.free()
+    t = float(np.median(times))
+    return {"workload": "binned CWB, L2, n=10,000, p=10 U[0,1] FP64, exact binning (n* = unique values), "
+                        "P-splines d=24 df=5, nu=0.1, M=500", "value": M / t, "unit": "iters/s",
+            "ms_per_fit": t * 1e3, "timing": "host clock around cwb_fit(M) and a synchronize, median of 3 fits"}
 
 
 def _percentile(xs, q):
@@ -530,17 +598,22 @@ def run_e2e(cwb, data, stream, dev, local):
 
 
 def run_hcwb(args):
+    """The HCWB workload's own JSON line (`--workload hcwb_binomial`)."""
+    import __graft_entry__ as g
+    g.build()
+    import paper_2110_03513_gb300 as cwb
+    print(json.dumps(measure_hcwb(cwb, args.steps, args.warmup, args.seed)), flush=True)
+
+
+def measure_hcwb(cwb, steps: int, warmup: int, seed: int):
     """ACWB with the hybrid switch (Algorithm 4), binomial loss, n = 2,000,000, p = 200 (100 U[0,1], 100
     N(0,1)), 20 informative, 20 % validation rows, n* = 1414 (uint16), gamma = 0.001, nu = 0.1, pat_0 = 5.
     A step is one iteration (cwb_fit(model, 1)); L2 is flushed before each timed step."""
     import numpy as np
     import torch
     import synthetic_inputs as S
-    import __graft_entry__ as g
-    g.build()
-    import paper_2110_03513_gb300 as cwb
     dev = torch.device("cuda", 0)
-    data = S.sim_binomial_hybrid(seed=args.seed)
+    data = S.sim_binomial_hybrid(seed=seed)
     p, n = data.X.shape
     stream = torch.cuda.Stream(device=dev)
     learners = [cwb.learner(j, n_bins=1414, df=5.0) for j in range(p)]
@@ -557,11 +630,11 @@ def run_hcwb(args):
             flush.zero_()
             torch.sum(flush, dim=0, keepdim=True, out=sink)
 
-        for _ in range(max(args.warmup, 3)):
+        for _ in range(max(warmup, 3)):
             flush_l2()
             model.fit(1)
         stream.synchronize()
-        K = args.steps
+        K = steps
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
         props = torch.cuda.get_device_properties(dev)
@@ -602,7 +675,7 @@ def run_hcwb(args):
     peak, peak_kind = measured_peaks()
     sc_bytes = p * n_tr * 2 + 2 * n_tr * 4 if acwb == K else p * n * 2 + n * 4
     line = {"metric": "ACWB/HCWB binomial iters/s at n=2M, p=200 (secondary workload)", "value": 1e3 / ms,
-            "unit": "iters/s", "n_gpus": 1, "steps": K, "warmup": args.warmup, "ms_per_step": ms,
+            "unit": "iters/s", "n_gpus": 1, "steps": K, "warmup": warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "HCWB (ACWB gamma=0.001 then CWB), binomial, n=2,000,000, p=200 (100 U[0,1] + "
                                    "100 N(0,1)), 20 informative, 20% validation, n*=1414 uint16, d=24 df=5, "
@@ -610,12 +683,15 @@ def run_hcwb(args):
                        "l2": "flushed before every timed step (256 MiB written, then read; untimed)"},
             "hbm_gbs": alg / (ms / 1e3) / 1e9,
             "roofline": {"bound": "hbm", "achieved": sc_bytes / sc_avg / 1e9, "peak": peak, "unit": "GB/s",
-                         "frac": sc_bytes / sc_avg / 1e9 / peak, "traffic": None, "kernel": "k_scatter",
+                         "frac": sc_bytes / sc_avg / 1e9 / peak,
+                         "traffic": (HCWB_SCATTER_TRAFFIC["bytes"] if acwb == K and
+                                     HCWB_SCATTER_TRAFFIC["sha256"] == scatter_source_hash() else None),
+                         "kernel": "k_scatter",
                          "peak_source": f"{peak_kind} hbm_gbs"},
             "scatter_us": sc_avg * 1e6, "gpu_launches": K * 4, "clocks": clocks, "scatter_plan": plan,
             "setup_ms": t_create * 1e3}
     model.free()
-    print(json.dumps(line), flush=True)
+    return line
 
 
 # ---------------------------------------------------------------------------------------------

@@ -569,6 +569,20 @@ static double learner_value(const bl_state* s, int64_t i, const double* theta)
     return v;
 }
 
+/* Threads of the learner loop in find_best (1 unless orc_set_threads asks for more; without
+ * OpenMP the loop runs on one thread whatever is asked). */
+static int orc_threads = 1;
+
+int orc_set_threads(int t)
+{
+    orc_threads = t < 1 ? 1 : t;
+#ifdef _OPENMP
+    return orc_threads;
+#else
+    return 1;
+#endif
+}
+
 /* findBestBaselearner (Algorithm 1, inner loop; Sec. 3.2): fit every learner to
  * r on the rows in `rows` by penalised least squares, theta_k = P_k Z_k^T W r,
  * compute SSE_k by its definition and return the argmin (ties: lowest k). */
@@ -578,28 +592,41 @@ static void find_best(int32_t K, bl_state* S, int a, int64_t n, const double* w,
 {
     double best = INFINITY, second = INFINITY;
     int32_t kb = -1;
-    double* s_vec = (double*)malloc(sizeof(double) * (size_t)dmax);
+    double* sse_all = (double*)malloc(sizeof(double) * (size_t)(K > 0 ? K : 1));
+    /* The learners' fits are independent: with OpenMP they run on several threads, each learner's
+     * sums still in row order, so every theta_k and SSE_k is the same as on one thread. */
+#pragma omp parallel num_threads(orc_threads)
+    {
+        double* s_vec = (double*)malloc(sizeof(double) * (size_t)dmax);
+#pragma omp for schedule(dynamic, 1)
+        for (int32_t k = 0; k < K; ++k) {
+            bl_state* s = &S[k];
+            int d = s->d;
+            orc_bin_matvec(s->ind, n, w, r, rows, s->nstar, s->Zb, d, s_vec);
+            double* th = theta_all + (int64_t)k * dmax;
+            for (int i = 0; i < dmax; ++i) th[i] = 0.0;
+            for (int i = 0; i < d; ++i) {
+                double t = 0.0;
+                for (int j = 0; j < d; ++j) t += s->P[a][i * d + j] * s_vec[j];
+                th[i] = t;
+            }
+            double sse = 0.0;
+            for (int64_t i = 0; i < n; ++i) {
+                if (rows && !rows[i]) continue;
+                double e = r[i] - learner_value(s, i, th);
+                sse += (w ? w[i] : 1.0) * e * e;
+            }
+            sse_all[k] = sse;
+        }
+        free(s_vec);
+    }
+    /* the argmin in learner order (ties: lowest k) */
     for (int32_t k = 0; k < K; ++k) {
-        bl_state* s = &S[k];
-        int d = s->d;
-        orc_bin_matvec(s->ind, n, w, r, rows, s->nstar, s->Zb, d, s_vec);
-        double* th = theta_all + (int64_t)k * dmax;
-        for (int i = 0; i < dmax; ++i) th[i] = 0.0;
-        for (int i = 0; i < d; ++i) {
-            double t = 0.0;
-            for (int j = 0; j < d; ++j) t += s->P[a][i * d + j] * s_vec[j];
-            th[i] = t;
-        }
-        double sse = 0.0;
-        for (int64_t i = 0; i < n; ++i) {
-            if (rows && !rows[i]) continue;
-            double e = r[i] - learner_value(s, i, th);
-            sse += (w ? w[i] : 1.0) * e * e;
-        }
+        const double sse = sse_all[k];
         if (sse < best) { second = best; best = sse; kb = k; }
         else if (sse < second) { second = sse; }
     }
-    free(s_vec);
+    free(sse_all);
     if (forced >= 0 && forced < K) kb = forced;
     *k_best = kb;
     if (sse1) *sse1 = best;

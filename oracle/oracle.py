@@ -32,8 +32,11 @@ def build(force: bool = False) -> str:
     """Compile the oracle into a shared library next to its source."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-                               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-o", tmp, _SRC]
+        try:      # OpenMP over learners where the compiler has it; the arithmetic is the same either way
+            subprocess.check_call(base + ["-fopenmp", "-lm"], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base + ["-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -71,7 +74,14 @@ def lib():
             L.orc_loss.argtypes = [C.c_int, C.c_double, C.c_double]
             L.orc_pseudo_residual.restype = C.c_double
             L.orc_pseudo_residual.argtypes = [C.c_int, C.c_double, C.c_double]
+            L.orc_set_threads.restype = C.c_int
+            L.orc_set_threads.argtypes = [C.c_int]
         return _lib
+
+
+def set_threads(t: int) -> int:
+    """Threads of the learner loop (1 by default); returns the count in effect (1 without OpenMP)."""
+    return int(lib().orc_set_threads(int(t)))
 
 
 def _p(a):

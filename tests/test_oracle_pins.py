@@ -604,3 +604,23 @@ def test_categorical_rejects_codes_outside_the_classes(bad):
     with pytest.raises(RuntimeError):
         O.fit(np.arange(900.0)[None, :] % 7, y, [dict(type=O.BL_CATEGORICAL_BINARY, feature=0, n_knots=7,
                                                         level=7)], iterations=1)
+
+
+def test_learner_loop_on_several_threads_is_bit_identical():
+    import synthetic_inputs as S
+    """The OpenMP learner loop of the oracle changes only who computes each learner's fit: the
+    selections, coefficients, criteria and fitted values equal the one-thread run bit for bit."""
+    data = S.additive_regression(3000, 6, 3, seed=17, dtype=np.float64)
+    specs = [dict(feature=j) for j in range(6)] + [dict(feature=j, type=O.BL_LINEAR) for j in range(3)]
+    O.set_threads(1)
+    one = O.fit(data.X, data.y, specs, iterations=25)
+    got = O.set_threads(4)
+    try:
+        many = O.fit(data.X, data.y, specs, iterations=25)
+    finally:
+        O.set_threads(1)
+    np.testing.assert_array_equal(one.k_sel, many.k_sel)
+    np.testing.assert_array_equal(one.theta_f, many.theta_f)
+    np.testing.assert_array_equal(one.sse_best, many.sse_best)
+    np.testing.assert_array_equal(one.f, many.f)
+    assert got in (1, 4)
