@@ -90,7 +90,9 @@ def parse_args():
     ap.add_argument("--batched-fits", type=int, default=512,
                     help="fits in the batched measurement (the first of the 512 seeded specs)")
     ap.add_argument("--served-requests", type=int, default=96, help="requests in the served measurement")
-    ap.add_argument("--workload", choices=["binned_l2", "hcwb_binomial", "mise"], default="binned_l2",
+    ap.add_argument("--served-full-requests", type=int, default=16,
+                    help="requests of the full-size served measurement (--workload served_full)")
+    ap.add_argument("--workload", choices=["binned_l2", "hcwb_binomial", "mise", "served_full"], default="binned_l2",
                     help="binned_l2: the headline line (n=1M, p=50); hcwb_binomial: ACWB with the hybrid "
                          "switch, binomial loss, n=2M, p=200, n*=1414 (a separate line); mise: estimation "
                          "quality of partial effects on paper-style simulated data (a separate line)")
@@ -570,6 +572,98 @@ def run_served(cwb, args):
                     "creation; admission by estimated device footprint"}
 
 
+def run_served_full(args):
+    """The served form at the request distribution's own scale: the first R requests of the seeded
+    Poisson stream (variant CWB/ACWB/HCWB and loss L2/binomial uniform, n log-uniform 10k-5M, p
+    log-uniform 10-500, M uniform 500-5000), unscaled, data in FP32 (request_dataset_f32).  Arm 1: the
+    requests one after another (create from host memory, fit, coefficients read back): the sequential
+    capacity.  Arm 2: the fit server under a 160 GiB HBM budget at offered loads 0.8x, 1.0x and 1.2x of
+    that capacity (Poisson arrivals rescaled) and a burst; latency = completion - arrival, creation
+    included.  Every served fit is compared with its sequential fit (same kernels: bit-identical)."""
+    import numpy as np
+    import torch
+    import synthetic_inputs as S
+    import __graft_entry__ as g
+    g.build()
+    import paper_2110_03513_gb300 as cwb
+    R = max(1, args.served_full_requests)
+    stream = S.served_request_stream(count=R, seed=4)
+    t_gen = time.perf_counter()
+    reqs = [(sp, S.request_dataset_f32(sp)) for sp in stream]
+    t_gen = time.perf_counter() - t_gen
+    opts = {0: cwb.OPT_CWB, 1: cwb.OPT_ACWB, 2: cwb.OPT_HCWB}
+    budget = 160 << 30
+
+    def kwargs(sp, d):
+        return dict(loss=cwb.LOSS_BINOMIAL if sp["loss"] == 1 else cwb.LOSS_L2, opt=opts[sp["variant"]], nu=0.1,
+                    gamma=0.001, iterations=sp["iterations"], patience=5, val_mask=d.val_mask)
+
+    def learners(sp):
+        return [cwb.learner(j, n_bins=-1, df=5.0) for j in range(sp["p"])]
+
+    service, coef_alone, trace_alone, creates = [], [], [], []
+    for sp, d in reqs:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m = cwb.Model(d.X, d.y, learners(sp), device=0, **kwargs(sp, d))
+        m.synchronize()
+        creates.append(time.perf_counter() - t0)
+        m.fit(sp["iterations"])
+        coef_alone.append(m.all_coefficients(0, dmax=24))
+        service.append(time.perf_counter() - t0)
+        trace_alone.append(m.trace()[0])
+        m.free()
+    cap = R / sum(service)
+    gaps = np.array([r["arrival_s"] for r in stream])
+    mean_gap = float(np.mean(np.diff(np.concatenate([[0.0], gaps])))) or 1.0
+
+    def replay(load):
+        srv = cwb.Server(hbm_budget_bytes=budget, device=0, max_active=16, slice_iterations=32)
+        arrival = np.zeros(R) if load is None else gaps / mean_gap / (load * cap)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        submitted, done_at, ids = 0, {}, {}
+        while len(done_at) < R:
+            now = time.perf_counter() - t0
+            while submitted < R and arrival[submitted] <= now:
+                sp, d = reqs[submitted]
+                ids[srv.submit(d.X, d.y, learners(sp), **kwargs(sp, d))] = submitted
+                submitted += 1
+            for rid in srv.poll(wait=False):
+                done_at[rid] = time.perf_counter() - t0
+            if submitted == R and len(done_at) < R:
+                for rid in srv.poll(wait=True):
+                    done_at[rid] = time.perf_counter() - t0
+        makespan = max(done_at.values())
+        lat = [done_at[rid] - arrival[i] for rid, i in ids.items()]
+        worst, same_k = 0.0, True
+        for rid, i in ids.items():
+            m = srv.take(rid)
+            th = m.all_coefficients(0, dmax=24)
+            ref = coef_alone[i]
+            worst = max(worst, float(np.abs(th - ref).max()) / (float(np.abs(ref).max()) or 1.0))
+            same_k = same_k and bool(np.array_equal(m.trace()[0], trace_alone[i]))
+            m.free()
+        srv.free()
+        return {"offered_load": load if load is not None else "burst", "fits_per_s": R / makespan,
+                "vs_sequential": (R / makespan) / cap, "makespan_s": makespan,
+                "p50_latency_s": _percentile(lat, 50), "p99_latency_s": _percentile(lat, 99),
+                "max_rel_coef_diff_vs_sequential": worst, "same_selections": same_k}
+
+    runs = [replay(0.8), replay(1.0), replay(1.2), replay(None)]
+    line = {"metric": "served fits/s, full-size request distribution (secondary workload)",
+            "value": max(r["fits_per_s"] for r in runs if r["offered_load"] != "burst"), "unit": "fits/s",
+            "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "first R requests of the seeded Poisson stream (seed 4): variant and loss uniform, "
+                                   "n log-uniform 10k-5M, p log-uniform 10-500, M uniform 500-5000, unscaled",
+                       "requests": R, "hbm_budget_bytes": budget, "max_active": 16, "slice_iterations": 32,
+                       "sizes": [[sp["variant"], sp["loss"], sp["n"], sp["p"], sp["iterations"]] for sp, _ in reqs]},
+            "sequential_fits_per_s": cap, "sequential_total_s": sum(service), "sequential_create_s": sum(creates),
+            "sequential_p50_service_s": _percentile(service, 50), "sequential_p99_service_s": _percentile(service, 99),
+            "runs": runs, "data_generation_s": t_gen}
+    print(json.dumps(line), flush=True)
+
+
 def run_e2e(cwb, data, stream, dev, local):
     """A full fit (M = 2000) through the C ABI from pinned host buffers, results read back."""
     import numpy as np
@@ -809,6 +903,8 @@ def main():
         run_hcwb(args)
     elif args.workload == "mise":
         run_mise(args)
+    elif args.workload == "served_full":
+        run_served_full(args)
     else:
         run_ours(args)
 

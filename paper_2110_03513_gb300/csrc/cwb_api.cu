@@ -174,7 +174,7 @@ cwb_status validate_learner(const cwb_learner& b, int32_t p, int k)
 
 cwb_status create_impl(const cwb_config* cfg, const void* X, int32_t x_dtype, int64_t n, int32_t p, const void* y,
                        const double* w, const cwb_learner* bl, int32_t K, int32_t device_ptrs, cwb_model** out,
-                       int iter_mode, const cwb_shard_config* sc = nullptr)
+                       int iter_mode, const cwb_shard_config* sc = nullptr, int stream_priority = 0)
 {
     if (!out) { set_error("out is NULL"); return CWB_EINVAL; }
     *out = nullptr;
@@ -249,7 +249,7 @@ cwb_status create_impl(const cwb_config* cfg, const void* X, int32_t x_dtype, in
     if (cfg->stream) {
         m->stream = static_cast<cudaStream_t>(cfg->stream);
     } else {
-        cudaError_t e = cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking);
+        cudaError_t e = cudaStreamCreateWithPriority(&m->stream, cudaStreamNonBlocking, stream_priority);
         if (e != cudaSuccess) {
             delete m;
             return cuda_status(e, "cudaStreamCreate");
@@ -366,11 +366,11 @@ cwb_status create_impl(const cwb_config* cfg, const void* X, int32_t x_dtype, in
 
 cwb_status create_model(const cwb_config* cfg, const void* X, int32_t x_dtype, int64_t n, int32_t p, const void* y,
                         const double* w, const cwb_learner* bl, int32_t K, int32_t device_ptrs, cwb_model** out,
-                        int iter_mode)
+                        int iter_mode, int stream_priority)
 {
     set_error("");
     try {
-        return create_impl(cfg, X, x_dtype, n, p, y, w, bl, K, device_ptrs, out, iter_mode);
+        return create_impl(cfg, X, x_dtype, n, p, y, w, bl, K, device_ptrs, out, iter_mode, nullptr, stream_priority);
     } catch (const std::exception& e) {
         set_error(std::string("host exception: ") + e.what());
         return CWB_ENOMEM;

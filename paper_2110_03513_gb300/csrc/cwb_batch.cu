@@ -7,6 +7,7 @@
 //               estimated device footprint fits a budget, run in slices of iterations on their
 //               own streams (interleaved on the GPU) and are handed back when done.
 #include <algorithm>
+#include <cmath>
 #include <chrono>
 #include <deque>
 #include <string>
@@ -216,6 +217,7 @@ struct Request {
     std::vector<cwb_learner> bl;
     std::vector<uint8_t> val_mask;        // copied: the config's pointer need not outlive submit
     uint64_t footprint = 0;
+    uint64_t index_bytes = 0;             // the index matrix's bytes (read once per iteration)
 };
 
 struct Active {
@@ -244,8 +246,9 @@ namespace {
 constexpr int kSlicesInFlight = 2;
 
 // Device bytes a fit holds while it runs (index matrix, row vectors, design tables, caches), plus
-// the feature copy its creation stages.  An estimate from the request alone.
-uint64_t estimate_footprint(const Request& r)
+// the feature copy its creation stages.  An estimate from the request alone; also records the index
+// matrix's bytes in the request.
+uint64_t estimate_footprint(Request& r)
 {
     const uint64_t n_pad = ((uint64_t)r.n + 255) / 256 * 256;
     std::vector<std::pair<int, int>> bins;
@@ -272,6 +275,7 @@ uint64_t estimate_footprint(const Request& r)
     const bool accel = r.cfg.opt != CWB_OPT_CWB;
     const uint64_t elem = nstar_max <= 256 ? 1 : 2;
     uint64_t bytes = B * n_pad * elem;                                  // index matrix
+    r.index_bytes = bytes;
     bytes += n_pad * (4 + 4 + 4 + 8 + 8);                               // y, y_lo, w, f, rw
     if (accel) bytes += n_pad * (8 + 4 + 4 + 4);                        // h, c, second channel, perm
     bytes += K * nstar_max * (16 + 4 + 16 + 8 + 8);                     // zb, zcol, ztab, v, zb64
@@ -280,6 +284,24 @@ uint64_t estimate_footprint(const Request& r)
     bytes += (uint64_t)r.p * r.n * (r.x_dtype == CWB_F64 ? 8 : 4);      // staged features during creation
     bytes += 64ull << 20;                                               // traces, tables, slack
     return bytes;
+}
+
+// Stream priority of a request: fits with less work (index bytes x iterations) run on streams of
+// higher priority, so that their kernels are dispatched ahead of those of long fits when SMs free up
+// (shortest work first: small requests finish without waiting behind the long ones; the long fits
+// take the SMs whenever the short ones have nothing queued).
+int request_priority(const Request& r, uint64_t footprint_index_bytes)
+{
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    const double work = (double)footprint_index_bytes * (double)std::max(1, r.cfg.iterations);
+    const int levels = least - greatest + 1;              // greatest is the most negative (highest) priority
+    int level = (int)std::floor(std::log10(std::max(work, 1.0))) - 8;
+    level = std::max(0, std::min(levels - 1, level));
+    return greatest + level;
 }
 
 bool slice_finished(Active& a)
@@ -379,7 +401,7 @@ cwb_status cwb_server_poll(cwb_server* s, int32_t wait, int64_t* done_ids, int32
             // server fits interleave their iterations with other fits on the GPU: the three-kernel path
             // (a persistent kernel would hold every SM for its whole slice)
             cwb_status st = create_model(&r.cfg, r.X, r.x_dtype, r.n, r.p, r.y, r.w, r.bl.data(), (int32_t)r.bl.size(), 0,
-                                         &a.m, kIterKernels);
+                                         &a.m, kIterKernels, request_priority(r, r.index_bytes));
             if (st != CWB_OK) {
                 s->failed[r.id] = cwb_last_error();
                 s->completed += 1;

@@ -71,6 +71,8 @@ struct DevState {
     int32_t cnt_log2p;      // ceil(log2(largest per-CTA bin count)) of the persistent plan
     int32_t fix_exp;        // fixed-point exponent of the residuals the persistent path wrote last
     int32_t resid_path;     // 0: the latest residuals are FP32 in rw, 1: fixed point in rq (persistent path)
+    int32_t resid_stale;    // HCWB: the row pass switched to CWB after computing ACWB residuals; the
+                            // residual pass that follows it recomputes them for the CWB iteration
 };
 
 // How cwb_fit runs iterations: auto picks the persistent kernel when the model qualifies.
@@ -299,10 +301,11 @@ cwb_status launch_persistent(cwb_model* m, int32_t iters);
 cwb_status persistent_profile(cwb_model* m, double ms[3], int64_t* iters, bool reset);
 cwb_status persistent_residuals(cwb_model* m, float* out_dev);
 
-// Model creation with an explicit iteration mode (kIterAuto, kIterKernels, kIterPersistent)
+// Model creation with an explicit iteration mode (kIterAuto, kIterKernels, kIterPersistent) and,
+// when the model creates its own stream, that stream's priority (0: the default)
 cwb_status create_model(const cwb_config* cfg, const void* X, int32_t x_dtype, int64_t n, int32_t p, const void* y,
                         const double* w, const cwb_learner* bl, int32_t K, int32_t device_ptrs, cwb_model** out,
-                        int iter_mode);
+                        int iter_mode, int stream_priority = 0);
 
 // Predict / fitted (cwb_api.cu)
 cwb_status launch_predict(const cwb_model* m, const void* Xnew, int x_dtype, int64_t n_new, float* out_dev);

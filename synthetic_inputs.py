@@ -29,6 +29,7 @@ __all__ = [
     "batched_fit_specs",
     "served_request_stream",
     "request_dataset",
+    "request_dataset_f32",
     "paper_style_simulation",
     "paper_style_effect",
     "paper_style_sample",
@@ -225,6 +226,33 @@ def request_dataset(spec: dict, dtype=np.float32) -> Dataset:
     val = (rng.random(n) < 0.2).astype(np.uint8) if int(spec.get("variant", 0)) == 2 else None
     return Dataset(X=d.X.astype(dtype), y=y.astype(dtype), val_mask=val, eta=d.eta,
                    description=f"request n={n} p={p} seed={seed}")
+
+
+def request_dataset_f32(spec: dict) -> Dataset:
+    """Data of one full-size fit request (n up to 5M, p up to 500), drawn straight in FP32 so that the
+    largest requests (billions of feature values) are generated without FP64 copies.
+
+    Features are U[0, 1) FP32 from PCG64(seed); the first min(p, 10) carry the additive effects of
+    ``additive_regression`` evaluated in FP64 on the FP32 values; Gaussian noise at SNR 1 (PCG64(seed ^
+    0x5EED)).  Binomial requests (loss 1) centre and scale the signal to unit standard deviation and draw
+    y ~ Bernoulli(sigmoid(signal)); hybrid requests (variant 2) draw a 20% validation mask.
+    """
+    n, p, seed = int(spec["n"]), int(spec["p"]), int(spec["seed"])
+    rng = np.random.Generator(np.random.PCG64(seed))
+    X = rng.random((p, n), dtype=np.float32)
+    eta = np.zeros(n, dtype=np.float64)
+    for j in range(min(p, 10)):
+        eta += _effect((j % 10) + 1, X[j].astype(np.float64))
+    rng2 = np.random.Generator(np.random.PCG64(seed ^ 0x5EED))
+    if int(spec.get("loss", 0)) == 1:
+        z = eta - eta.mean()
+        z /= max(float(z.std()), 1e-12)
+        y = (rng2.random(n) < 1.0 / (1.0 + np.exp(-z))).astype(np.float32)
+    else:
+        sd = float(np.std(eta)) if n > 1 else 1.0
+        y = (eta + rng2.standard_normal(n) * sd).astype(np.float32)
+    val = (rng2.random(n) < 0.2).astype(np.uint8) if int(spec.get("variant", 0)) == 2 else None
+    return Dataset(X=X, y=y, val_mask=val, eta=eta, description=f"full-size request n={n} p={p} seed={seed}")
 
 
 def paper_style_effect(truth_j: tuple, x: np.ndarray) -> np.ndarray:
