@@ -141,6 +141,9 @@ __global__ void __launch_bounds__(kRowThreads, 4) k_rows(RowArgs a)
     grid_dep_launch();
     if (a.hybrid) first_pass_loads();
     const DevState st = *a.state;
+    // HCWB runs the fused pass (update, validation risk, residuals of the current mode) and then this
+    // residual pass, which has work only in the iteration where the fused pass switched to CWB
+    if (KIND == kRowsResid && a.hybrid && !st.resid_stale) return;
     const bool pend = (KIND != kRowsResid) && (st.m > st.m_applied);
     const int pm = st.pend_mode;
     const bool pm_acwb = ACC && pm == kModeACWB;
@@ -191,7 +194,7 @@ __global__ void __launch_bounds__(kRowThreads, 4) k_rows(RowArgs a)
     const DF nu = {a.nu_hi, a.nu_lo};
     const bool need_bc = pend && pm_acwb;
     const bool need_bc_resid = (KIND != kRowsUpdate) && acwb_n && !first_acwb;
-    const bool eval_risk = (KIND == kRowsUpdate) && a.hybrid && (!st.risk_valid || (pend && pm_acwb));
+    const bool eval_risk = (KIND != kRowsResid) && a.hybrid && (!st.risk_valid || (pend && pm_acwb));
 
     double risk_acc = 0.0;
     float rmax0 = 0.0f, rmax1 = 0.0f;
@@ -330,9 +333,9 @@ __global__ void __launch_bounds__(kRowThreads, 4) k_rows(RowArgs a)
             if (acwb_n) atomicMax(&a.state->rmax_bits[1], __float_as_uint(b1));
             if (bad_blk) atomicOr(&a.state->err, kErrNonFinite);
         }
-        // the residual passes end here: the next iteration's row pass sees m > m_applied for
-        // the pending update, and only the update pass records what it applied
-        if (KIND != kRowsUpdate) return;
+        // the residual passes end here (the fused pass too, outside HCWB): the next iteration's row
+        // pass sees m > m_applied for the pending update, and only an update pass records what it applied
+        if (KIND == kRowsResid || !a.hybrid) return;
     }
     if (eval_risk) {
         red[threadIdx.x] = risk_acc;
@@ -378,10 +381,21 @@ __global__ void __launch_bounds__(kRowThreads, 4) k_rows(RowArgs a)
                 S->risk_prev = risk;
             }
         }
-        if (KIND == kRowsUpdate && a.hybrid && S->mode == kModeACWB && S->counter >= a.patience) {
+        bool switched = false;
+        if (KIND != kRowsResid && a.hybrid && S->mode == kModeACWB && S->counter >= a.patience) {
             S->mode = kModeCWB;
             S->phase = 1;
             S->switch_iter = S->m + 1;
+            switched = true;
+        }
+        if (KIND == kRowsFused) {
+            // the residuals this pass wrote are those of the mode it started in; after a switch the
+            // residual pass recomputes them (CWB on all rows) and takes the maxima afresh
+            S->resid_stale = switched ? 1 : 0;
+            if (switched) {
+                S->rmax_bits[0] = 0u;
+                S->rmax_bits[1] = 0u;
+            }
         }
         if (pend) S->m_applied = st.m;
         S->ticket_rows = 0;
@@ -430,6 +444,7 @@ struct ScatterArgs {
 };
 
 constexpr int kEpiVec = 4;                         // 16-byte vectors per thread and pass of the cluster epilogue
+constexpr int kMaxScatterStages = 16;              // ring stages of the scatter (shared memory permitting)
 
 // FL2 >= 0: the lanes per channel F = 2^FL2 is a compile-time constant (the common plans), -1: read at run time.
 template <typename IndT, int CMAX, bool INT_ACC, bool RANGED, int FL2>
@@ -1371,6 +1386,7 @@ cudaError_t launch_scatter_t(cwb_model* m, cudaStream_t s, const ScatterArgs& a)
     if (P.bin_ranges > 1) return cudaLaunchKernelEx(&cfg, k_scatter<IndT, CMAX, INT_ACC, true, -1>, m->tmap, a);
     if (P.f_lane == 32) return cudaLaunchKernelEx(&cfg, k_scatter<IndT, CMAX, INT_ACC, false, 5>, m->tmap, a);
     if (P.f_lane == 16) return cudaLaunchKernelEx(&cfg, k_scatter<IndT, CMAX, INT_ACC, false, 4>, m->tmap, a);
+    if (P.f_lane == 8) return cudaLaunchKernelEx(&cfg, k_scatter<IndT, CMAX, INT_ACC, false, 3>, m->tmap, a);
     return cudaLaunchKernelEx(&cfg, k_scatter<IndT, CMAX, INT_ACC, false, -1>, m->tmap, a);
 }
 
@@ -1512,6 +1528,7 @@ cwb_status prepare_scatter_kernel(cwb_model* m, int cs, int* active_clusters)
         (const void*)k_scatter<IndT, CMAX, true, true, -1>,  (const void*)k_scatter<IndT, CMAX, false, true, -1>,
         (const void*)k_scatter<IndT, CMAX, true, false, 5>,  (const void*)k_scatter<IndT, CMAX, false, false, 5>,
         (const void*)k_scatter<IndT, CMAX, true, false, 4>,  (const void*)k_scatter<IndT, CMAX, false, false, 4>,
+        (const void*)k_scatter<IndT, CMAX, true, false, 3>,  (const void*)k_scatter<IndT, CMAX, false, false, 3>,
         (const void*)k_scatter<IndT, CMAX, true, false, -1>, (const void*)k_scatter<IndT, CMAX, false, false, -1>};
     for (const void* kf : kernels) {
         CWB_CUDA_TRY(allow_max_dynamic_smem(kf, m->device));
@@ -1578,12 +1595,8 @@ void enqueue_iteration(cwb_model* m, cudaStream_t s, int mask)
         if (mask & (1 << cls)) cudaEventRecordWithFlags(m->prof_ph[2 * cls + edge], s, cudaEventRecordExternal);
     };
     mark(0, 0);
-    if (m->hybrid) {
-        launch_rows<kRowsUpdate>(m, s);
-        launch_rows<kRowsResid>(m, s);
-    } else {
-        launch_rows<kRowsFused>(m, s);
-    }
+    launch_rows<kRowsFused>(m, s);
+    if (m->hybrid) launch_rows<kRowsResid>(m, s);        // work only in the iteration that switches to CWB
     mark(0, 1);
     mark(1, 0);
     launch_scatter(m, s);
@@ -1638,8 +1651,11 @@ cwb_status plan_scatter(cwb_model* m, int max_ctas, int cs_req)
     // a stage's index box starts on a 1024-byte boundary (the 128-byte swizzle pattern repeats every 1 KB)
     auto stage_bytes = [&](int F) { return ((F * P.stage_rows * elem + 1023) / 1024) * 1024 + cmax * P.stage_rows * 4; };
     P.f_lane = 0;
+    int f_req = 0;
+    if (const char* env = std::getenv("CWB_F_LANE")) f_req = std::atoi(env);
     for (int F = 32; F >= 1; F >>= 1) {
         if (F * cmax > 32 || F > pow2B) continue;
+        if (f_req > 0 && F > f_req) continue;
         if (hist_bytes(nbins, F) + 3 * stage_bytes(F) <= budget) {
             P.f_lane = F;
             break;
@@ -1659,7 +1675,7 @@ cwb_status plan_scatter(cwb_model* m, int max_ctas, int cs_req)
     P.stage_ind_bytes = (uint32_t)(((P.box_bytes + 1023) / 1024) * 1024);
     P.stage_r_bytes = (uint32_t)(cmax * P.stage_rows * 4);
     const int hb = hist_bytes(P.nb_cta, F);
-    P.stages = std::min(8, (budget - hb) / stage_bytes(P.fe));
+    P.stages = std::min(kMaxScatterStages, (budget - hb) / stage_bytes(P.fe));
     P.ind_off = 0;
     P.r_off = P.ind_off + (uint32_t)P.stages * P.stage_ind_bytes;
     P.q_off = P.r_off;                              // fixed point replaces the residuals in place
