@@ -444,7 +444,6 @@ struct ScatterArgs {
 };
 
 constexpr int kEpiVec = 4;                         // 16-byte vectors per thread and pass of the cluster epilogue
-constexpr int kMaxScatterStages = 16;              // ring stages of the scatter (shared memory permitting)
 
 // FL2 >= 0: the lanes per channel F = 2^FL2 is a compile-time constant (the common plans), -1: read at run time.
 template <typename IndT, int CMAX, bool INT_ACC, bool RANGED, int FL2>
@@ -1625,6 +1624,7 @@ void release_scatter_plan(cwb_model* m)
 // work: every resident CTA for large inputs, about kTilesPerCta tile-slots per CTA for small ones,
 // so that small fits leave SMs to others.  cs_req > 0 forces the cluster size when it can be resident.
 constexpr int kTilesPerCta = 8;
+constexpr int kMaxScatterStages = 8;               // ring stages of the scatter (shared memory permitting)
 
 cwb_status plan_scatter(cwb_model* m, int max_ctas, int cs_req)
 {
@@ -1676,12 +1676,16 @@ cwb_status plan_scatter(cwb_model* m, int max_ctas, int cs_req)
     P.stage_r_bytes = (uint32_t)(cmax * P.stage_rows * 4);
     const int hb = hist_bytes(P.nb_cta, F);
     P.stages = std::min(kMaxScatterStages, (budget - hb) / stage_bytes(P.fe));
-    P.ind_off = 0;
-    P.r_off = P.ind_off + (uint32_t)P.stages * P.stage_ind_bytes;
-    P.q_off = P.r_off;                              // fixed point replaces the residuals in place
-    P.hist_off = ((P.q_off + (uint32_t)P.stages * P.stage_r_bytes + 1023) / 1024) * 1024;
-    P.bar_off = P.hist_off + (uint32_t)hb;
-    P.smem = (size_t)P.bar_off + 3 * 8 * P.stages + 1024;
+    for (;;) {
+        P.ind_off = 0;
+        P.r_off = P.ind_off + (uint32_t)P.stages * P.stage_ind_bytes;
+        P.q_off = P.r_off;                              // fixed point replaces the residuals in place
+        P.hist_off = ((P.q_off + (uint32_t)P.stages * P.stage_r_bytes + 1023) / 1024) * 1024;
+        P.bar_off = P.hist_off + (uint32_t)hb;
+        P.smem = (size_t)P.bar_off + 3 * 8 * P.stages + 1024;   // + alignment slack of the dynamic base
+        if (P.smem <= (size_t)optin || P.stages <= 1) break;
+        --P.stages;
+    }
     P.slots = P.groups * P.bin_ranges;
     P.threads = kScatterThreads;
     m->plan = P;
