@@ -165,7 +165,8 @@ cwb_status cwb_create(const cwb_config* cfg, const void* X, int32_t x_dtype, int
  * coefficients apply it first.  A device-side wait that ran out is reported by
  * the next call that synchronises, as CWB_ETIMEOUT (the kernel that waited has
  * returned; the model's state is then undefined, other models are unaffected);
- * a non-finite residual or criterion (a diverging fit) as CWB_ENUMERIC.  The
+ * a non-finite residual or criterion (a diverging fit), or a residual above the
+ * bound of its fixed-point scale (which the bound rules out), as CWB_ENUMERIC.  The
  * limit of the waits is about two seconds; the environment variable
  * CWB_WAIT_CYCLES, read when a model is created, sets it in SM clock cycles.
  */
@@ -283,6 +284,13 @@ cwb_status cwb_get_residuals(const cwb_model* m, int32_t channel, float* out);
  * cwb_fit call with grid-wide barriers between the phases of an iteration
  * (cwb_create fails with CWB_EINVAL for a model that does not qualify).  Both
  * compute the same iteration; results agree within the oracle tolerances.
+ *
+ * In the three-kernel path, plain CWB models with fixed-point histograms have
+ * the row pass write the residuals as int32 fixed point directly, at a scale set
+ * by a bound on max |w r| known before the pass (the previous maximum plus the
+ * pending update's largest step; max w for the binomial loss), so the scatter
+ * needs no conversion step.  CWB_DIRECT_Q=0, read when a model is created, keeps
+ * the conversion inside the scatter (scale from the measured maximum) instead.
  */
 cwb_status cwb_get_scatter_plan(const cwb_model* m, int32_t* values, int32_t cap);
 

@@ -240,6 +240,7 @@ cwb_status create_impl(const cwb_config* cfg, const void* X, int32_t x_dtype, in
         m->withhold_tile = std::atoi(wt);
     }
     if (const char* lk = std::getenv("CWB_L2_KEEP")) m->l2_keep = std::atoi(lk) != 0;
+    if (const char* dq = std::getenv("CWB_DIRECT_Q")) m->direct_enabled = std::atoi(dq) != 0;
     if (const char* mode = std::getenv("CWB_ITER_MODE")) {
         // "kernels" or unset: three kernels per iteration (rows, scatter, solve) launched from CUDA
         // graphs; "persistent": one persistent cooperative kernel for plain CWB models that qualify
@@ -339,6 +340,7 @@ cwb_status create_impl(const cwb_config* cfg, const void* X, int32_t x_dtype, in
             if (e != cudaSuccess) st = cuda_status(e, "state init");
         }
         if (st == CWB_OK) st = scatter_count_pass(m);
+        if (st == CWB_OK && !m->accel && !m->shard) st = init_residual_bound(m);
         if (st == CWB_OK) st = plan_persistent(m);
         if (st == CWB_OK && m->iter_mode == kIterPersistent && !m->persist_ok) {
             set_error("CWB_ITER_MODE=persistent: this model does not qualify for the persistent iteration kernel");
@@ -637,6 +639,16 @@ cwb_status cwb_get_residuals(const cwb_model* m, int32_t channel, float* out)
     } else {
         CWB_CUDA_TRY(cudaMemcpyAsync(raw.data(), m->rw + (int64_t)channel * m->n_pad, sizeof(float) * m->n,
                                      cudaMemcpyDeviceToHost, m->stream));
+    }
+    if (st.resid_path == 2) {
+        // the row pass wrote w r as int32 fixed point, w r * 2^fix_exp (channel 1 is not used)
+        CWB_CUDA_TRY(cudaStreamSynchronize(m->stream));
+        const double sc = ldexp(1.0, -st.fix_exp);
+        for (int64_t q = 0; q < m->n; ++q) {
+            int32_t v;
+            std::memcpy(&v, &raw[q], sizeof(v));
+            raw[q] = channel == 1 ? 0.0f : (float)((double)v * sc);
+        }
     }
     if (m->perm) {
         perm.resize(m->n);

@@ -244,6 +244,20 @@ __device__ __forceinline__ int fixed_scale(uint32_t rmax_bits, int cnt_log2)
     return max(-120, min(100, 30 - cnt_log2 - e));
 }
 
+// Upper bound (FP32 bits) on max |w r| of the residuals a row pass is about to form, known before
+// the pass: binomial |y - sigmoid(f)| < 1, so max w bounds it; L2 residuals move by at most
+// nu max|w| max|v_k*| from the previous ones (max |w r| of the previous pass, rprev) when an update
+// is pending.  A relative margin of 2^-12 covers the rounding of the compensated update.
+__device__ __forceinline__ uint32_t residual_bound(int loss, bool pending, uint32_t rprev_bits, float vmax_sel,
+                                                   float nu, float wmax)
+{
+    float b;
+    if (loss == CWB_LOSS_BINOMIAL) b = wmax;
+    else b = __uint_as_float(rprev_bits) + (pending ? nu * wmax * vmax_sel : 0.0f);
+    b = b * (1.0f + 1.0f / 4096.0f);
+    return __float_as_uint(b);
+}
+
 // 2^e as an FP32 value for -126 <= e <= 127 (fixed_scale keeps every exponent used here in range).
 __device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }
 

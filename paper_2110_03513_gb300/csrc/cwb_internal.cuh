@@ -42,6 +42,7 @@ enum : uint32_t {
     kErrNumeric = 2u,      // factorisation failed / df not reachable
     kErrIndex = 4u,        // an index fell outside its table (should never happen)
     kErrNonFinite = 8u,    // non-finite criterion
+    kErrBound = 16u,       // a residual above the bound that set its fixed-point scale (should never happen)
 };
 
 enum : int32_t { kModeCWB = 0, kModeACWB = 1 };
@@ -219,6 +220,7 @@ struct cwb_model {
     float* ztab_lo = nullptr;             // [K][4 S] low parts of the column-major design
     float* vmax = nullptr;                // [K] max |v_k| of the latest update tables
     double wmax = 1.0;                    // largest observation weight
+    bool direct_enabled = true;           // CWB_DIRECT_Q=0 turns the direct fixed-point residuals off
     long long wait_cycles = 4000000000LL; // limit of each device-side ring wait (SM clocks, ~2 s)
     int l2_keep = 0;                      // scatter copies with L2 hints: the index kept, the residual rows streamed
     int withhold_tile = -1;               // test hook (CWB_WITHHOLD_TILE): a scatter tile whose copies are never issued
@@ -297,6 +299,16 @@ cwb_status shard_solve(cwb_model* m, const long long* u, int device_ptrs);
 
 // Persistent iteration kernel (cwb_persist.cu)
 cwb_status plan_persistent(cwb_model* m);
+cwb_status init_residual_bound(cwb_model* m);
+
+// Plain CWB with exact fixed-point histograms: the row pass writes the residuals as int32 fixed
+// point with a scale from residual_bound (known before the pass), so the scatter needs no conversion
+// step.  Accelerated, hybrid and sharded models and the persistent path keep the converter.
+inline bool direct_q(const cwb_model* m)
+{
+    return !m->accel && !m->hybrid && !m->shard && m->plan.int_acc && m->direct_enabled &&
+           m->iter_mode != kIterPersistent;
+}
 cwb_status launch_persistent(cwb_model* m, int32_t iters);
 cwb_status persistent_profile(cwb_model* m, double ms[3], int64_t* iters, bool reset);
 cwb_status persistent_residuals(cwb_model* m, float* out_dev);

@@ -61,6 +61,9 @@ struct RowArgs {
     int hybrid;
     int patience;
     double* risk_part;
+    int direct;               // plain CWB: write w r as int32 fixed point (scale from residual_bound)
+    float wmax;               // largest observation weight (1 without weights)
+    const float* vmax;        // [K] max |v_k| of the last solve
 };
 
 __device__ __forceinline__ float get4(const float4& v, int t)
@@ -143,7 +146,7 @@ __global__ void __launch_bounds__(kRowThreads, 4) k_rows(RowArgs a)
     const DevState st = *a.state;
     // HCWB runs the fused pass (update, validation risk, residuals of the current mode) and then this
     // residual pass, which has work only in the iteration where the fused pass switched to CWB
-    if (KIND == kRowsResid && a.hybrid && !st.resid_stale) return;
+    if (KIND == kRowsResid && ACC && a.hybrid && !st.resid_stale) return;
     const bool pend = (KIND != kRowsResid) && (st.m > st.m_applied);
     const int pm = st.pend_mode;
     const bool pm_acwb = ACC && pm == kModeACWB;
@@ -194,7 +197,25 @@ __global__ void __launch_bounds__(kRowThreads, 4) k_rows(RowArgs a)
     const DF nu = {a.nu_hi, a.nu_lo};
     const bool need_bc = pend && pm_acwb;
     const bool need_bc_resid = (KIND != kRowsUpdate) && acwb_n && !first_acwb;
-    const bool eval_risk = (KIND != kRowsResid) && a.hybrid && (!st.risk_valid || (pend && pm_acwb));
+    const bool eval_risk = (KIND != kRowsResid) && ACC && a.hybrid && (!st.risk_valid || (pend && pm_acwb));
+    // plain CWB: the residuals go out as int32 fixed point at the scale of a bound on max |w r| known
+    // before the pass, so the scatter needs no conversion step (the histograms keep their overflow
+    // guarantee as long as the bound holds, which is checked)
+    constexpr bool kDirect = !ACC && KIND == kRowsFused;
+    int q_exp = 0;
+    float q_scale = 1.0f, q_bound = 0.0f;
+    if (kDirect && a.direct) {
+        const float vsel = (pend && st.k_sel >= 0) ? __ldcg(a.vmax + st.k_sel) : 0.0f;
+        const uint32_t bb = residual_bound(a.loss, pend, st.rprev_bits, vsel, a.nu_hi, a.wmax);
+        q_exp = fixed_scale(bb, st.cnt_log2[0]);
+        q_scale = pow2f(q_exp);
+        q_bound = __uint_as_float(bb);
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            a.state->fix_exp = q_exp;
+            a.state->resid_path = 2;
+        }
+    }
+    bool over_bound = false;
 
     double risk_acc = 0.0;
     float rmax0 = 0.0f, rmax1 = 0.0f;
@@ -291,7 +312,14 @@ __global__ void __launch_bounds__(kRowThreads, 4) k_rows(RowArgs a)
                     nonfinite = true;
                 rmax0 = fmaxf(rmax0, m0);
                 rmax1 = fmaxf(rmax1, m1);
-                *reinterpret_cast<float4*>(a.rw + i4) = r0;
+                if (kDirect && a.direct) {
+                    if (m0 > q_bound) over_bound = true;
+                    *reinterpret_cast<int4*>(a.rw + i4) =
+                        make_int4(__float2int_rn(r0.x * q_scale), __float2int_rn(r0.y * q_scale),
+                                  __float2int_rn(r0.z * q_scale), __float2int_rn(r0.w * q_scale));
+                } else {
+                    *reinterpret_cast<float4*>(a.rw + i4) = r0;
+                }
                 if (acwb_n) {
                     *reinterpret_cast<float4*>(a.rw + a.n_pad + i4) = r1;
                     *reinterpret_cast<float4*>(a.c + i4) = c4;
@@ -313,6 +341,7 @@ __global__ void __launch_bounds__(kRowThreads, 4) k_rows(RowArgs a)
             rmax1 = fmaxf(rmax1, __shfl_xor_sync(0xffffffffu, rmax1, o));
         }
         const bool anybad = __any_sync(0xffffffffu, nonfinite);
+        if (kDirect && __any_sync(0xffffffffu, over_bound) && (threadIdx.x & 31) == 0) atomicOr(&a.state->err, kErrBound);
         __shared__ bool wbad[kRowThreads / 32];
         if ((threadIdx.x & 31) == 0) {
             wmax[0][threadIdx.x >> 5] = rmax0;
@@ -335,7 +364,7 @@ __global__ void __launch_bounds__(kRowThreads, 4) k_rows(RowArgs a)
         }
         // the residual passes end here (the fused pass too, outside HCWB): the next iteration's row
         // pass sees m > m_applied for the pending update, and only an update pass records what it applied
-        if (KIND == kRowsResid || !a.hybrid) return;
+        if (KIND == kRowsResid || !(ACC && a.hybrid)) return;   // (HCWB models are accelerated)
     }
     if (eval_risk) {
         red[threadIdx.x] = risk_acc;
@@ -382,7 +411,7 @@ __global__ void __launch_bounds__(kRowThreads, 4) k_rows(RowArgs a)
             }
         }
         bool switched = false;
-        if (KIND != kRowsResid && a.hybrid && S->mode == kModeACWB && S->counter >= a.patience) {
+        if (KIND != kRowsResid && ACC && a.hybrid && S->mode == kModeACWB && S->counter >= a.patience) {
             S->mode = kModeCWB;
             S->phase = 1;
             S->switch_iter = S->m + 1;
@@ -398,6 +427,11 @@ __global__ void __launch_bounds__(kRowThreads, 4) k_rows(RowArgs a)
             }
         }
         if (pend) S->m_applied = st.m;
+        if (KIND == kRowsUpdate && pend && st.k_sel >= 0) {
+            // this pass moved f without forming residuals: widen the bound on max |w r| by the update,
+            // so that the next row pass's fixed-point scale stays valid
+            S->rprev_bits = residual_bound(a.loss, true, S->rprev_bits, __ldcg(a.vmax + st.k_sel), a.nu_hi, a.wmax);
+        }
         S->ticket_rows = 0;
     }
 }
@@ -441,6 +475,7 @@ struct ScatterArgs {
     long long wait_cycles;         // limit of each ring wait (SM clocks); copies in flight are drained with kWaitCycles
     int withhold;                  // test hook: >= 0 makes CTA 0 arm, but never fill, its tile min(withhold, ntiles - 1)
     int l2_keep;                   // 1: index boxes with the evict-last hint, residual rows with evict-first
+    int direct;                    // 1: the residual rows are already int32 fixed point (no conversion step)
 };
 
 constexpr int kEpiVec = 4;                         // 16-byte vectors per thread and pass of the cluster epilogue
@@ -577,7 +612,7 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
                     if (it != wh) mbar_wait(&full[it % a.stages], (it / a.stages) & 1, d2);
             }
         }
-    } else if (warp == W + 1) {
+    } else if (warp == W + 1 && !a.direct) {
         // converter: residual tile -> fixed point (or a plain hand-over for FP32 accumulation)
         if (fixed_mode) grid_dep_wait();
         float scale[2] = {1.0f, 1.0f};
@@ -628,7 +663,7 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
             __syncwarp();
             if (lane == 0) mbar_arrive(&ready[s]);
         }
-    } else {
+    } else if (warp < W) {
         const int q = lane / F;
         const int f = lane % F;
         const int ch = q % C, rs = q / C;
@@ -645,7 +680,8 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
                 s = 0;
                 ph ^= 1u;
             }
-            if (!__all_sync(0xffffffffu, mbar_wait(&ready[s], ph, deadline))) {
+            // (without a conversion step the stage is ready as soon as its copies have landed)
+            if (!__all_sync(0xffffffffu, mbar_wait(a.direct ? &full[s] : &ready[s], ph, deadline))) {
                 if (lane == 0) atomicOr(a.err, kErrTimeout);
                 break;
             }
@@ -859,8 +895,9 @@ struct SolveArgs {
     double* tr_q;             // [cap][2]
     const int32_t* forced;    // [cap]
     int trace_cap;
-    float* vmax;              // [K] max |v_k| of channel 0 (the bound of the persistent path's fixed point)
+    float* vmax;              // [K] max |v_k| of channel 0 (input of the residual bound of the next row pass)
     const long long* u64;     // row shards: exact histogram sums [B][S] of all shards (replaces the partials)
+    int direct;               // the row pass wrote the fixed point itself, at the state's fix_exp
 };
 
 __device__ __forceinline__ void cp_async4(void* dst, const void* src)
@@ -1051,7 +1088,7 @@ __global__ void __launch_bounds__(kSolveThreads, 512 / kSolveThreads) k_solve(So
             if (INT_ACC) {
                 // (selects, not an index: a run-time index into the state copy would put it in local memory)
                 const int cl2 = (a.hybrid && mode == kModeACWB) ? st.cnt_log2[1] : st.cnt_log2[0];
-                scl0 = pow2f(-fixed_scale(st.rmax_bits[0], cl2));
+                scl0 = a.direct ? pow2f(-st.fix_exp) : pow2f(-fixed_scale(st.rmax_bits[0], cl2));
                 scl1 = pow2f(-fixed_scale(st.rmax_bits[1], cl2));
             }
 #pragma unroll
@@ -1264,7 +1301,7 @@ __global__ void __launch_bounds__(kSolveThreads, 512 / kSolveThreads) k_solve(So
         S_->pend_mode = mode;
         S_->m = st.m + 1;
         S_->rprev_bits = S_->rmax_bits[0];   // max |w r| of this iteration (input of the persistent path's bound)
-        S_->resid_path = 0;
+        S_->resid_path = a.direct ? 2 : 0;
         S_->rmax_bits[0] = 0u;           // the next row pass takes its maxima with atomicMax
         S_->rmax_bits[1] = 0u;
         S_->ticket_solve = 0;
@@ -1339,6 +1376,9 @@ RowArgs row_args(cwb_model* m)
     a.hybrid = m->hybrid ? 1 : 0;
     a.patience = m->cfg.patience;
     a.risk_part = m->risk_part;
+    a.direct = direct_q(m) ? 1 : 0;
+    a.wmax = (float)m->wmax;
+    a.vmax = m->vmax;
     return a;
 }
 
@@ -1427,6 +1467,7 @@ ScatterArgs scatter_args(cwb_model* m)
     a.wait_cycles = m->wait_cycles;
     a.withhold = m->withhold_tile;
     a.l2_keep = m->l2_keep;
+    a.direct = direct_q(m) ? 1 : 0;
     return a;
 }
 
@@ -1498,6 +1539,7 @@ void launch_solve(cwb_model* m, cudaStream_t s)
     a.trace_cap = m->trace_cap;
     a.vmax = m->vmax;
     a.u64 = m->solve_u64;
+    a.direct = direct_q(m) ? 1 : 0;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(m->K, 1, 1);
     const int threads = solve_threads(m);
@@ -1821,6 +1863,7 @@ cwb_status scatter_count_pass(cwb_model* m)
         a.count_rows = idx == 1 ? m->n_tr : m->n;
         a.wait_cycles = kWaitCycles;             // setup work: the default limit
         a.withhold = -1;
+        a.direct = 0;                            // the converter writes the counting pass's ones
         CWB_CUDA_TRY(launch_scatter_args(m, m->stream, a, true));
         const int64_t total = (int64_t)P.clusters * P.nb_cta * P.f_lane;
         const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(4 * num_sms(m->device), (total + 255) / 256));
@@ -2181,6 +2224,10 @@ cwb_status read_device_error(cwb_model* m)
     }
     if (st.err & kErrNonFinite) {
         set_error("non-finite base-learner criterion (diverging fit?)");
+        return CWB_ENUMERIC;
+    }
+    if (st.err & kErrBound) {
+        set_error("a pseudo residual exceeded the bound of its fixed-point scale");
         return CWB_ENUMERIC;
     }
     if (st.err) {

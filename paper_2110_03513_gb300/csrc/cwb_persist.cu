@@ -146,20 +146,6 @@ __device__ __forceinline__ void barrier_wait_release(unsigned* sync, unsigned ge
     }
 }
 
-// Bound on max |w r| of the iteration about to run, known before its row pass: for the L2 loss
-// r changes by nu v_k*[ind] under the pending update, so |w r| <= max |w r_prev| + nu max(w)
-// max |v_k*| (times 1 + 2^-12 for the roundings of the compensated update); for the binomial
-// loss |y - sigmoid(f)| < 1, so |w r| < max(w).
-__device__ __forceinline__ uint32_t residual_bound(int loss, bool pending, uint32_t rprev_bits, float vmax_sel,
-                                                   float nu, float wmax)
-{
-    float b;
-    if (loss == CWB_LOSS_BINOMIAL) b = wmax;
-    else b = __uint_as_float(rprev_bits) + (pending ? nu * wmax * vmax_sel : 0.0f);
-    b = b * (1.0f + 1.0f / 4096.0f);
-    return __float_as_uint(b);
-}
-
 template <typename IndT>
 __device__ __forceinline__ void lds_ind4(const unsigned char* p, int out[4]);
 template <>
@@ -731,6 +717,37 @@ using EncodeTiledFnP = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_
 // beside a ring of at least three stages; sets m->persist_ok.  Allocates its buffers (the second
 // f buffer, the exact sums, the barrier words) and runs the counting pass for the fixed-point
 // scale.
+// The inputs of residual_bound known at creation: the largest weight (m->wmax) and, before the
+// first iteration, max |w r| of the residuals at the offset (the state's rprev_bits).
+cwb_status init_residual_bound(cwb_model* m)
+{
+    cudaStream_t s = m->stream;
+    const int sms = num_sms_p(m->device);
+    uint32_t* mx = nullptr;
+    CWB_TRY(dev_alloc((void**)&mx, sizeof(uint32_t) * 2, s));
+    uint32_t mx_h[2] = {0u, 0u};
+    DevState st;
+    cudaError_t e = cudaMemsetAsync(mx, 0, sizeof(uint32_t) * 2, s);
+    if (e == cudaSuccess) {
+        k_init_rmax<<<std::max(1, std::min(4 * sms, (int)((m->n + 255) / 256))), 256, 0, s>>>(
+            m->n, m->cfg.loss, m->y, m->y_lo, m->w, m->f, mx);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(mx_h, mx, sizeof(mx_h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&st, m->state, sizeof(st), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    dev_free(mx);
+    if (e != cudaSuccess) return cuda_status(e, "residual bound at creation");
+    float wmax_f = 1.0f;
+    std::memcpy(&wmax_f, &mx_h[1], sizeof(float));
+    m->wmax = wmax_f > 0.0f ? wmax_f : 1.0f;
+    if (st.m == 0 && st.rprev_bits == 0u) {
+        CWB_CUDA_TRY(cudaMemcpyAsync(&m->state->rprev_bits, &mx_h[0], sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+        CWB_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    return CWB_OK;
+}
+
 cwb_status plan_persistent(cwb_model* m)
 {
     m->persist_ok = false;
@@ -825,22 +842,10 @@ cwb_status plan_persistent(cwb_model* m)
         k_pcount<uint16_t><<<sms, 512, csm, s>>>((const uint16_t*)m->ind, m->n, m->n_pad, m->B, P.FE, P.G, P.per_group,
                                                 P.tiles, P.nb, m->state);
     k_pcount_log2<<<1, 32, 0, s>>>(m->state);
-    // residual maximum at the current model and the largest weight
-    uint32_t* mx = reinterpret_cast<uint32_t*>(m->gbar);
-    CWB_CUDA_TRY(cudaMemsetAsync(mx, 0, sizeof(uint32_t) * 2, s));
-    k_init_rmax<<<std::max(1, std::min(4 * sms, (int)((m->n + 255) / 256))), 256, 0, s>>>(m->n, m->cfg.loss, m->y, m->y_lo,
-                                                                                            m->w, m->f, mx);
-    CWB_CUDA_TRY(cudaGetLastError());
-    uint32_t mx_h[2] = {0u, 0u};
-    CWB_CUDA_TRY(cudaMemcpyAsync(mx_h, mx, sizeof(mx_h), cudaMemcpyDeviceToHost, s));
+    CWB_TRY(init_residual_bound(m));
     DevState st;
     CWB_CUDA_TRY(cudaMemcpyAsync(&st, m->state, sizeof(st), cudaMemcpyDeviceToHost, s));
     CWB_CUDA_TRY(cudaStreamSynchronize(s));
-    float wmax_f = 1.0f;
-    std::memcpy(&wmax_f, &mx_h[1], sizeof(float));
-    m->wmax = wmax_f > 0.0f ? wmax_f : 1.0f;
-    if (st.m == 0 && st.rprev_bits == 0u)
-        CWB_CUDA_TRY(cudaMemcpyAsync(&m->state->rprev_bits, &mx_h[0], sizeof(uint32_t), cudaMemcpyHostToDevice, s));
     if (st.cnt_log2p > 13) return CWB_OK;   // heavily skewed bins: the kernel path (FP32 fallback) handles them
     m->pplan = P;
     m->persist_ok = true;
