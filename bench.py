@@ -51,17 +51,22 @@ WORKLOAD = ("binned CWB, L2 loss, n=1,000,000, p=50 U[0,1] FP32 features (10 inf
 
 # DRAM traffic of one scatter launch from the committed ncu capture, valid for the
 # scatter kernel source with this SHA-256 prefix (null once the kernel changes).
-SCATTER_TRAFFIC = {"sha256": "b0668182fc5739b1", "bytes": 104056320 + 3544320}   # one ncu capture of this kernel
+SCATTER_TRAFFIC = {"sha256": "b9d9873e32a1d806", "bytes": 104057344 + 3549184}   # one ncu capture of this kernel
 # the same kernel on the HCWB workload (ACWB phase: 200 binnings x 1.6M training rows, two channels)
-HCWB_SCATTER_TRAFFIC = {"sha256": "b0668182fc5739b1", "bytes": 663282688 + 3199744}
+HCWB_SCATTER_TRAFFIC = {"sha256": "b9d9873e32a1d806", "bytes": 663280896 + 3408640}
 
 
 def scatter_source_hash() -> str:
-    path = os.path.join(ROOT, "paper_2110_03513_gb300", "csrc", "cwb_iter.cu")
-    text = open(path).read()
+    """Hash of the scatter kernel's source and of the device helpers it uses (a recorded ncu traffic
+    figure is reported only while both are unchanged)."""
+    csrc = os.path.join(ROOT, "paper_2110_03513_gb300", "csrc")
+    text = open(os.path.join(csrc, "cwb_iter.cu")).read()
     start = text.find("// binMatVec scatter")
     end = text.find("// Per-learner fit, criterion and argmin")
-    return hashlib.sha256(text[start:end].encode()).hexdigest()[:16]
+    helpers = open(os.path.join(csrc, "cwb_device.cuh")).read()
+    # comments and blank lines do not change the kernel
+    code = [ln.split("//", 1)[0].rstrip() for ln in (text[start:end] + helpers).splitlines()]
+    return hashlib.sha256("\n".join(ln for ln in code if ln).encode()).hexdigest()[:16]
 
 
 def measured_peaks():

@@ -291,6 +291,9 @@ cwb_status cwb_get_residuals(const cwb_model* m, int32_t channel, float* out);
  * pending update's largest step; max w for the binomial loss), so the scatter
  * needs no conversion step.  CWB_DIRECT_Q=0, read when a model is created, keeps
  * the conversion inside the scatter (scale from the measured maximum) instead.
+ * The scatter's ring waits sleep with a suspend-time hint when its ring has six or
+ * more stages; CWB_SLEEP_WAITS=1 or 0, read when a model is created, forces the
+ * hint on or off.
  */
 cwb_status cwb_get_scatter_plan(const cwb_model* m, int32_t* values, int32_t cap);
 

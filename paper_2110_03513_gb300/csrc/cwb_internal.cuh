@@ -221,6 +221,7 @@ struct cwb_model {
     float* vmax = nullptr;                // [K] max |v_k| of the latest update tables
     double wmax = 1.0;                    // largest observation weight
     bool direct_enabled = true;           // CWB_DIRECT_Q=0 turns the direct fixed-point residuals off
+    int sleep_waits = -1;                 // CWB_SLEEP_WAITS: 1 / 0 forces the scatter's suspend-time hint on / off
     long long wait_cycles = 4000000000LL; // limit of each device-side ring wait (SM clocks, ~2 s)
     int l2_keep = 0;                      // scatter copies with L2 hints: the index kept, the residual rows streamed
     int withhold_tile = -1;               // test hook (CWB_WITHHOLD_TILE): a scatter tile whose copies are never issued

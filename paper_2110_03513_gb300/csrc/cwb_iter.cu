@@ -476,6 +476,7 @@ struct ScatterArgs {
     int withhold;                  // test hook: >= 0 makes CTA 0 arm, but never fill, its tile min(withhold, ntiles - 1)
     int l2_keep;                   // 1: index boxes with the evict-last hint, residual rows with evict-first
     int direct;                    // 1: the residual rows are already int32 fixed point (no conversion step)
+    int sleep_waits;               // 1: ring waits sleep with a suspend-time hint (deep rings)
 };
 
 constexpr int kEpiVec = 4;                         // 16-byte vectors per thread and pass of the cluster epilogue
@@ -589,7 +590,7 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
                     s = 0;
                     ph ^= 1u;
                 }
-                if (it >= a.stages && !mbar_wait(&empty[s], ph ^ 1u, deadline)) {
+                if (it >= a.stages && !mbar_wait(&empty[s], ph ^ 1u, deadline, a.sleep_waits)) {
                     ok = false;
                     break;
                 }
@@ -628,7 +629,7 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
                 s = 0;
                 ph ^= 1u;
             }
-            if (!__all_sync(0xffffffffu, mbar_wait(&full[s], ph, deadline))) {
+            if (!__all_sync(0xffffffffu, mbar_wait(&full[s], ph, deadline, a.sleep_waits))) {
                 if (lane == 0) atomicOr(a.err, kErrTimeout);
                 break;
             }
@@ -681,7 +682,7 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
                 ph ^= 1u;
             }
             // (without a conversion step the stage is ready as soon as its copies have landed)
-            if (!__all_sync(0xffffffffu, mbar_wait(a.direct ? &full[s] : &ready[s], ph, deadline))) {
+            if (!__all_sync(0xffffffffu, mbar_wait(a.direct ? &full[s] : &ready[s], ph, deadline, a.sleep_waits))) {
                 if (lane == 0) atomicOr(a.err, kErrTimeout);
                 break;
             }
@@ -1429,6 +1430,8 @@ cudaError_t launch_scatter_t(cwb_model* m, cudaStream_t s, const ScatterArgs& a)
     return cudaLaunchKernelEx(&cfg, k_scatter<IndT, CMAX, INT_ACC, false, -1>, m->tmap, a);
 }
 
+constexpr int kSleepStages = 6;                    // rings at least this deep wait with a suspend-time hint
+
 ScatterArgs scatter_args(cwb_model* m)
 {
     const ScatterPlan& P = m->plan;
@@ -1468,6 +1471,7 @@ ScatterArgs scatter_args(cwb_model* m)
     a.withhold = m->withhold_tile;
     a.l2_keep = m->l2_keep;
     a.direct = direct_q(m) ? 1 : 0;
+    a.sleep_waits = m->sleep_waits >= 0 ? m->sleep_waits : (P.stages >= kSleepStages ? 1 : 0);
     return a;
 }
 
