@@ -690,52 +690,61 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
             const Acc* r_st =
                 reinterpret_cast<const Acc*>(smem + (INT_ACC ? a.q_off : a.r_off) + (size_t)s * a.stage_r_bytes) +
                 ch * kStageRows;
-            if (active) {
+            bool released = false;
 #pragma unroll 1
-                for (int u0 = warp * step; u0 < nunits; u0 += W * step) {
-                    uint4 raw[UN];
-                    Acc rv[UN][U];
-                    bool live[UN];
+            for (int u0 = warp * step; u0 < nunits; u0 += W * step) {      // warp-uniform bounds
+                uint4 raw[UN];
+                Acc rv[UN][U];
+                bool live[UN];
 #pragma unroll
-                    for (int k = 0; k < UN; ++k) {
-                        // the lanes of a row set read the same logical 16-byte unit (8 or 16 rows) of
-                        // their binnings: the residuals are one broadcast, and the 128-byte swizzle
-                        // of the TMA box spreads the index reads over all banks.  Unit u of binning
-                        // f sits in 128-byte row R = (u / 8) FE + f at 16-byte slot (u % 8) ^ (R % 8).
-                        const int pos = u0 + k * RS + rs;
-                        live[k] = pos < nunits;
-                        const int R = (pos >> 3) * FE + f;
-                        raw[k] = *reinterpret_cast<const uint4*>(ind_st + R * 128 + (((pos & 7) ^ (R & 7)) << 4));
+                for (int k = 0; k < UN; ++k) {
+                    // the lanes of a row set read the same logical 16-byte unit (8 or 16 rows) of
+                    // their binnings: the residuals are one broadcast, and the 128-byte swizzle
+                    // of the TMA box spreads the index reads over all banks.  Unit u of binning
+                    // f sits in 128-byte row R = (u / 8) FE + f at 16-byte slot (u % 8) ^ (R % 8).
+                    const int pos = u0 + k * RS + rs;
+                    live[k] = active && pos < nunits;
+                    if (!active) continue;
+                    const int R = (pos >> 3) * FE + f;
+                    raw[k] = *reinterpret_cast<const uint4*>(ind_st + R * 128 + (((pos & 7) ^ (R & 7)) << 4));
 #pragma unroll
-                        for (int t4 = 0; t4 < U / 4; ++t4) {
-                            if (INT_ACC) {
-                                const int4 r4 = reinterpret_cast<const int4*>(r_st + pos * U)[t4];
-                                rv[k][4 * t4] = r4.x; rv[k][4 * t4 + 1] = r4.y; rv[k][4 * t4 + 2] = r4.z; rv[k][4 * t4 + 3] = r4.w;
-                            } else {
-                                const float4 r4 = reinterpret_cast<const float4*>(r_st + pos * U)[t4];
-                                rv[k][4 * t4] = r4.x; rv[k][4 * t4 + 1] = r4.y; rv[k][4 * t4 + 2] = r4.z; rv[k][4 * t4 + 3] = r4.w;
-                            }
+                    for (int t4 = 0; t4 < U / 4; ++t4) {
+                        if (INT_ACC) {
+                            const int4 r4 = reinterpret_cast<const int4*>(r_st + pos * U)[t4];
+                            rv[k][4 * t4] = r4.x; rv[k][4 * t4 + 1] = r4.y; rv[k][4 * t4 + 2] = r4.z; rv[k][4 * t4 + 3] = r4.w;
+                        } else {
+                            const float4 r4 = reinterpret_cast<const float4*>(r_st + pos * U)[t4];
+                            rv[k][4 * t4] = r4.x; rv[k][4 * t4 + 1] = r4.y; rv[k][4 * t4 + 2] = r4.z; rv[k][4 * t4 + 3] = r4.w;
                         }
                     }
+                }
+                if (u0 + W * step >= nunits) {
+                    // the stage is free once the warp's last values of it are in registers: hand it
+                    // back to the loader before the atomics (the arrive orders the loads before it)
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&empty[s]);
+                    released = true;
+                }
 #pragma unroll
-                    for (int k = 0; k < UN; ++k) {
-                        if (!live[k]) continue;
-                        int idx[U];
-                        unpack16<IndT>(raw[k], idx);
+                for (int k = 0; k < UN; ++k) {
+                    if (!live[k]) continue;
+                    int idx[U];
+                    unpack16<IndT>(raw[k], idx);
 #pragma unroll
-                        for (int t = 0; t < U; ++t) {
-                            if (RANGED) {
-                                const unsigned bl = (unsigned)(idx[t] - b_lo);
-                                if (bl < (unsigned)a.nb_cta) atomicAdd(hf + (bl << fsh), rv[k][t]);
-                            } else {
-                                atomicAdd(hf + (idx[t] << fsh), rv[k][t]);
-                            }
+                    for (int t = 0; t < U; ++t) {
+                        if (RANGED) {
+                            const unsigned bl = (unsigned)(idx[t] - b_lo);
+                            if (bl < (unsigned)a.nb_cta) atomicAdd(hf + (bl << fsh), rv[k][t]);
+                        } else {
+                            atomicAdd(hf + (idx[t] << fsh), rv[k][t]);
                         }
                     }
                 }
             }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[s]);
+            if (!released) {
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[s]);
+            }
         }
     }
     grid_dep_launch();                 // the solve may be scheduled as SMs free up
