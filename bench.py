@@ -51,9 +51,9 @@ WORKLOAD = ("binned CWB, L2 loss, n=1,000,000, p=50 U[0,1] FP32 features (10 inf
 
 # DRAM traffic of one scatter launch from the committed ncu capture, valid for the
 # scatter kernel source with this SHA-256 prefix (null once the kernel changes).
-SCATTER_TRAFFIC = {"sha256": "b9d9873e32a1d806", "bytes": 104057344 + 3549184}   # one ncu capture of this kernel
+SCATTER_TRAFFIC = {"sha256": "d96b109e3f2e370e", "bytes": 104067584 + 3252736}   # one ncu capture of this kernel
 # the same kernel on the HCWB workload (ACWB phase: 200 binnings x 1.6M training rows, two channels)
-HCWB_SCATTER_TRAFFIC = {"sha256": "b9d9873e32a1d806", "bytes": 663280896 + 3408640}
+HCWB_SCATTER_TRAFFIC = {"sha256": "d96b109e3f2e370e", "bytes": 663209728 + 3176704}
 
 
 def scatter_source_hash() -> str:
