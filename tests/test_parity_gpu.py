@@ -337,6 +337,45 @@ def test_resumed_fit_equals_single_fit(cwb):
     assert rel_err(a.fitted(), ref.f) <= REL_TOL
 
 
+def test_fit_resumes_after_reading_fitted_values(cwb):
+    """Reading the fitted values applies the last update without forming residuals; the next row
+    pass must still take a valid fixed-point scale (the bound grows by that update), for the L2 and
+    the binomial loss, with and without observation weights."""
+    for loss, w_on in [(0, False), (0, True), (1, False)]:
+        data = S.additive_regression(20_000, 5, 4, seed=41 + loss, dtype=np.float32)
+        y = data.y if loss == 0 else (data.eta > np.median(data.eta)).astype(np.float32)
+        w = np.random.default_rng(5).uniform(0.5, 2.0, size=data.n) if w_on else None
+        specs = [dict(feature=j, n_bins=-1) for j in range(5)]
+        a = cwb.Model(data.X, y, _specs_to_gpu(cwb, specs), loss=loss, w=w, iterations=60, device=0)
+        for chunk in (7, 13, 20, 20):
+            a.fit(chunk)
+            a.fitted()
+            a.all_coefficients(0)
+        ref = O.fit(data.X.astype(np.float64), y.astype(np.float64), specs, loss=loss, w=w, iterations=60)
+        k_sel, _, _ = a.trace()
+        if check_sequences(k_sel, ref) < 0:
+            check_coefficients(a.all_coefficients(0, dmax=ref.dmax), ref.theta_f)
+            assert rel_err(a.fitted(), ref.f) <= REL_TOL
+        a.free()
+
+
+@pytest.mark.parametrize("direct", ["1", "0"])
+def test_residual_getter_matches_oracle(cwb, monkeypatch, direct):
+    """cwb_get_residuals returns w r of the last iteration: with the row pass writing fixed point
+    (the default for plain CWB) and with the conversion inside the scatter (CWB_DIRECT_Q=0), it equals
+    the oracle's y - f after M - 1 iterations; the fit itself matches the oracle either way."""
+    monkeypatch.setenv("CWB_DIRECT_Q", direct)
+    data = S.additive_regression(30_001, 6, 4, seed=43, dtype=np.float32)
+    specs = [dict(feature=j, n_bins=-1) for j in range(6)]
+    M = 25
+    model, ref = run_pair(cwb, data.X, data.y, specs, M=M, check_predict=False)
+    r = model.residuals(0)
+    prev = O.fit(data.X.astype(np.float64), data.y.astype(np.float64), specs, iterations=M - 1)
+    r_ref = data.y.astype(np.float64) - prev.f
+    assert rel_err(r, r_ref) <= REL_TOL, rel_err(r, r_ref)
+    model.free()
+
+
 # ------------------------------------------------------------------ ACWB / HCWB
 
 def test_acwb_l2(cwb):
