@@ -876,7 +876,10 @@ __global__ void k_partials_to_u(const int* __restrict__ part, const int32_t* __r
 // so that two solve CTAs share an SM: fits that run side by side (batches, the server) are bound by
 // the solve's SM occupancy, not its latency.  A pass covers 2 x threads bins (kSolveChunk).
 __host__ __device__ constexpr int solve_chunk(int threads) { return 2 * threads; }
-constexpr int kSolveBatch = 20;        // partial-histogram rows per thread and batch (per channel)
+// partial-histogram rows per thread and batch (per channel): 20 for the 512-thread solve of large
+// models (many clusters per slot); the 256-thread solve of small models (few clusters) takes 8, which
+// keeps it within its 128 registers (20 spilled there)
+__host__ __device__ constexpr int solve_batch(int threads) { return threads >= 512 ? 20 : 8; }
 
 struct SolveArgs {
     DevState* state;
@@ -928,6 +931,7 @@ template <bool INT_ACC, int kSolveThreads>
 __global__ void __launch_bounds__(kSolveThreads, 512 / kSolveThreads) k_solve(SolveArgs a)
 {
     constexpr int kSolveChunk = solve_chunk(kSolveThreads);
+    constexpr int kSolveBatch = solve_batch(kSolveThreads);
     constexpr int NW = kSolveThreads / 32;
     constexpr int kColsPerWarp = (kMaxD + NW - 1) / NW;
     const int k = blockIdx.x;
