@@ -1042,7 +1042,16 @@ __global__ void __launch_bounds__(kSolveThreads, 512 / kSolveThreads) k_solve(So
         const int L1 = min(nst, L0 + kSolveChunk);
         const bool mine = 4 * gi < L1 - L0;
         int c0 = c0n, c1 = c1n, lb = lbn;
-        if (L0 > 0) chunk_clusters(L0, L1, c0, c1, lb);
+        if (L0 > 0) {
+            if (a.bin_ranges == 1) {
+                // one bin range: every chunk's bins lie in the slot of chunk 0 (no table lookup)
+                c0 = mine ? c0n : 0;
+                c1 = mine ? c1n : 0;
+                lb = mine ? L0 + 4 * gi : 0;
+            } else {
+                chunk_clusters(L0, L1, c0, c1, lb);
+            }
+        }
         long long it0[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
         if (a.u64) {
             // row shards: the exchanged exact sums of every shard's histograms stand for the partials
