@@ -168,12 +168,23 @@ __global__ void k_minmax_final(const double* __restrict__ pmin, const double* __
 // when no integer lies within 4e-7 |t| + 1e-6 of t - 1/2 (the interval is evaluated in
 // FP32, whose own roundings the margin also covers) the FP32 and FP64 rules agree;
 // only values that close to a half-way point take the FP64 path.
+// One equidistant binning of the fit: its feature, range and design-point count.
+struct BinJob {
+    int64_t feature;
+    double xmin, h;
+    int32_t nstar, binning;
+};
+
+// Every equidistant binning of a fit in one launch (blockIdx.y = job).
 template <typename T, typename IndT>
-__global__ void k_bin_equidistant(const T* __restrict__ X, int64_t feat, const int32_t* __restrict__ perm,
-                                  int64_t n, int64_t n_pad, double xmin, double h, int nstar,
-                                  IndT* __restrict__ out)
+__global__ void k_bin_equidistant(const T* __restrict__ X, const BinJob* __restrict__ jobs,
+                                  const int32_t* __restrict__ perm, int64_t n, int64_t n_pad, IndT* __restrict__ ind)
 {
-    const T* x = X + feat * n;
+    const BinJob jb = jobs[blockIdx.y];
+    const T* x = X + jb.feature * n;
+    const double xmin = jb.xmin, h = jb.h;
+    const int nstar = jb.nstar;
+    IndT* out = ind + (int64_t)jb.binning * n_pad;
     const float inv_h = (float)(1.0 / h);
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n_pad; q += (int64_t)gridDim.x * blockDim.x) {
         int l = 0;
@@ -1215,6 +1226,7 @@ cwb_status setup_model(cwb_model* m, const void* X_in, int x_dtype, const void* 
     // --- index vectors [B][n_pad]
     CWB_TRY(dev_alloc(&m->ind, (size_t)m->ind_bytes * B * n_pad, s));
     std::vector<double> h_h(B, 0.0);
+    std::vector<BinJob> jobs_h;
     for (int b = 0; b < B; ++b) {
         const HostBinning& hb = m->bins[b];
         if (hb.exact) {
@@ -1229,17 +1241,24 @@ cwb_status setup_model(cwb_model* m, const void* X_in, int x_dtype, const void* 
                 else k_bin_exact<<<g_rows, kThreads, 0, s>>>((const float*)Xd, hb.feature, m->perm, n, n_pad, zvals[b], hb.nstar, out, errp);
             }
         } else {
-            double h = (hb.xmax - hb.xmin) / (double)(hb.nstar - 1);
+            const double h = (hb.xmax - hb.xmin) / (double)(hb.nstar - 1);
             h_h[b] = h;
-            if (m->ind_bytes == 1) {
-                uint8_t* out = (uint8_t*)m->ind + (int64_t)b * n_pad;
-                if (x_dtype == CWB_F64) k_bin_equidistant<<<g_rows, kThreads, 0, s>>>((const double*)Xd, hb.feature, m->perm, n, n_pad, hb.xmin, h, hb.nstar, out);
-                else k_bin_equidistant<<<g_rows, kThreads, 0, s>>>((const float*)Xd, hb.feature, m->perm, n, n_pad, hb.xmin, h, hb.nstar, out);
-            } else {
-                uint16_t* out = (uint16_t*)m->ind + (int64_t)b * n_pad;
-                if (x_dtype == CWB_F64) k_bin_equidistant<<<g_rows, kThreads, 0, s>>>((const double*)Xd, hb.feature, m->perm, n, n_pad, hb.xmin, h, hb.nstar, out);
-                else k_bin_equidistant<<<g_rows, kThreads, 0, s>>>((const float*)Xd, hb.feature, m->perm, n, n_pad, hb.xmin, h, hb.nstar, out);
-            }
+            jobs_h.push_back(BinJob{(int64_t)hb.feature, hb.xmin, h, hb.nstar, b});
+        }
+    }
+    if (!jobs_h.empty()) {
+        // all equidistant binnings in one launch, the rows of each spread over a share of the grid
+        BinJob* jobs = nullptr;
+        CWB_TRY(tmp.get(&jobs, jobs_h.size(), s));
+        CWB_CUDA_TRY(cudaMemcpyAsync(jobs, jobs_h.data(), sizeof(BinJob) * jobs_h.size(), cudaMemcpyHostToDevice, s));
+        const int nj = (int)jobs_h.size();
+        const dim3 grid((unsigned)std::max(1, std::min(g_rows, (4 * num_sms(m->device) + nj - 1) / nj)), (unsigned)nj);
+        if (m->ind_bytes == 1) {
+            if (x_dtype == CWB_F64) k_bin_equidistant<<<grid, kThreads, 0, s>>>((const double*)Xd, jobs, m->perm, n, n_pad, (uint8_t*)m->ind);
+            else k_bin_equidistant<<<grid, kThreads, 0, s>>>((const float*)Xd, jobs, m->perm, n, n_pad, (uint8_t*)m->ind);
+        } else {
+            if (x_dtype == CWB_F64) k_bin_equidistant<<<grid, kThreads, 0, s>>>((const double*)Xd, jobs, m->perm, n, n_pad, (uint16_t*)m->ind);
+            else k_bin_equidistant<<<grid, kThreads, 0, s>>>((const float*)Xd, jobs, m->perm, n, n_pad, (uint16_t*)m->ind);
         }
     }
     CWB_CUDA_TRY(cudaGetLastError());

@@ -47,3 +47,41 @@ def test_quarter_root_bins_are_too_coarse_at_high_snr(rows, n):
 def test_momentum_stops_earlier(rows, n, snr):
     """H3: ACWB with momentum reaches its early-stopping optimum in far fewer iterations."""
     assert 2 * _get(rows, n, snr, "sqrt ACWB gamma 0.1")["stop_iter"] <= _get(rows, n, snr, "sqrt df5")["stop_iter"]
+
+
+@pytest.mark.parametrize("variant", ["exact", "sqrt", "acwb"])
+def test_mise_figure_matches_the_oracle_fit(variant):
+    """The MISE of a GPU fit equals the MISE of the FP64 oracle's fit of the same data and iterations
+    (Sec. 4.1.1's measure through the same partial-effect code): the harness's figures are those of the
+    method, not of the implementation."""
+    import math
+    import numpy as np
+    import __graft_entry__ as g
+    g.build()
+    import paper_2110_03513_gb300 as cwb
+    import bench
+    import synthetic_inputs as S
+    from oracle import oracle as O
+    data = S.paper_style_simulation(4_000, 5, 5, 10.0, seed=23)
+    p = data.X.shape[0]
+    nb = cwb.BINS_EXACT if variant == "exact" else math.isqrt(data.n)
+    opt = cwb.OPT_ACWB if variant == "acwb" else cwb.OPT_CWB
+    M = 300
+    specs = [dict(feature=j, n_bins=nb, df=5.0) for j in range(p)]
+    model = cwb.Model(np.ascontiguousarray(data.X), data.y, [cwb.learner(j, n_bins=nb, df=5.0) for j in range(p)],
+                      opt=opt, nu=0.05, gamma=0.1, iterations=M, device=0)
+    model.fit(M)
+    ref = O.fit(data.X.astype(np.float64), data.y.astype(np.float64), specs, opt=opt, nu=0.05, gamma=0.1,
+                iterations=M)
+    xmin = [float(data.X[j].min()) for j in range(p)]
+    xmax = [float(data.X[j].max()) for j in range(p)]
+
+    class OracleFit:
+        def predict(self, Xg):
+            return O.predict(np.asarray(Xg, dtype=np.float64), specs, xmin, xmax, ref.theta_f, ref.offset)
+
+    m_gpu = bench.partial_effect_mise(model, data)
+    m_ref = bench.partial_effect_mise(OracleFit(), data)
+    model.free()
+    # coefficients agree to ~1e-5 relative; the squared, integrated difference to the truth to ~1e-3
+    assert abs(m_gpu - m_ref) <= 2e-3 * m_ref, (m_gpu, m_ref)
