@@ -806,7 +806,10 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
             }
             __syncthreads();
             const int nbc = c1 - c0;
-            for (int f = warp; f < F; f += (int)(blockDim.x >> 5))          // a warp per binning row
+            // the rows of lanes beyond the group's binnings are never read (the counting pass's
+            // maximum reads every row, so it writes them all)
+            const int f_end = counting ? F : FE;
+            for (int f = warp; f < f_end; f += (int)(blockDim.x >> 5))      // a warp per binning row
                 for (int lb = lane; lb < nbc; lb += 32) dst[(int64_t)f * nb + c0 + lb] = stg[f * (cb + 1) + lb];
             __syncthreads();
         }
