@@ -275,7 +275,8 @@ cwb_status cwb_get_residuals(const cwb_model* m, int32_t channel, float* out);
  * CWB_ITER_MODE below), that kernel's ring stages, CTAs and shared memory bytes.
  * The cluster size is the largest that keeps nearly every SM busy; the
  * environment variable CWB_CLUSTER_SIZE (1, 2, 4, 8 or 16), read when a model is
- * created, overrides it when that size can be resident.
+ * created, overrides it when that size can be resident.  CWB_F_LANE (a power of
+ * two), read likewise, caps the binnings side by side in a warp.
  *
  * CWB_ITER_MODE, read when a model is created: unset or "kernels" runs every
  * iteration as three kernels (pseudo residuals, binMatVec scatter, solve with the

@@ -239,7 +239,6 @@ cwb_status create_impl(const cwb_config* cfg, const void* X, int32_t x_dtype, in
         // copies, so the waits on it run out and the kernel returns CWB_ETIMEOUT
         m->withhold_tile = std::atoi(wt);
     }
-    if (const char* lk = std::getenv("CWB_L2_KEEP")) m->l2_keep = std::atoi(lk) != 0;
     if (const char* dq = std::getenv("CWB_DIRECT_Q")) m->direct_enabled = std::atoi(dq) != 0;
     if (const char* sw = std::getenv("CWB_SLEEP_WAITS")) m->sleep_waits = std::atoi(sw) != 0 ? 1 : 0;
     if (const char* mode = std::getenv("CWB_ITER_MODE")) {

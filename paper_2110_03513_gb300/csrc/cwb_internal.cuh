@@ -223,7 +223,6 @@ struct cwb_model {
     bool direct_enabled = true;           // CWB_DIRECT_Q=0 turns the direct fixed-point residuals off
     int sleep_waits = -1;                 // CWB_SLEEP_WAITS: 1 / 0 forces the scatter's suspend-time hint on / off
     long long wait_cycles = 4000000000LL; // limit of each device-side ring wait (SM clocks, ~2 s)
-    int l2_keep = 0;                      // scatter copies with L2 hints: the index kept, the residual rows streamed
     int withhold_tile = -1;               // test hook (CWB_WITHHOLD_TILE): a scatter tile whose copies are never issued
     // row shards (cwb_shard_*): global binning ranges and row count, exchanged histogram sums
     bool shard = false;

@@ -474,7 +474,6 @@ struct ScatterArgs {
     int64_t count_rows;            // >= 0: counting pass over this many rows (every row adds 1)
     long long wait_cycles;         // limit of each ring wait (SM clocks); copies in flight are drained with kWaitCycles
     int withhold;                  // test hook: >= 0 makes CTA 0 arm, but never fill, its tile min(withhold, ntiles - 1)
-    int l2_keep;                   // 1: index boxes with the evict-last hint, residual rows with evict-first
     int direct;                    // 1: the residual rows are already int32 fixed point (no conversion step)
     int sleep_waits;               // 1: ring waits sleep with a suspend-time hint (deep rings)
 };
@@ -554,16 +553,12 @@ __global__ void __launch_bounds__(kScatterThreads, 1) k_scatter(const __grid_con
             // the first ring's index boxes before the wait (their barriers expect the residual
             // bytes too, which follow once the row pass is complete)
             const int early = fixed_mode ? min(a.stages, ntiles) : 0;
-            const uint64_t pol_keep = policy_evict_last(), pol_once = policy_evict_first();
             auto load_ind = [&](int st, int64_t row0) {
-                void* dst = smem + a.ind_off + (size_t)st * a.stage_ind_bytes;
-                const int z = (int)(row0 / (128 / (int)sizeof(IndT)));
-                if (a.l2_keep) tma_load_3d_hint(dst, &tmap, 0, g * FE, z, &full[st], pol_keep);
-                else tma_load_3d(dst, &tmap, 0, g * FE, z, &full[st]);
+                tma_load_3d(smem + a.ind_off + (size_t)st * a.stage_ind_bytes, &tmap, 0, g * FE,
+                            (int)(row0 / (128 / (int)sizeof(IndT))), &full[st]);
             };
             auto load_r = [&](float* dst, const float* src, uint64_t* bar) {
-                if (a.l2_keep) bulk_load_hint(dst, src, (uint32_t)kStageRows * 4, bar, pol_once);
-                else bulk_load(dst, src, (uint32_t)kStageRows * 4, bar);
+                bulk_load(dst, src, (uint32_t)kStageRows * 4, bar);
             };
             for (int it = 0; it < early; ++it) {
                 const int64_t row0 = (t_lo + it) * kStageRows;
@@ -1494,7 +1489,6 @@ ScatterArgs scatter_args(cwb_model* m)
     a.count_rows = -1;
     a.wait_cycles = m->wait_cycles;
     a.withhold = m->withhold_tile;
-    a.l2_keep = m->l2_keep;
     a.direct = direct_q(m) ? 1 : 0;
     a.sleep_waits = m->sleep_waits >= 0 ? m->sleep_waits : (P.stages >= kSleepStages ? 1 : 0);
     return a;
