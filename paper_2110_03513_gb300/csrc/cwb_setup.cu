@@ -190,12 +190,11 @@ __global__ void k_bin_equidistant(const T* __restrict__ X, const BinJob* __restr
         int l = 0;
         if (q < n) {
             const T xv = x[perm ? perm[q] : q];
-            double dv;
+            double dv = 0.0;
             float d32;
             if (sizeof(T) == 4) {
                 // x and xmin are FP32 values here (xmin is the feature's minimum, or 0 for class
                 // codes): the FP32 difference is the exact difference rounded once
-                dv = __dsub_rn((double)xv, xmin);
                 d32 = (float)xv - (float)xmin;
             } else {
                 dv = __dsub_rn((double)xv, xmin);
@@ -204,11 +203,16 @@ __global__ void k_bin_equidistant(const T* __restrict__ X, const BinJob* __restr
             const float t32 = d32 * inv_h;
             const float e = 4.0e-7f * fabsf(t32) + 1.0e-6f;
             const float c_lo = ceilf(t32 - 0.5f - e), c_hi = ceilf(t32 - 0.5f + e);
-            double c = (double)c_lo;
-            if (c_lo != c_hi || !isfinite(t32)) c = ceil(__dsub_rn(__ddiv_rn(dv, h), 0.5));
-            c = fmax(c, 0.0);
-            c = fmin(c, (double)(nstar - 1));
-            l = (int)c;
+            if (c_lo == c_hi && isfinite(t32)) {
+                // the common case stays on the FP32 pipe (c_lo holds an integer; n* - 1 < 2^24 is exact)
+                l = (int)fminf(fmaxf(c_lo, 0.0f), (float)(nstar - 1));
+            } else {
+                if (sizeof(T) == 4) dv = __dsub_rn((double)xv, xmin);
+                double c = ceil(__dsub_rn(__ddiv_rn(dv, h), 0.5));
+                c = fmax(c, 0.0);
+                c = fmin(c, (double)(nstar - 1));
+                l = (int)c;
+            }
         }
         out[q] = (IndT)l;
     }
@@ -1247,12 +1251,13 @@ cwb_status setup_model(cwb_model* m, const void* X_in, int x_dtype, const void* 
         }
     }
     if (!jobs_h.empty()) {
-        // all equidistant binnings in one launch, the rows of each spread over a share of the grid
+        // all equidistant binnings in one launch: the row grid of one binning, once per binning
+        // (a thread takes a few rows, so the loads of the launch are in flight together)
         BinJob* jobs = nullptr;
         CWB_TRY(tmp.get(&jobs, jobs_h.size(), s));
         CWB_CUDA_TRY(cudaMemcpyAsync(jobs, jobs_h.data(), sizeof(BinJob) * jobs_h.size(), cudaMemcpyHostToDevice, s));
         const int nj = (int)jobs_h.size();
-        const dim3 grid((unsigned)std::max(1, std::min(g_rows, (4 * num_sms(m->device) + nj - 1) / nj)), (unsigned)nj);
+        const dim3 grid((unsigned)g_rows, (unsigned)nj);
         if (m->ind_bytes == 1) {
             if (x_dtype == CWB_F64) k_bin_equidistant<<<grid, kThreads, 0, s>>>((const double*)Xd, jobs, m->perm, n, n_pad, (uint8_t*)m->ind);
             else k_bin_equidistant<<<grid, kThreads, 0, s>>>((const float*)Xd, jobs, m->perm, n, n_pad, (uint8_t*)m->ind);
