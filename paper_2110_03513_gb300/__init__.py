@@ -12,4 +12,4 @@ from .binding import (  # noqa: F401
     cwb_get_profile, cwb_get_residuals, cwb_get_scatter_plan, cwb_last_error, cwb_predict, cwb_predict_noalloc, cwb_profile, cwb_synchronize, learner, library_path, load_library,
     cwb_shard_create, cwb_shard_finish, cwb_shard_rows, cwb_shard_scatter, cwb_shard_sizes, cwb_shard_solve, cwb_shard_stats,
 )
-from .sharded import ShardedFit, split_rows, torch_allreduce  # noqa: F401
+from .sharded import ShardedFit, split_rows, torch_allreduce, torch_allreduce_tensor  # noqa: F401

@@ -9,7 +9,10 @@ row count, the bin counts and the target sum (SUM) and the scatter's bin-count b
 `ShardedFit` drives the shards one process owns (several in one process emulate several GPUs;
 one per process with an `allreduce` across processes, e.g. :func:`torch_allreduce`).  The shard
 operations go through a backend object (default: the CUDA library), so the exchange logic can
-be exercised without a GPU.  Nothing here computes any part of the method.
+be exercised without a GPU.  With `device_exchange=True` the per-iteration buffers stay on the GPU
+(torch CUDA tensors, all work on the current torch stream), so a NCCL all-reduce
+(:func:`torch_allreduce_tensor`) moves them without host copies.  Nothing here computes any part
+of the method.
 """
 from __future__ import annotations
 
@@ -41,16 +44,35 @@ def torch_allreduce(group=None):
     return allreduce
 
 
-class GpuShard:
-    """The CUDA library's row shard (one cwb_shard_* model)."""
+def torch_allreduce_tensor(group=None):
+    """An in-place `allreduce(tensor, op)` of torch tensors over a torch.distributed group (NCCL for
+    CUDA tensors); returns the tensor."""
+    import torch.distributed as dist
+    ops = {"sum": dist.ReduceOp.SUM, "max": dist.ReduceOp.MAX, "min": dist.ReduceOp.MIN}
 
-    def __init__(self, X, y, learners, *, n_global, xmin, xmax, loss, nu, iterations, device):
+    def allreduce(t, op: str):
+        dist.all_reduce(t, op=ops[op], group=group)
+        return t
+    return allreduce
+
+
+class GpuShard:
+    """The CUDA library's row shard (one cwb_shard_* model).  With `device_exchange` the model runs on
+    the current torch stream and rows / scatter / solve take and return CUDA tensors."""
+
+    def __init__(self, X, y, learners, *, n_global, xmin, xmax, loss, nu, iterations, device,
+                 device_exchange=False):
         X = np.ascontiguousarray(X)
         y = np.ascontiguousarray(y, dtype=X.dtype)
         self.p, self.n = int(X.shape[0]), int(X.shape[1])
         self.learners = list(learners)
+        self.device_exchange = device_exchange
+        stream = None
+        if device_exchange:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
         cfg = _b.cwb_config(loss=loss, opt=_b.OPT_CWB, nu=nu, gamma=0.0, iterations=iterations, patience=0,
-                            val_mask=None, stream=None, device=device)
+                            val_mask=None, stream=stream, device=device)
         self.handle = _b.cwb_shard_create(cfg, X, _b._dtype_code(X), self.n, self.p, y, self.learners, 0, n_global,
                                           xmin, xmax)
         self.B, self.S = _b.cwb_shard_sizes(self.handle)
@@ -66,18 +88,31 @@ class GpuShard:
         _b.cwb_shard_finish(self.handle, np.ascontiguousarray(counts, dtype=np.float64),
                             np.ascontiguousarray(sums, dtype=np.float64), int(cnt_log2))
 
-    def rows(self) -> float:
+    def rows(self):
+        if self.device_exchange:
+            import torch
+            r = torch.zeros(1, dtype=torch.float32, device="cuda")
+            _b.cwb_shard_rows(self.handle, r, 1)
+            return r
         r = np.zeros(1, dtype=np.float32)
         _b.cwb_shard_rows(self.handle, r, 0)
         return float(r[0])
 
-    def scatter(self, rmax: float) -> np.ndarray:
+    def scatter(self, rmax):
+        if self.device_exchange:
+            import torch
+            u = torch.empty(self.B * self.S, dtype=torch.int64, device="cuda")
+            _b.cwb_shard_scatter(self.handle, rmax, u, 1)
+            return u
         r = np.array([rmax], dtype=np.float32)
         u = np.zeros(self.B * self.S, dtype=np.int64)
         _b.cwb_shard_scatter(self.handle, r, u, 0)
         return u
 
-    def solve(self, u: np.ndarray):
+    def solve(self, u):
+        if self.device_exchange:
+            _b.cwb_shard_solve(self.handle, u.contiguous(), 1)
+            return
         _b.cwb_shard_solve(self.handle, np.ascontiguousarray(u, dtype=np.int64), 0)
 
     def free(self):
@@ -92,8 +127,9 @@ class ShardedFit:
     """
 
     def __init__(self, parts, learners, *, loss=_b.LOSS_L2, nu=0.1, iterations=100, device=0, allreduce=None,
-                 backend=GpuShard):
+                 backend=GpuShard, device_exchange=False):
         self.allreduce = allreduce
+        self.device_exchange = device_exchange
         X0 = np.asarray(parts[0][0])
         p = X0.shape[0] if X0.ndim > 1 else 1
         mins = np.min([np.asarray(X).reshape(p, -1).min(axis=1) for X, _ in parts], axis=0).astype(np.float64)
@@ -102,8 +138,9 @@ class ShardedFit:
         self.xmin = self._reduce(mins, "min")
         self.xmax = self._reduce(maxs, "max")
         self.n_global = int(self._reduce(n_local, "sum")[0])
+        kw = {"device_exchange": True} if device_exchange else {}
         self.shards = [backend(X, y, learners, n_global=self.n_global, xmin=self.xmin, xmax=self.xmax, loss=loss,
-                               nu=nu, iterations=iterations, device=device) for X, y in parts]
+                               nu=nu, iterations=iterations, device=device, **kw) for X, y in parts]
         # setup exchange: bin counts and target sums (SUM), the scatter's bin-count bound (MAX)
         st = [s.stats() for s in self.shards]
         counts = self._reduce(self._local(np.stack([c for c, _, _ in st]), "sum"), "sum")
@@ -121,6 +158,16 @@ class ShardedFit:
 
     def step(self):
         """One iteration: rows -> MAX of |r| -> scatter -> SUM of the histograms -> solve."""
+        if self.device_exchange:
+            import torch
+            rmax = torch.stack([s.rows() for s in self.shards]).amax(dim=0)          # [1] float32 on the GPU
+            rmax = self._reduce(rmax, "max")
+            u = torch.stack([s.scatter(rmax) for s in self.shards]).sum(dim=0)      # exact int64 sums
+            u = self._reduce(u, "sum")
+            for s in self.shards:
+                s.solve(u)
+            self.iterations_done += 1
+            return
         rmax = np.array([max(s.rows() for s in self.shards)], dtype=np.float32)
         rmax = self._reduce(rmax, "max")
         u = self._local(np.stack([s.scatter(float(rmax[0])) for s in self.shards]), "sum")

@@ -90,3 +90,23 @@ def test_shard_rejects_rows_outside_the_global_range_and_cwb_fit(cwb):
     with pytest.raises(cwb.CwbError):
         m.fit(3)
     m.free()
+
+
+def test_device_exchange_equals_host_exchange(cwb):
+    """The exchange through device buffers (CUDA tensors on the current stream, what a NCCL all-reduce
+    moves) gives the same fit as the exchange through host arrays, bit for bit."""
+    M = 30
+    data = S.additive_regression(50_001, 4, 3, seed=37, dtype=np.float32)
+    specs = [dict(feature=j, n_bins=-1) for j in range(4)]
+    parts = [(data.X[:, a:b], data.y[a:b]) for a, b in cwb.split_rows(data.n, 2)]
+    fits = []
+    for dev in (False, True):
+        fit = cwb.ShardedFit(parts, _gpu_specs(cwb, specs), nu=0.1, iterations=M, device_exchange=dev)
+        fit.fit(M)
+        fits.append(fit)
+    for a, b in zip(fits[0].shards, fits[1].shards):
+        np.testing.assert_array_equal(a.model.trace()[0], b.model.trace()[0])
+        np.testing.assert_array_equal(a.model.all_coefficients(0), b.model.all_coefficients(0))
+        np.testing.assert_array_equal(a.model.fitted(), b.model.fitted())
+    for f in fits:
+        f.free()
