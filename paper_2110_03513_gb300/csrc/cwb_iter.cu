@@ -116,7 +116,7 @@ __device__ __forceinline__ void load_row_in(const RowArgs& a, int64_t i4, RowIn&
 // before the iteration state is read, so a pass costs about one memory round trip.  One group
 // for every model: plain CWB models with two groups per thread (half the threads) ran 4 % slower
 // per iteration at n = 1M, with four 20 % slower.
-__host__ __device__ constexpr int row_groups(bool acc) { return acc ? 1 : 1; }
+__host__ __device__ constexpr int row_groups(bool) { return 1; }
 
 // ACC: the model runs accelerated iterations (ACWB / HCWB); plain CWB models compile without
 // the momentum sequence, the error-corrected residual and their loads.
