@@ -452,13 +452,21 @@ def run_batched(cwb, args):
     import synthetic_inputs as S
     M = 1000
     specs = S.batched_fit_specs(count=512)[: max(1, args.batched_fits)]
-    seq_models, bat_models = [], []
-    for sp in specs:
-        d = S.request_dataset(sp)
-        lrn = [cwb.learner(j, n_bins=-1, df=sp["df"]) for j in range(sp["p"])]
-        seq_models.append(cwb.Model(d.X, d.y, lrn, nu=sp["nu"], iterations=M, device=0))
-        bat_models.append(cwb.Model(d.X, d.y, lrn, nu=sp["nu"], iterations=M, device=0))
+    datasets = [S.request_dataset(sp) for sp in specs]
+    learner_sets = [[cwb.learner(j, n_bins=-1, df=sp["df"]) for j in range(sp["p"])] for sp in specs]
+    # setup of every fit: one create after another, and all at once (cwb_create_many)
     torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    seq_models = [cwb.Model(d.X, d.y, lrn, nu=sp["nu"], iterations=M, device=0)
+                  for sp, d, lrn in zip(specs, datasets, learner_sets)]
+    torch.cuda.synchronize()
+    t_create_seq = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    bat_models = cwb.Model.create_many([dict(X=d.X, y=d.y, learners=lrn, nu=sp["nu"], iterations=M, device=0)
+                                        for sp, d, lrn in zip(specs, datasets, learner_sets)])
+    torch.cuda.synchronize()
+    t_create_many = time.perf_counter() - t0
+    del datasets
     # sequential arm
     t_seq, coef_seq = 0.0, []
     for m in seq_models:
@@ -492,6 +500,7 @@ def run_batched(cwb, args):
     return {"fits": nf, "iterations": M, "fits_per_s": nf / t_bat, "sequential_fits_per_s": nf / t_seq,
             "speedup_vs_sequential": t_seq / t_bat, "batched_s": t_bat, "sequential_s": t_seq,
             "autotune_s": t_tune, "max_rel_coef_diff_vs_sequential": worst,
+            "setup_sequential_s": t_create_seq, "setup_create_many_s": t_create_many,
             "what": "n log-uniform 5k-500k, p uniform 5-100, n*=floor(sqrt n), L2, df in {4,5,6,8}, nu in "
                     "{0.05,0.1,0.2,0.3}, M=1000; wall clock of fit + synchronize, setup excluded"}
 

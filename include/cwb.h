@@ -153,6 +153,30 @@ cwb_status cwb_create(const cwb_config* cfg, const void* X, int32_t x_dtype, int
                       int32_t device_ptrs, cwb_model** out);
 
 /*
+ * cwb_create_many -- the setup of many fits at once (Sec. 2.4 and Sec. 3.1.2: binning, bin counts,
+ * Z^T W Z, df -> lambda and the factorisations are computed once, before boosting).  Request i holds
+ * the arguments of one cwb_create call; `threads` host threads (<= 0: up to 16) create the models
+ * concurrently, each on its own stream (cfg.stream is honoured when set), so the setup kernels and the
+ * host-side steps of different fits overlap on the GPU.  Each model equals the one cwb_create would
+ * return for the same request.  out[i] receives model i (NULL if its creation failed); status[i]
+ * (nullable) its status.  Returns CWB_OK when every request succeeded, else the status of the first
+ * failing request (its message names the request index).  device_ptrs applies to every request.
+ */
+typedef struct {
+    cwb_config cfg;
+    const void* X;          /* p x n features, as in cwb_create */
+    int32_t x_dtype;
+    int64_t n;
+    int32_t p;
+    const void* y;
+    const double* w;        /* nullable */
+    const cwb_learner* bl;
+    int32_t K;
+} cwb_fit_request;
+cwb_status cwb_create_many(const cwb_fit_request* reqs, int32_t count, int32_t device_ptrs, int32_t threads,
+                           cwb_model** out, cwb_status* status);
+
+/*
  * cwb_fit -- run `iterations` boosting iterations (<= 0: cfg.iterations) on the
  * device, continuing from the model's current state (fits are resumable).  One
  * iteration is: pseudo residuals, binMatVec scatter of W r into every binning's

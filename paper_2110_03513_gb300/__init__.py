@@ -10,6 +10,6 @@ from .binding import (  # noqa: F401
     Batch, CwbError, Model, Server, cwb_create, cwb_fit, cwb_force_selection, cwb_free, cwb_get_bin_index, cwb_get_coefficients,
     cwb_get_criteria, cwb_get_fitted, cwb_get_learner_info, cwb_get_learner_matrices, cwb_get_trace,
     cwb_get_profile, cwb_get_residuals, cwb_get_scatter_plan, cwb_last_error, cwb_predict, cwb_predict_noalloc, cwb_profile, cwb_synchronize, learner, library_path, load_library,
-    cwb_shard_create, cwb_shard_finish, cwb_shard_rows, cwb_shard_scatter, cwb_shard_sizes, cwb_shard_solve, cwb_shard_stats,
+    cwb_create_many, cwb_shard_create, cwb_shard_finish, cwb_shard_rows, cwb_shard_scatter, cwb_shard_sizes, cwb_shard_solve, cwb_shard_stats,
 )
 from .sharded import ShardedFit, split_rows, torch_allreduce, torch_allreduce_tensor  # noqa: F401

@@ -49,6 +49,11 @@ class cwb_server_config(C.Structure):
                 ("slice_iterations", C.c_int32)]
 
 
+class cwb_fit_request(C.Structure):
+    _fields_ = [("cfg", cwb_config), ("X", C.c_void_p), ("x_dtype", C.c_int32), ("n", C.c_int64), ("p", C.c_int32),
+                ("y", C.c_void_p), ("w", C.c_void_p), ("bl", C.POINTER(cwb_learner)), ("K", C.c_int32)]
+
+
 class cwb_shard_config(C.Structure):
     _fields_ = [("n_global", C.c_int64), ("xmin", C.c_void_p), ("xmax", C.c_void_p)]
 
@@ -91,6 +96,8 @@ _SIGS = {
     "cwb_server_take": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_void_p)]),
     "cwb_server_stats": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
     "cwb_server_free": (None, [C.c_void_p]),
+    "cwb_create_many": (C.c_int, [C.POINTER(cwb_fit_request), C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_void_p),
+                                  C.c_void_p]),
     "cwb_shard_create": (C.c_int, [C.POINTER(cwb_config), C.c_void_p, C.c_int32, C.c_int64, C.c_int32, C.c_void_p,
                                    C.POINTER(cwb_learner), C.c_int32, C.c_int32, C.POINTER(cwb_shard_config),
                                    C.POINTER(C.c_void_p)]),
@@ -171,6 +178,22 @@ def cwb_create(cfg: cwb_config, X, x_dtype: int, n: int, p: int, y, w, learners,
                                    device_ptrs, C.byref(out))
     _check(st, "cwb_create")
     return out
+
+
+def cwb_create_many(reqs, device_ptrs: int = 0, threads: int = 0):
+    """Create len(reqs) models (a list of cwb_fit_request); returns (handles, statuses)."""
+    count = len(reqs)
+    arr = (cwb_fit_request * count)(*reqs)
+    out = (C.c_void_p * count)()
+    st = np.zeros(count, dtype=np.int32)
+    rc = load_library().cwb_create_many(arr, count, device_ptrs, threads, out, _ptr(st))
+    handles = [C.c_void_p(h) if h else None for h in out]
+    if rc != 0:
+        for h in handles:
+            if h:
+                cwb_free(h)
+        _check(rc, "cwb_create_many")
+    return handles, st
 
 
 def cwb_fit(model, iterations: int):
@@ -333,6 +356,32 @@ class Model:
                          stream=sh, device=device)
         self.handle = cwb_create(cfg, X, _dtype_code(X), n, p, y, w, self.learners, 1 if dev else 0)
         self._keep = None
+
+    @classmethod
+    def create_many(cls, requests, threads: int = 0) -> list:
+        """Models for many fits at once (cwb_create_many: their setups overlap on the GPU).  Each request
+        is a dict with X, y, learners and the keyword arguments of Model (loss, opt, nu, gamma,
+        iterations, patience, val_mask, w; host arrays)."""
+        keep, reqs = [], []
+        for r in requests:
+            X = np.ascontiguousarray(r["X"])
+            if X.ndim == 1:
+                X = X.reshape(1, -1)
+            y = np.ascontiguousarray(r["y"], dtype=X.dtype)
+            w = None if r.get("w") is None else np.ascontiguousarray(r["w"], dtype=np.float64)
+            vm = None if r.get("val_mask") is None else np.ascontiguousarray(r["val_mask"], dtype=np.uint8)
+            lrn = list(r["learners"])
+            arr = (cwb_learner * len(lrn))(*lrn)
+            cfg = cwb_config(loss=r.get("loss", LOSS_L2), opt=r.get("opt", OPT_CWB), nu=r.get("nu", 0.1),
+                             gamma=r.get("gamma", 0.0), iterations=r.get("iterations", 100),
+                             patience=r.get("patience", 5), val_mask=None if vm is None else _ptr(vm).value,
+                             stream=None, device=r.get("device", -1))
+            p, n = int(X.shape[0]), int(X.shape[1])
+            reqs.append(cwb_fit_request(cfg=cfg, X=_ptr(X).value, x_dtype=_dtype_code(X), n=n, p=p, y=_ptr(y).value,
+                                        w=None if w is None else _ptr(w).value, bl=arr, K=len(lrn)))
+            keep.append((X, y, w, vm, arr, lrn, n, p))
+        handles, _ = cwb_create_many(reqs, 0, threads)
+        return [cls._adopt(h, n, p, lrn) for h, (_, _, _, _, _, lrn, n, p) in zip(handles, keep)]
 
     @classmethod
     def _adopt(cls, handle, n: int, p: int, learners):

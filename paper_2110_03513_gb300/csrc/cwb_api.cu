@@ -4,11 +4,13 @@
 #include <math.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <tuple>
 #include <utility>
 #include <vector>
@@ -404,6 +406,44 @@ cwb_status cwb_create(const cwb_config* cfg, const void* X, int32_t x_dtype, int
                       const double* w, const cwb_learner* bl, int32_t K, int32_t device_ptrs, cwb_model** out)
 {
     return create_model(cfg, X, x_dtype, n, p, y, w, bl, K, device_ptrs, out, kIterAuto);
+}
+
+cwb_status cwb_create_many(const cwb_fit_request* reqs, int32_t count, int32_t device_ptrs, int32_t threads,
+                           cwb_model** out, cwb_status* status)
+{
+    set_error("");
+    if (!reqs || !out || count < 0) { set_error("cwb_create_many: bad argument"); return CWB_EINVAL; }
+    if (count == 0) return CWB_OK;
+    int nt = threads > 0 ? threads : std::min(16, (int)std::max(1u, std::thread::hardware_concurrency()));
+    nt = std::max(1, std::min(nt, (int)count));
+    std::vector<cwb_status> st((size_t)count, CWB_OK);
+    std::vector<std::string> msg((size_t)count);
+    std::atomic<int32_t> next{0};
+    // each worker takes the next request and creates its model (own stream, own temporaries); the
+    // setup kernels and the host-side steps of different requests overlap
+    auto work = [&]() {
+        for (;;) {
+            const int32_t i = next.fetch_add(1);
+            if (i >= count) break;
+            const cwb_fit_request& r = reqs[i];
+            out[i] = nullptr;
+            st[i] = create_model(&r.cfg, r.X, r.x_dtype, r.n, r.p, r.y, r.w, r.bl, r.K, device_ptrs, &out[i], kIterAuto);
+            if (st[i] != CWB_OK) msg[i] = g_last_error;
+        }
+    };
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nt; ++t) pool.emplace_back(work);
+    work();
+    for (std::thread& t : pool) t.join();
+    cwb_status first = CWB_OK;
+    for (int32_t i = 0; i < count; ++i) {
+        if (status) status[i] = st[i];
+        if (st[i] != CWB_OK && first == CWB_OK) {
+            first = st[i];
+            set_error("cwb_create_many: request " + std::to_string(i) + ": " + msg[i]);
+        }
+    }
+    return first;
 }
 
 cwb_status cwb_fit(cwb_model* m, int32_t iterations)

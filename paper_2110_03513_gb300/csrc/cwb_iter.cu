@@ -1636,15 +1636,18 @@ using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t
 
 EncodeTiledFn encode_tiled_fn()
 {
-    static EncodeTiledFn fn = nullptr;
-    if (!fn) {
+    // looked up once (a function-local static is initialised once even when models are created on
+    // several host threads at the same time)
+    static const EncodeTiledFn fn = []() -> EncodeTiledFn {
         void* p = nullptr;
         cudaDriverEntryPointQueryResult q;
+        EncodeTiledFn f = nullptr;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiledFn>(p);
+            f = reinterpret_cast<EncodeTiledFn>(p);
         cudaGetLastError();
-    }
+        return f;
+    }();
     return fn;
 }
 

@@ -724,7 +724,11 @@ cwb_status init_residual_bound(cwb_model* m)
     cudaStream_t s = m->stream;
     const int sms = num_sms_p(m->device);
     uint32_t* mx = nullptr;
-    CWB_TRY(dev_alloc((void**)&mx, sizeof(uint32_t) * 2, s));
+    if (cudaMallocAsync((void**)&mx, sizeof(uint32_t) * 2, s) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("device allocation for the residual bound failed");
+        return CWB_ENOMEM;
+    }
     uint32_t mx_h[2] = {0u, 0u};
     DevState st;
     cudaError_t e = cudaMemsetAsync(mx, 0, sizeof(uint32_t) * 2, s);
@@ -735,8 +739,8 @@ cwb_status init_residual_bound(cwb_model* m)
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(mx_h, mx, sizeof(mx_h), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&st, m->state, sizeof(st), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(mx, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    dev_free(mx);
     if (e != cudaSuccess) return cuda_status(e, "residual bound at creation");
     float wmax_f = 1.0f;
     std::memcpy(&wmax_f, &mx_h[1], sizeof(float));

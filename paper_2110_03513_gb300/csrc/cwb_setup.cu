@@ -832,19 +832,27 @@ __global__ void k_init_rows(int64_t n_pad, float off_hi, float off_lo, float* f,
 
 // ---------------------------------------------------------------------------
 
+// Temporaries of a setup step: stream-ordered allocations on the model's stream, released in stream
+// order when the step ends.  Unlike cudaFree, which waits for all work on the device, this never stalls
+// on other models' kernels, so the setups of many fits (cwb_create_many) overlap.
 struct TempBuf {
-    std::vector<void*> ptrs;
+    std::vector<std::pair<void*, cudaStream_t>> ptrs;
     ~TempBuf()
     {
-        for (void* p : ptrs) dev_free(p);
+        for (auto& ps : ptrs) cudaFreeAsync(ps.first, ps.second);
     }
     template <typename T>
     cwb_status get(T** out, size_t count, cudaStream_t s)
     {
         void* p = nullptr;
-        cwb_status st = dev_alloc(&p, sizeof(T) * (count ? count : 1), s);
-        if (st != CWB_OK) return st;
-        ptrs.push_back(p);
+        const size_t bytes = sizeof(T) * (count ? count : 1);
+        cudaError_t e = cudaMallocAsync(&p, bytes, s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            set_error("device allocation of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
+            return CWB_ENOMEM;
+        }
+        ptrs.push_back({p, s});
         *out = static_cast<T*>(p);
         return CWB_OK;
     }

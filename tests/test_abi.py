@@ -64,7 +64,8 @@ def test_binding_structs_match_the_header_layout(tmp_path):
     import subprocess
     from paper_2110_03513_gb300 import binding
     structs = {name: getattr(binding, name) for name in ("cwb_learner", "cwb_config", "cwb_learner_info",
-                                                          "cwb_server_config")}
+                                                          "cwb_server_config", "cwb_shard_config",
+                                                          "cwb_fit_request")}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "cwb.h"', "int main(void) {"]
     for name, cls in structs.items():
         lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')

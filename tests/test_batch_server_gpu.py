@@ -172,3 +172,26 @@ def test_batched_fit_specs_match_the_oracle(cwb):
     batch.free()
     for m in models:
         m.free()
+
+
+def test_create_many_equals_single_creates(cwb):
+    """cwb_create_many (the setups of several fits overlapped on host threads and streams) returns the
+    models that separate cwb_create calls return: the same fits, bit for bit; a bad request is reported
+    by its index and leaves no model behind."""
+    M = 40
+    fits = _fit_specs()
+    reqs = [dict(X=d.X, y=d.y, learners=_learners(cwb, specs), nu=nu, iterations=M) for d, specs, nu in fits]
+    many = cwb.Model.create_many(reqs, threads=4)
+    for (d, specs, nu), m in zip(fits, many):
+        one = cwb.Model(d.X, d.y, _learners(cwb, specs), nu=nu, iterations=M, device=0)
+        one.fit(M)
+        m.fit(M)
+        np.testing.assert_array_equal(m.trace()[0], one.trace()[0])
+        np.testing.assert_array_equal(m.all_coefficients(0, dmax=24), one.all_coefficients(0, dmax=24))
+        np.testing.assert_array_equal(m.fitted(), one.fitted())
+        one.free()
+        m.free()
+    bad = list(reqs[:3])
+    bad[1] = dict(bad[1], learners=[cwb.learner(99)])          # a feature that does not exist
+    with pytest.raises(cwb.CwbError, match="request 1"):
+        cwb.Model.create_many(bad, threads=2)
