@@ -71,6 +71,10 @@ class GpuShard:
         if device_exchange:
             import torch
             stream = torch.cuda.current_stream().cuda_stream
+            if not stream:
+                # the legacy default stream (handle 0) would leave the model on a stream of its own,
+                # unordered with the exchange's tensor operations
+                raise ValueError("device exchange needs a created torch stream as the current stream")
         cfg = _b.cwb_config(loss=loss, opt=_b.OPT_CWB, nu=nu, gamma=0.0, iterations=iterations, patience=0,
                             val_mask=None, stream=stream, device=device)
         self.handle = _b.cwb_shard_create(cfg, X, _b._dtype_code(X), self.n, self.p, y, self.learners, 0, n_global,
@@ -139,8 +143,14 @@ class ShardedFit:
         self.xmax = self._reduce(maxs, "max")
         self.n_global = int(self._reduce(n_local, "sum")[0])
         kw = {"device_exchange": True} if device_exchange else {}
-        self.shards = [backend(X, y, learners, n_global=self.n_global, xmin=self.xmin, xmax=self.xmax, loss=loss,
-                               nu=nu, iterations=iterations, device=device, **kw) for X, y in parts]
+        self.stream = None
+        if device_exchange:
+            # one stream for the shards' work and the exchange's tensor operations, in issue order
+            import torch
+            self.stream = torch.cuda.Stream(device=device)
+        with self._on_stream():
+            self.shards = [backend(X, y, learners, n_global=self.n_global, xmin=self.xmin, xmax=self.xmax, loss=loss,
+                                   nu=nu, iterations=iterations, device=device, **kw) for X, y in parts]
         # setup exchange: bin counts and target sums (SUM), the scatter's bin-count bound (MAX)
         st = [s.stats() for s in self.shards]
         counts = self._reduce(self._local(np.stack([c for c, _, _ in st]), "sum"), "sum")
@@ -149,6 +159,13 @@ class ShardedFit:
         for s in self.shards:
             s.finish(counts, sums, clog)
         self.iterations_done = 0
+
+    def _on_stream(self):
+        import contextlib
+        if self.stream is None:
+            return contextlib.nullcontext()
+        import torch
+        return torch.cuda.stream(self.stream)
 
     def _local(self, stacked: np.ndarray, op: str) -> np.ndarray:
         return _OPS[op].reduce(stacked, axis=0)
@@ -160,12 +177,13 @@ class ShardedFit:
         """One iteration: rows -> MAX of |r| -> scatter -> SUM of the histograms -> solve."""
         if self.device_exchange:
             import torch
-            rmax = torch.stack([s.rows() for s in self.shards]).amax(dim=0)          # [1] float32 on the GPU
-            rmax = self._reduce(rmax, "max")
-            u = torch.stack([s.scatter(rmax) for s in self.shards]).sum(dim=0)      # exact int64 sums
-            u = self._reduce(u, "sum")
-            for s in self.shards:
-                s.solve(u)
+            with torch.cuda.stream(self.stream):
+                rmax = torch.stack([s.rows() for s in self.shards]).amax(dim=0)      # [1] float32 on the GPU
+                rmax = self._reduce(rmax, "max")
+                u = torch.stack([s.scatter(rmax) for s in self.shards]).sum(dim=0)  # exact int64 sums
+                u = self._reduce(u, "sum")
+                for s in self.shards:
+                    s.solve(u)
             self.iterations_done += 1
             return
         rmax = np.array([max(s.rows() for s in self.shards)], dtype=np.float32)
