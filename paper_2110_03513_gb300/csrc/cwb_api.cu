@@ -414,36 +414,46 @@ cwb_status cwb_create_many(const cwb_fit_request* reqs, int32_t count, int32_t d
     set_error("");
     if (!reqs || !out || count < 0) { set_error("cwb_create_many: bad argument"); return CWB_EINVAL; }
     if (count == 0) return CWB_OK;
-    int nt = threads > 0 ? threads : std::min(16, (int)std::max(1u, std::thread::hardware_concurrency()));
-    nt = std::max(1, std::min(nt, (int)count));
-    std::vector<cwb_status> st((size_t)count, CWB_OK);
-    std::vector<std::string> msg((size_t)count);
-    std::atomic<int32_t> next{0};
-    // each worker takes the next request and creates its model (own stream, own temporaries); the
-    // setup kernels and the host-side steps of different requests overlap
-    auto work = [&]() {
-        for (;;) {
-            const int32_t i = next.fetch_add(1);
-            if (i >= count) break;
-            const cwb_fit_request& r = reqs[i];
-            out[i] = nullptr;
-            st[i] = create_model(&r.cfg, r.X, r.x_dtype, r.n, r.p, r.y, r.w, r.bl, r.K, device_ptrs, &out[i], kIterAuto);
-            if (st[i] != CWB_OK) msg[i] = g_last_error;
+    for (int32_t i = 0; i < count; ++i) out[i] = nullptr;
+    try {
+        int nt = threads > 0 ? threads : std::min(16, (int)std::max(1u, std::thread::hardware_concurrency()));
+        nt = std::max(1, std::min(nt, (int)count));
+        std::vector<cwb_status> st((size_t)count, CWB_OK);
+        std::vector<std::string> msg((size_t)count);
+        std::atomic<int32_t> next{0};
+        // each worker takes the next request and creates its model (own stream, own temporaries); the
+        // setup kernels and the host-side steps of different requests overlap
+        auto work = [&]() {
+            for (;;) {
+                const int32_t i = next.fetch_add(1);
+                if (i >= count) break;
+                const cwb_fit_request& r = reqs[i];
+                st[i] = create_model(&r.cfg, r.X, r.x_dtype, r.n, r.p, r.y, r.w, r.bl, r.K, device_ptrs, &out[i],
+                                     kIterAuto);
+                if (st[i] != CWB_OK) msg[i] = g_last_error;
+            }
+        };
+        std::vector<std::thread> pool;
+        try {
+            for (int t = 1; t < nt; ++t) pool.emplace_back(work);
+        } catch (const std::exception&) {
+            // fewer threads than asked (the host refused more): the ones running take every request
         }
-    };
-    std::vector<std::thread> pool;
-    for (int t = 1; t < nt; ++t) pool.emplace_back(work);
-    work();
-    for (std::thread& t : pool) t.join();
-    cwb_status first = CWB_OK;
-    for (int32_t i = 0; i < count; ++i) {
-        if (status) status[i] = st[i];
-        if (st[i] != CWB_OK && first == CWB_OK) {
-            first = st[i];
-            set_error("cwb_create_many: request " + std::to_string(i) + ": " + msg[i]);
+        work();
+        for (std::thread& t : pool) t.join();
+        cwb_status first = CWB_OK;
+        for (int32_t i = 0; i < count; ++i) {
+            if (status) status[i] = st[i];
+            if (st[i] != CWB_OK && first == CWB_OK) {
+                first = st[i];
+                set_error("cwb_create_many: request " + std::to_string(i) + ": " + msg[i]);
+            }
         }
+        return first;
+    } catch (const std::exception& e) {
+        set_error(std::string("cwb_create_many: host exception: ") + e.what());
+        return CWB_ENOMEM;
     }
-    return first;
 }
 
 cwb_status cwb_fit(cwb_model* m, int32_t iterations)
