@@ -32,3 +32,17 @@ def test_reference_arm_prints_one_contract_line():
 
 def test_reference_arm_other_ranks_exit_quietly():
     assert _run({"RANK": "1", "WORLD_SIZE": "2"}) == []
+
+
+def test_cpu_baseline_reports_one_thread_and_openmp_figures():
+    """The bench's CPU baseline times the oracle on one thread and with its learner loop on every core,
+    and names the host CPU (here on a small sample so that the test stays quick)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import synthetic_inputs as S
+    data = S.additive_regression(20_000, 50, 10, seed=1, dtype=S.np.float32)
+    cb = bench.cpu_baseline_full(data, iters=2)
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] > 0
+    assert cb["nproc"] >= 1 and isinstance(cb["cpu"], str) and cb["cpu"]
+    mt = cb["openmp"]
+    assert mt["value"] > 0 and 1 <= mt["cores"] <= cb["nproc"] and mt["unit"] == cb["unit"]
