@@ -137,3 +137,33 @@ def test_gloo_ranks_equal_one_shard():
             for (ka, va), (kb, vb) in zip(log, whole.shards[0].log):
                 assert ka == kb
                 np.testing.assert_array_equal(va, vb)
+
+
+def _tensor_rank_main(rank, world, port, out):
+    import torch
+    from paper_2110_03513_gb300.sharded import torch_allreduce_tensor
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        ar = torch_allreduce_tensor()
+        u = torch.arange(6, dtype=torch.int64) * (rank + 1) + (1 << 40)
+        r = torch.tensor([0.5 + rank], dtype=torch.float32)
+        out[rank] = (ar(u, "sum").tolist(), ar(r, "max").tolist())
+    finally:
+        dist.destroy_process_group()
+
+
+def test_tensor_allreduce_sums_int64_exactly_and_takes_the_max():
+    """The in-place tensor all-reduce of the device exchange (gloo on CPU tensors here, NCCL on CUDA
+    tensors on GPUs): int64 histogram sums stay exact integers, the scale takes the maximum."""
+    world = 2
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(_tensor_rank_main, args=(world, _free_port(), out), nprocs=world, join=True,
+                       start_method="spawn")
+    want = [3 * i + 2 * (1 << 40) for i in range(6)]
+    for rank in range(world):
+        u, r = out[rank]
+        assert u == want
+        assert r == [1.5]
